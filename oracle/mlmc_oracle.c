@@ -25,7 +25,8 @@
  *     the call index inside one sample and s the sample index inside the level.  Call j gives
  *     four words x0..x3; the pairs (x0,x1) and (x2,x3) each give two normals by Box--Muller.
  *   - Uniforms from a 32-bit word x: FP64 stream u = (x + 1) 2^-32; FP32 stream
- *     u = 1 - (x >> 9) 2^-23.  Both lie in (0, 1], so log(u) is finite.
+ *     u = 1 - (x mod 2^23) 2^-23 (the low 23 bits, exactly a float mantissa).  Both lie in
+ *     (0, 1], so log(u) is finite.
  *   - Box--Muller: rho = sqrt(-2 log u1), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
  *   - Each sample draws G = max(M^l, 8) normals; fine step k takes the G / M^l consecutive
  *     normals starting at k G / M^l, dW = sqrt(T / G) * (their sum).  This keeps the Brownian
@@ -75,7 +76,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 double oracle_uniform(uint32_t x, int stream)
 {
     if (stream == STREAM_FP32)
-        return 1.0 - (double)(x >> 9) * 0x1p-23;
+        return 1.0 - (double)(x & 0x7FFFFFu) * 0x1p-23;
     return ((double)x + 1.0) * 0x1p-32;
 }
 

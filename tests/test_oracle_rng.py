@@ -41,7 +41,8 @@ def test_uniform_mapping_exact_endpoints():
     assert oracle.uniform(0xFFFFFFFF, "fp64") == 1.0
     assert oracle.uniform(0, "fp32") == 1.0
     assert oracle.uniform(0xFFFFFFFF, "fp32") == 2.0 ** -23
-    assert oracle.uniform(0x800001FF, "fp32") == 0.5          # top 23 bits select 2^22
+    assert oracle.uniform(0xFF400000, "fp32") == 0.5          # low 23 bits select 2^22
+    assert oracle.uniform(0x00800000, "fp32") == 1.0          # bit 23 and above are unused
     assert oracle.uniform(0x7FFFFFFF, "fp64") == 0.5
 
 
