@@ -1,0 +1,210 @@
+/*
+ * mlmc.h -- C ABI of the GB300 multilevel Monte Carlo level engine.
+ *
+ * The engine computes, on one GPU, the level estimators of multilevel Monte Carlo for option
+ * valuation (D. J. Higham, "An Introduction to Multilevel Monte Carlo for Option Valuation",
+ * Sec. 5): for level l it simulates N coupled pairs of Euler--Maruyama paths (Sec. 2, Eq. em)
+ * of geometric Brownian motion, the fine path with step T / M^l and the coarse path with
+ * step T / M^(l-1) driven by sums of M consecutive fine increments (Sec. 5, Fig. 2), and
+ * returns sum Y, sum Y^2, sum Y^3, sum Y^4 of Y = P_l - P_{l-1} (Eq. Yldef; Y = P_0 on
+ * level 0, Eq. mlmc:Yzero).  The adaptive driver combines the levels by the telescoping sum
+ * of Eq. (mlmc:ident).
+ *
+ * Conventions for every function below:
+ *   - Return value: an mlmc_status; 0 (MLMC_OK) on success.  On failure the outputs are left
+ *     untouched and mlmc_last_error() returns a message for the calling host thread.
+ *   - Pointers documented as "host" are caller-owned host memory, read or written only during
+ *     the call.  Pointers documented as "device" are caller-owned device memory on the current
+ *     CUDA device; the engine only reads or writes them in work queued on the given stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Functions with host outputs synchronise `stream` before returning.  Functions with the
+ *     _async suffix only queue work on `stream` and never synchronise.
+ *   - All floating-point arguments are FP64; the path arithmetic precision is chosen by an
+ *     mlmc_precision argument.
+ *   - Random numbers: sample s of level l draws Philox4x32-10 blocks with key = (seed low,
+ *     seed high) and counter = (j, s low, s high, (tag << 16) | l), j = 0, 1, ...  Each block
+ *     gives two Box--Muller pairs.  Every level and every sample index therefore has its own,
+ *     independent numbers (Sec. 5: fresh random numbers on every level), and a sample range
+ *     [first, first + N) can be computed in any order, on any device, with identical results.
+ */
+#ifndef MLMC_GB300_H
+#define MLMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mlmc_status {
+    MLMC_OK = 0,
+    MLMC_EINVAL = 1,      /* an argument is out of range or a required pointer is NULL */
+    MLMC_ECUDA = 2,       /* a CUDA call failed; the message carries the CUDA error string */
+    MLMC_ENOMEM = 3,      /* a device or host allocation failed */
+    MLMC_ENOTCONV = 4,    /* the driver reached Lmax before the bias test passed */
+    MLMC_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
+    MLMC_ENOTIMPL = 6     /* the combination of options is not implemented */
+} mlmc_status;
+
+/* Model: geometric Brownian motion dS = r S dt + sigma S dW, S(0) = S0, on [0, T]
+ * (the SDE of Sec. 2, Eq. sde, with f(x) = r x and g(x) = sigma x as in Sec. 6). */
+typedef enum mlmc_model_kind { MLMC_MODEL_GBM = 0 } mlmc_model_kind;
+typedef struct mlmc_model {
+    int32_t kind;          /* mlmc_model_kind */
+    int32_t reserved;      /* must be 0 */
+    double S0, r, sigma, T; /* S0 > 0, sigma > 0, T > 0, all finite */
+} mlmc_model;
+
+/* Payoffs, discounted by exp(-r T) (Sec. 6):
+ *   EUROPEAN  max(S_n - K, 0)                                   (Sec. 5, Sec. 6)
+ *   ASIAN     max(A - K, 0), A = (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 on the path's own grid
+ *   LOOKBACK  max(max_{0<=i<=n} S_i - K, 0)  (fixed strike, discrete monitoring)
+ *   DIGITAL   cash * 1{S_n > K}, cash / 2 when S_n == K        (Sec. 6)
+ *   LINEAR_TEST     S_n, not discounted (test payoff with exact Euler--Maruyama moments)
+ *   GEO_ASIAN_TEST  max(exp((1/n) sum (log S_i + log S_{i+1}) / 2) - K, 0) (closed-form test)
+ * The paper names the Asian and lookback options (Sec. 7) without defining them; the
+ * definitions above are this library's reading. */
+typedef enum mlmc_payoff_kind {
+    MLMC_EUROPEAN = 0, MLMC_ASIAN = 1, MLMC_LOOKBACK = 2, MLMC_DIGITAL = 3,
+    MLMC_LINEAR_TEST = 100, MLMC_GEO_ASIAN_TEST = 101
+} mlmc_payoff_kind;
+typedef struct mlmc_payoff {
+    int32_t kind;          /* mlmc_payoff_kind */
+    int32_t reserved;      /* must be 0 */
+    double K;              /* strike, finite */
+    double cash;           /* digital cash amount (Sec. 6 uses 100), finite */
+} mlmc_payoff;
+
+/* Path arithmetic precision.  Moment sums are FP64 in both. */
+typedef enum mlmc_precision {
+    MLMC_FP64 = 0,         /* FP64 normals (32-bit uniforms) and FP64 paths */
+    MLMC_FP32_PATH = 1     /* FP32 normals (23-bit uniforms) and FP32 paths */
+} mlmc_precision;
+
+/* Random-number stream tags (the `tag` field of the Philox counter). */
+enum { MLMC_TAG_PATHS = 0, MLMC_TAG_CV_MEAN = 1, MLMC_TAG_CV_TRAIN = 2 };
+
+/* Launch shape of one level kernel.  Zero in a field means "choose automatically".
+ *   threads_per_block  multiple of 32, 32..1024
+ *   lanes_per_path     1 (one thread per sample) or a power of two up to 32: that many lanes of
+ *                      one warp split the time steps of one sample into equal chunks and join
+ *                      them by a product scan (GBM's step is multiplicative); requires
+ *                      M^l / lanes_per_path to be a multiple of max(M, 4)
+ *   blocks             grid size; the kernel strides over the samples */
+typedef struct mlmc_launch {
+    int32_t threads_per_block;
+    int32_t lanes_per_path;
+    int32_t blocks;
+    int32_t reserved;      /* must be 0 */
+} mlmc_launch;
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char *mlmc_last_error(void);
+
+/* Library version string. */
+const char *mlmc_version(void);
+
+/*
+ * mlmc_level_sums -- the level estimator of Sec. 5, Eq. (Yldef) (Eq. mlmc:Yzero at l = 0),
+ * in its short form: samples [0, N), FP32 paths, tag MLMC_TAG_PATHS, default stream.
+ *   level   0..12, with M^level <= 2^24
+ *   M       refinement factor of Eq. (mlmc:Dtl): 2, 4 or 8
+ *   N       number of samples (0 gives zero sums and cost)
+ *   model, payoff   host, read only
+ *   seed    64-bit Philox key
+ *   sums    host, 4 doubles written: sum over samples of Y, Y^2, Y^3, Y^4
+ *   cost    host, 1 double written: N * C_l with C_0 = 1, C_l = M^l + M^(l-1), the number of
+ *           Euler--Maruyama steps taken (the cost measure of Sec. 3)
+ * Errors: MLMC_EINVAL for out-of-range arguments or NULL pointers; MLMC_ECUDA if a CUDA call
+ * fails (no device, launch failure).
+ */
+int mlmc_level_sums(int level, int M, uint64_t N, const mlmc_model *model,
+                    const mlmc_payoff *payoff, uint64_t seed, double sums[4], double *cost);
+
+/*
+ * mlmc_level_sums_ex -- the same estimator over samples [first, first + N) with explicit
+ * precision, random-stream tag, launch shape (NULL = automatic) and stream.  Adaptive drivers
+ * pass first = the number of samples already taken on this level, so that every round draws
+ * new samples.  Host outputs as in mlmc_level_sums; synchronises `stream`.  The engine
+ * allocates its small reduction workspace with stream-ordered allocation on `stream`.
+ * Errors: as mlmc_level_sums; MLMC_EINVAL also if first + N overflows 64 bits or the launch
+ * shape is invalid for this level.
+ */
+int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,
+                       const mlmc_payoff *payoff, uint64_t seed, int precision, int tag,
+                       const mlmc_launch *launch, void *stream, double sums[4], double *cost);
+
+/* Bytes of device workspace that mlmc_level_sums_async needs for this launch shape
+ * (NULL = automatic shape); 0 on invalid arguments. */
+size_t mlmc_level_workspace_bytes(int level, int M, uint64_t N, int precision,
+                                  const mlmc_launch *launch);
+
+/*
+ * mlmc_level_sums_async -- queue the level estimator on `stream` with device outputs:
+ *   d_sums       device, 4 doubles overwritten with sum Y^k, k = 1..4
+ *   d_workspace  device, at least mlmc_level_workspace_bytes(...) bytes, 256-byte aligned,
+ *                zero-filled before its first use; every launch leaves it zero-filled again.
+ *                Launches that share one workspace must be ordered (same stream).
+ *   d_y          device or NULL: if not NULL, N doubles receive Y of each sample in order
+ * Never synchronises and allocates nothing.  Errors: MLMC_EINVAL (also for a workspace that is
+ * too small or misaligned), MLMC_ECUDA for a failed launch.
+ */
+int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first,
+                          const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
+                          int precision, int tag, const mlmc_launch *launch, double *d_sums,
+                          void *d_workspace, size_t workspace_bytes, double *d_y, void *stream);
+
+/* Result of one adaptive estimate (Sec. 5).  Arrays are indexed by level 0..L. */
+#define MLMC_MAX_LEVELS 16
+typedef struct mlmc_result {
+    double P;                        /* estimate sum_l mean_l, Eq. (mlmc:ident) */
+    double eps;                      /* requested root-mean-square accuracy */
+    int32_t L;                       /* finest level used */
+    int32_t converged;               /* 1 if the bias test passed */
+    int32_t rounds;                  /* sampling rounds taken */
+    int32_t reserved;
+    uint64_t N[MLMC_MAX_LEVELS];      /* samples per level */
+    double sums[MLMC_MAX_LEVELS][4];  /* sum Y^k per level */
+    double mean[MLMC_MAX_LEVELS];     /* sample mean of Y_l */
+    double var[MLMC_MAX_LEVELS];      /* sample variance of Y_l */
+    double cost[MLMC_MAX_LEVELS];     /* N_l C_l */
+    double alpha, beta;              /* fitted weak and variance rates (base M) */
+    double total_cost;               /* sum_l N_l C_l */
+    double path_steps;               /* sum_l N_l M^l: coupled fine steps simulated */
+    double kernel_ms;                /* device time of the level kernels */
+    double wall_ms;                  /* host wall time of the call */
+} mlmc_result;
+
+/*
+ * mlmc_estimate -- adaptive multilevel Monte Carlo estimate of E[h(X(T))] to root-mean-square
+ * accuracy eps (Sec. 5; mean-square error bound of the Theorem in Sec. 5).
+ *   Start with levels 0..Lmin and N0 samples each.  After every round of sampling, estimate
+ *   V_l and set N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)) (the variance target
+ *   eps^2 / 2 at least cost, the pre-processing optimisation remarked on in Sec. 5).  When no
+ *   level needs more than 1% more samples, test the bias estimate
+ *   max(|m_L|, |m_{L-1}| / M^alpha) / (M^alpha - 1) against eps / sqrt(2) and add a level
+ *   (variance extrapolated as V_{L-1} / M^beta) if it fails.  alpha, beta are least-squares
+ *   slopes over levels 1..L, floored at 1/2; for l >= 2 the means and variances used in these
+ *   formulas are floored at half the extrapolation from the level below.
+ *   eps > 0; M in {2, 4, 8}; 1 <= Lmin <= Lmax < MLMC_MAX_LEVELS, M^Lmax <= 2^24; N0 >= 2.
+ *   model, payoff  host, read only.  out  host, written on success and on MLMC_ENOTCONV.
+ *   stream  void* cudaStream_t (NULL = default); synchronised before return.
+ * Errors: MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM; MLMC_ENOTCONV when Lmax is reached first
+ * (out then holds the estimate at L = Lmax).
+ */
+int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc_model *model,
+                  const mlmc_payoff *payoff, uint64_t seed, int precision, void *stream,
+                  mlmc_result *out);
+
+/* Number of streaming multiprocessors of the current device, or -1 with an error message. */
+int mlmc_device_sm_count(void);
+
+/* Release every device resource the library holds on the current device. */
+int mlmc_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_GB300_H */

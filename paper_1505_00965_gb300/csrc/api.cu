@@ -1,0 +1,544 @@
+// api.cu -- the C ABI declared in include/mlmc.h: argument checks, launch planning, the
+// workspace, and the adaptive multilevel driver (host side, FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "mlmc.h"
+
+using namespace mlmcgb;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));            \
+    } while (0)
+
+long ipow(long b, int e)
+{
+    long p = 1;
+    while (e-- > 0) p *= b;
+    return p;
+}
+
+bool valid_payoff_kind(int k)
+{
+    return k == kEuropean || k == kAsian || k == kLookback || k == kDigital || k == kLinear ||
+           k == kGeoAsian;
+}
+
+int check_problem(const mlmc_model *model, const mlmc_payoff *payoff)
+{
+    if (!model || !payoff) return fail(MLMC_EINVAL, "model and payoff must not be NULL");
+    if (model->kind != MLMC_MODEL_GBM || model->reserved != 0)
+        return fail(MLMC_EINVAL, "unsupported model kind %d", model->kind);
+    if (!(model->S0 > 0) || !std::isfinite(model->S0) || !(model->sigma > 0) ||
+        !std::isfinite(model->sigma) || !(model->T > 0) || !std::isfinite(model->T) ||
+        !std::isfinite(model->r))
+        return fail(MLMC_EINVAL, "GBM needs finite S0 > 0, sigma > 0, T > 0 and r");
+    if (!valid_payoff_kind(payoff->kind) || payoff->reserved != 0)
+        return fail(MLMC_EINVAL, "unsupported payoff kind %d", payoff->kind);
+    if (!std::isfinite(payoff->K) || !std::isfinite(payoff->cash))
+        return fail(MLMC_EINVAL, "payoff K and cash must be finite");
+    return MLMC_OK;
+}
+
+int check_level(int level, int M)
+{
+    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8 (got %d)", M);
+    if (level < 0 || level >= MLMC_MAX_LEVELS || ipow(M, level) > (1L << 24))
+        return fail(MLMC_EINVAL, "level %d out of range for M = %d (need M^level <= 2^24)", level, M);
+    return MLMC_OK;
+}
+
+struct Plan {
+    const void *kernel;
+    int threads, lanes, blocks;
+};
+
+int device_sms(int *sms)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+    return MLMC_OK;
+}
+
+// Largest grid the workspace must hold for a given block size: resident blocks of the kernel.
+int max_resident_blocks(const void *kernel, int threads, int *out)
+{
+    int sms = 0, per_sm = 0;
+    int rc = device_sms(&sms);
+    if (rc) return rc;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+    if (per_sm < 1) return fail(MLMC_EINVAL, "level kernel cannot run with %d threads per block", threads);
+    *out = per_sm * sms;
+    return MLMC_OK;
+}
+
+// Launch shape for one level: explicit fields of `launch` win, zeros are filled in.
+int plan_level(int level, int M, uint64_t N, int precision, int payoff, const mlmc_launch *launch,
+               Plan *plan)
+{
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
+    const long nf = ipow(M, level);
+    const int unit = std::max(M, 4);  // a lane's chunk holds whole Philox blocks and coarse steps
+    int threads = launch && launch->threads_per_block ? launch->threads_per_block : 256;
+    if (threads < 32 || threads > 1024 || threads % 32)
+        return fail(MLMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
+    int lanes = launch && launch->lanes_per_path ? launch->lanes_per_path : 0;
+    if (lanes) {
+        if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
+            return fail(MLMC_EINVAL, "lanes_per_path must be a power of two in [1, 32]");
+        if (lanes > 1 && (nf < 8 || (nf / lanes) % unit != 0 || nf % lanes != 0))
+            return fail(MLMC_EINVAL, "lanes_per_path %d does not divide M^l = %ld into chunks of a "
+                        "multiple of %d steps", lanes, nf, unit);
+    } else {
+        // Enough independent samples keep every SM busy with one thread per sample; deep levels
+        // with few samples split each path over several lanes instead.
+        int sms = 0;
+        int rc = device_sms(&sms);
+        if (rc) return rc;
+        lanes = 1;
+        const double want_threads = (double)sms * 2048.0;
+        while (lanes < 32 && (double)N * lanes < want_threads && nf / (2 * lanes) >= 32 &&
+               (nf / (2 * lanes)) % unit == 0)
+            lanes *= 2;
+    }
+    const bool split = lanes > 1;
+    const int mt = M == 4 ? 4 : 0;
+    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split)
+                                               : level_kernel_fp64(payoff, mt, split);
+    if (!plan->kernel) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
+    int max_blocks = 0;
+    int rc = max_resident_blocks(plan->kernel, threads, &max_blocks);
+    if (rc) return rc;
+    int blocks = launch && launch->blocks ? launch->blocks : 0;
+    if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
+    if (!blocks) {
+        const double need = std::ceil((double)std::max<uint64_t>(N, 1) * lanes / threads);
+        blocks = (int)std::min<double>(need, max_blocks);
+    }
+    blocks = std::max(blocks, 1);
+    plan->threads = threads;
+    plan->lanes = lanes;
+    plan->blocks = blocks;
+    return MLMC_OK;
+}
+
+void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
+                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes)
+{
+    const long nf = ipow(M, level);
+    p.S0 = m->S0;
+    p.disc = std::exp(-m->r * m->T);
+    p.K = pay->K;
+    p.Q = pay->cash;
+    const double h = m->T / (double)nf;
+    p.small = nf < 8 ? 1 : 0;
+    p.a = m->sigma * std::sqrt(p.small ? m->T / 8.0 : h);
+    p.rh = m->r * h;
+    p.inv_nf = 1.0 / (double)nf;
+    p.inv_nc = level > 0 ? (double)M / (double)nf : 0.0;
+    p.first = first;
+    p.N = N;
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.ctr3 = ((uint32_t)tag << 16) | (uint32_t)level;
+    p.level = level;
+    p.M = M;
+    p.nf = (int)nf;
+    p.lanes = lanes;
+    p.partials = nullptr;
+    p.out = nullptr;
+    p.ticket = nullptr;
+    p.y_out = nullptr;
+}
+
+double level_cost(int level, int M)
+{
+    return level == 0 ? 1.0 : (double)(ipow(M, level) + ipow(M, level - 1));
+}
+
+int check_tag(int tag)
+{
+    if (tag < 0 || tag > 0xFFFF) return fail(MLMC_EINVAL, "tag must be in [0, 65535]");
+    return MLMC_OK;
+}
+
+int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st)
+{
+    p.partials = (double *)ws;
+    const size_t partial_bytes = workspace_bytes_for_blocks(plan.blocks) - 256;
+    p.ticket = (unsigned *)((char *)ws + partial_bytes);
+    void *args[] = {&p};
+    CUDA_TRY(cudaLaunchKernel(plan.kernel, dim3(plan.blocks), dim3(plan.threads), args, 0, st));
+    return MLMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mlmc_last_error(void) { return g_error.c_str(); }
+
+const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+int mlmc_device_sm_count(void)
+{
+    int sms = 0;
+    if (device_sms(&sms)) return -1;
+    return sms;
+}
+
+int mlmc_shutdown(void)
+{
+    return MLMC_OK;
+}
+
+size_t mlmc_level_workspace_bytes(int level, int M, uint64_t N, int precision,
+                                  const mlmc_launch *launch)
+{
+    if (check_level(level, M)) return 0;
+    Plan plan;
+    if (plan_level(level, M, N, precision, kEuropean, launch, &plan)) return 0;
+    // The grid the planner picks depends on the payoff's kernel; size for the largest grid any
+    // of them can get: an explicit block count, or 32 resident blocks on every SM.
+    int sms = 0;
+    if (device_sms(&sms)) return 0;
+    const int bound = launch && launch->blocks ? launch->blocks : sms * 32;
+    return workspace_bytes_for_blocks(bound);
+}
+
+int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,
+                          const mlmc_payoff *payoff, uint64_t seed, int precision, int tag,
+                          const mlmc_launch *launch, double *d_sums, void *d_workspace,
+                          size_t workspace_bytes, double *d_y, void *stream)
+{
+    int rc = check_level(level, M);
+    if (!rc) rc = check_problem(model, payoff);
+    if (!rc) rc = check_tag(tag);
+    if (rc) return rc;
+    if (!d_sums) return fail(MLMC_EINVAL, "d_sums must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan plan;
+    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    if (rc) return rc;
+    if (N == 0) {
+        CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
+        return MLMC_OK;
+    }
+    if (!d_workspace || ((uintptr_t)d_workspace & 255))
+        return fail(MLMC_EINVAL, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < workspace_bytes_for_blocks(plan.blocks))
+        return fail(MLMC_EINVAL, "workspace of %zu bytes is smaller than the %zu this launch needs",
+                    workspace_bytes, workspace_bytes_for_blocks(plan.blocks));
+    LevelParams p;
+    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+    p.out = d_sums;
+    p.y_out = d_y;
+    return launch_level(plan, p, d_workspace, st);
+}
+
+int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,
+                       const mlmc_payoff *payoff, uint64_t seed, int precision, int tag,
+                       const mlmc_launch *launch, void *stream, double sums[4], double *cost)
+{
+    int rc = check_level(level, M);
+    if (!rc) rc = check_problem(model, payoff);
+    if (!rc) rc = check_tag(tag);
+    if (rc) return rc;
+    if (!sums || !cost) return fail(MLMC_EINVAL, "sums and cost must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan plan;
+    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    if (rc) return rc;
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    if (N > 0) {
+        const size_t ws_bytes = workspace_bytes_for_blocks(plan.blocks) + 256;
+        void *ws = nullptr;
+        CUDA_TRY(cudaMallocAsync(&ws, ws_bytes, st));
+        cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, st);
+        LevelParams p;
+        fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+        p.out = (double *)((char *)ws + ws_bytes - 256);
+        if (e == cudaSuccess) rc = launch_level(plan, p, ws, st);
+        else rc = fail(MLMC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+        if (!rc) {
+            e = cudaMemcpyAsync(out, p.out, sizeof(out), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) rc = fail(MLMC_ECUDA, "cudaMemcpyAsync failed: %s", cudaGetErrorString(e));
+        }
+        cudaFreeAsync(ws, st);
+        e = cudaStreamSynchronize(st);
+        if (!rc && e != cudaSuccess) rc = fail(MLMC_ECUDA, "level kernel failed: %s", cudaGetErrorString(e));
+        if (rc) return rc;
+    }
+    std::memcpy(sums, out, sizeof(out));
+    *cost = (double)N * level_cost(level, M);
+    return MLMC_OK;
+}
+
+int mlmc_level_sums(int level, int M, uint64_t N, const mlmc_model *model,
+                    const mlmc_payoff *payoff, uint64_t seed, double sums[4], double *cost)
+{
+    return mlmc_level_sums_ex(level, M, N, 0, model, payoff, seed, MLMC_FP32_PATH, MLMC_TAG_PATHS,
+                              nullptr, nullptr, sums, cost);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adaptive driver (Sec. 5)
+
+namespace {
+
+double lsq_slope(const std::vector<double> &x, const std::vector<double> &y)
+{
+    const size_t n = x.size();
+    double mx = 0, my = 0;
+    for (size_t i = 0; i < n; ++i) {
+        mx += x[i];
+        my += y[i];
+    }
+    mx /= n;
+    my /= n;
+    double sxy = 0, sxx = 0;
+    for (size_t i = 0; i < n; ++i) {
+        sxy += (x[i] - mx) * (y[i] - my);
+        sxx += (x[i] - mx) * (x[i] - mx);
+    }
+    return sxy / sxx;
+}
+
+struct DriverState {
+    int M, L;
+    std::vector<uint64_t> N;
+    std::vector<std::array<double, 4>> S;
+    std::vector<double> mean, var, C;
+    double alpha = 0.5, beta = 0.5;
+};
+
+// Weak and variance rates: least-squares slopes of log_M |m_l| and log_M V_l over l = 1..L,
+// floored at 1/2.
+void fit_rates(DriverState &d)
+{
+    const double tiny = 1e-300, lnM = std::log((double)d.M);
+    std::vector<double> ls, lm, lv;
+    for (int l = 1; l <= d.L; ++l) {
+        ls.push_back(l);
+        lm.push_back(std::log(std::max(std::fabs(d.mean[l]), tiny)) / lnM);
+        lv.push_back(std::log(std::max(d.var[l], tiny)) / lnM);
+    }
+    d.alpha = std::max(0.5, -lsq_slope(ls, lm));
+    d.beta = std::max(0.5, -lsq_slope(ls, lv));
+}
+
+// Means and variances used by the formulas: for l >= 2, at least half the extrapolation
+// from the level below.
+void floored(const DriverState &d, std::vector<double> &mf, std::vector<double> &vf)
+{
+    mf = d.mean;
+    vf = d.var;
+    const double Ma = std::pow((double)d.M, d.alpha), Mb = std::pow((double)d.M, d.beta);
+    for (size_t l = 2; l < mf.size(); ++l) {
+        mf[l] = std::max(std::fabs(mf[l]), 0.5 * std::fabs(mf[l - 1]) / Ma);
+        vf[l] = std::max(vf[l], 0.5 * vf[l - 1] / Mb);
+    }
+}
+
+double bias_estimate(const std::vector<double> &mf, int M, double alpha)
+{
+    const int L = (int)mf.size() - 1;
+    const double Ma = std::pow((double)M, alpha);
+    return std::max(std::fabs(mf[L]), std::fabs(mf[L - 1]) / Ma) / (Ma - 1.0);
+}
+
+// N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)); dN_l = max(0, N_l - done_l).
+std::vector<uint64_t> extra_samples(const std::vector<double> &V, const std::vector<double> &C,
+                                    const std::vector<uint64_t> &done, double eps)
+{
+    double tot = 0;
+    for (size_t l = 0; l < V.size(); ++l) tot += std::sqrt(V[l] * C[l]);
+    std::vector<uint64_t> dN(V.size(), 0);
+    for (size_t l = 0; l < V.size(); ++l) {
+        const double n = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * tot);
+        const uint64_t want = n > 9.0e18 ? (uint64_t)9.0e18 : (uint64_t)n;
+        dN[l] = want > done[l] ? want - done[l] : 0;
+    }
+    return dN;
+}
+
+}  // namespace
+
+extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
+                             const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
+                             int precision, void *stream, mlmc_result *out)
+{
+    const auto t_start = std::chrono::steady_clock::now();
+    int rc = check_problem(model, payoff);
+    if (rc) return rc;
+    if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(MLMC_EINVAL, "eps must be positive and finite");
+    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
+    if (Lmin < 1 || Lmax < Lmin || Lmax >= MLMC_MAX_LEVELS || ipow(M, Lmax) > (1L << 24))
+        return fail(MLMC_EINVAL, "need 1 <= Lmin <= Lmax < %d and M^Lmax <= 2^24", MLMC_MAX_LEVELS);
+    if (N0 < 2) return fail(MLMC_EINVAL, "N0 must be at least 2");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // One workspace for every launch of this call: launches are ordered on `st`.
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    const int ws_blocks = sms * 32;
+    const size_t ws_bytes = workspace_bytes_for_blocks(ws_blocks);
+    void *ws = nullptr;
+    double *d_sums = nullptr;
+    double *h_sums = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    CUDA_TRY(cudaMalloc(&ws, ws_bytes));
+    auto cleanup = [&]() {
+        if (ws) cudaFree(ws);
+        if (d_sums) cudaFree(d_sums);
+        if (h_sums) cudaFreeHost(h_sums);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    };
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        cleanup();
+        return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaMemset(ws, 0, ws_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "driver setup");
+
+    DriverState d;
+    d.M = M;
+    d.L = Lmin;
+    d.N.assign(Lmin + 1, 0);
+    d.S.assign(Lmin + 1, {0.0, 0.0, 0.0, 0.0});
+    d.C.clear();
+    for (int l = 0; l <= Lmin; ++l) d.C.push_back(level_cost(l, M));
+    std::vector<uint64_t> dN(Lmin + 1, N0);
+    double kernel_ms = 0.0;
+    int rounds = 0;
+    while (std::any_of(dN.begin(), dN.end(), [](uint64_t v) { return v > 0; })) {
+        ++rounds;
+        if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (int l = 0; l <= d.L; ++l) {
+            if (!dN[l]) continue;
+            Plan plan;
+            rc = plan_level(l, M, dN[l], precision, payoff->kind, nullptr, &plan);
+            if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+            LevelParams p;
+            fill_params(p, l, M, dN[l], d.N[l], model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+            p.out = d_sums + 4 * l;
+            rc = launch_level(plan, p, ws, st);
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+        }
+        if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        e = cudaMemcpyAsync(h_sums, d_sums, (d.L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "level round");
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) kernel_ms += ms;
+        for (int l = 0; l <= d.L; ++l) {
+            if (!dN[l]) continue;
+            for (int k = 0; k < 4; ++k) d.S[l][k] += h_sums[4 * l + k];
+            d.N[l] += dN[l];
+        }
+        d.mean.assign(d.L + 1, 0.0);
+        d.var.assign(d.L + 1, 0.0);
+        for (int l = 0; l <= d.L; ++l) {
+            d.mean[l] = d.S[l][0] / (double)d.N[l];
+            d.var[l] = std::max(d.S[l][1] / (double)d.N[l] - d.mean[l] * d.mean[l], 0.0);
+        }
+        fit_rates(d);
+        std::vector<double> mf, vf;
+        floored(d, mf, vf);
+        dN = extra_samples(vf, d.C, d.N, eps);
+        bool settled = true;
+        for (int l = 0; l <= d.L; ++l)
+            if ((double)dN[l] > 0.01 * (double)d.N[l]) settled = false;
+        if (settled && bias_estimate(mf, M, d.alpha) > eps / std::sqrt(2.0) && d.L < Lmax) {
+            d.L += 1;
+            vf.push_back(vf.back() / std::pow((double)M, d.beta));
+            d.N.push_back(0);
+            d.S.push_back({0.0, 0.0, 0.0, 0.0});
+            d.C.push_back(level_cost(d.L, M));
+            dN = extra_samples(vf, d.C, d.N, eps);
+        }
+    }
+    std::vector<double> mf, vf;
+    floored(d, mf, vf);
+    const bool converged = bias_estimate(mf, M, d.alpha) <= eps / std::sqrt(2.0);
+    cleanup();
+
+    std::memset(out, 0, sizeof(*out));
+    out->eps = eps;
+    out->L = d.L;
+    out->converged = converged ? 1 : 0;
+    out->rounds = rounds;
+    double P = 0.0, total = 0.0, steps = 0.0;
+    for (int l = 0; l <= d.L; ++l) {
+        out->N[l] = d.N[l];
+        for (int k = 0; k < 4; ++k) out->sums[l][k] = d.S[l][k];
+        out->mean[l] = d.mean[l];
+        out->var[l] = d.var[l];
+        out->cost[l] = (double)d.N[l] * d.C[l];
+        P += d.mean[l];
+        total += out->cost[l];
+        steps += (double)d.N[l] * (double)ipow(M, l);
+    }
+    out->P = P;
+    out->alpha = d.alpha;
+    out->beta = d.beta;
+    out->total_cost = total;
+    out->path_steps = steps;
+    out->kernel_ms = kernel_ms;
+    out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (!converged) {
+        fail(MLMC_ENOTCONV, "bias test still failing at Lmax = %d", Lmax);
+        return MLMC_ENOTCONV;
+    }
+    return MLMC_OK;
+}

@@ -1,0 +1,46 @@
+// engine.h -- internal interface between the C ABI and the level kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace mlmcgb {
+
+// Payoff codes, equal to the public mlmc_payoff_kind values.
+enum : int { kEuropean = 0, kAsian = 1, kLookback = 2, kDigital = 3, kLinear = 100, kGeoAsian = 101 };
+
+// Everything one level launch needs, passed by value as the kernel argument.
+struct LevelParams {
+    double S0;        // initial value
+    double disc;      // exp(-r T)
+    double K, Q;      // strike, digital cash
+    double a;         // sigma * sqrt(grid step): grid step = T / M^l, or T / 8 on small levels
+    double rh;        // r * fine step
+    double inv_nf;    // 1 / M^l
+    double inv_nc;    // 1 / M^(l-1)
+    uint64_t first;   // first sample index
+    uint64_t N;       // number of samples
+    uint32_t key0, key1;  // Philox key (seed low, seed high)
+    uint32_t ctr3;        // Philox counter word 3: (tag << 16) | level
+    int level, M;
+    int nf;           // fine steps M^l
+    int lanes;        // lanes per sample (1 = one thread per sample)
+    int small;        // 1 when M^l < 8: the sample draws 8 normals on the T/8 grid
+    double *partials; // [gridDim.x][4] block partial sums (workspace)
+    double *out;      // [4] level sums (device)
+    unsigned *ticket; // completion counter (workspace), zero between launches
+    double *y_out;    // optional per-sample Y, NULL = off
+};
+
+// Workspace layout: partial sums of `blocks` blocks, then the ticket word.
+inline size_t workspace_bytes_for_blocks(int blocks)
+{
+    size_t partial = (size_t)blocks * 4 * sizeof(double);
+    partial = (partial + 255) / 256 * 256;
+    return partial + 256;
+}
+
+// Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel.
+const void *level_kernel_fp32(int payoff, int mt, bool split);
+const void *level_kernel_fp64(int payoff, int mt, bool split);
+
+}  // namespace mlmcgb

@@ -1,0 +1,9 @@
+// level_fp32.cu -- FP32-path level kernels (FP32 normals and paths, FP64 moment sums).
+#include "level_kernel.cuh"
+
+namespace mlmcgb {
+const void *level_kernel_fp32(int payoff, int mt, bool split)
+{
+    return select_level_kernel<float>(payoff, mt, split);
+}
+}  // namespace mlmcgb

@@ -1,0 +1,9 @@
+// level_fp64.cu -- FP64-path level kernels (FP64 normals, paths and moment sums).
+#include "level_kernel.cuh"
+
+namespace mlmcgb {
+const void *level_kernel_fp64(int payoff, int mt, bool split)
+{
+    return select_level_kernel<double>(payoff, mt, split);
+}
+}  // namespace mlmcgb

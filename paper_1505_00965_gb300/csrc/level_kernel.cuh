@@ -1,0 +1,364 @@
+// level_kernel.cuh -- one level of multilevel Monte Carlo on the GPU (Sec. 5).
+//
+// For each sample s in [first, first + N) the kernel simulates, in registers, the fine
+// Euler--Maruyama path of GBM with step h = T / M^l and the coarse path with step M h driven by
+// sums of M consecutive fine increments (Sec. 2 Eq. em; Sec. 5 Eq. Yldef and Fig. 2), evaluates
+// the payoff difference Y = P_l - P_{l-1} (Y = P_0 on level 0, Eq. mlmc:Yzero), and accumulates
+// sum Y^k, k = 1..4, in FP64.  Warp shuffles and shared memory reduce each block to four
+// doubles; the last block to finish adds the block partials in a fixed order, so the result
+// does not depend on scheduling.
+//
+// GBM's Euler--Maruyama step is S_{n+1} = S_n (1 + d_n) with d_n = r h + sigma dW_n, so the step
+// is written S <- fma(S, d, S) and the coarse factor is 1 + sum of the M fine d_n (their sum is
+// r M h + sigma dW_coarse).  With lanes_per_path > 1 a sample's time steps are split into equal
+// chunks, one per lane; every lane runs its chunk from the value 1, and a product scan over the
+// lanes gives each chunk's true starting value (the recurrence is linear in S).
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "engine.h"
+#include "rng.cuh"
+
+namespace mlmcgb {
+
+// Running state of one path over the steps a lane simulates.  The step loops below keep these
+// values in local scalars and store the struct once at the end: an FP64 build that updated the
+// struct's members through a reference inside the loop lost the updates (every step restarted
+// from the initial value), while the same arithmetic on local scalars is exact.
+template <typename R, int PAY, bool SPLIT> struct PathAcc {
+    R S;     // current value (relative to the chunk's start when SPLIT)
+    R sum;   // sum of the values after each step (Asian)
+    R hi;    // largest value seen, start included (lookback)
+    R lo;    // smallest value seen (lookback, SPLIT only: a negative start flips max and min)
+    R lsum;  // sum of log of the values after each step (geometric Asian test payoff)
+
+    __device__ __forceinline__ void init(R x0)
+    {
+        S = x0;
+        sum = R(0);
+        hi = x0;
+        lo = x0;
+        lsum = R(0);
+    }
+    __device__ __forceinline__ static R log_r(R x)
+    {
+        return log(x);  // test payoff only: the accurate library logarithm
+    }
+};
+
+// One Euler--Maruyama step of GBM, S <- S (1 + d), and the payoff's running functionals of
+// the new value (on local scalars).
+template <typename R, int PAY, bool SPLIT>
+__device__ __forceinline__ void em_step(R &S, R &sum, R &hi, R &lo, R &lsum, R d)
+{
+    S = fma(S, d, S);
+    if constexpr (PAY == kAsian) sum += S;
+    if constexpr (PAY == kLookback) {
+        hi = fmax(hi, S);
+        if constexpr (SPLIT) lo = fmin(lo, S);
+    }
+    if constexpr (PAY == kGeoAsian) lsum += log(S);
+}
+
+// Discounted payoff of a path from its totals: final value Sn, sum of post-step values
+// `post` (i = 1..n), maximum over S_0..S_n, sum of log post-step values; n = steps.
+template <typename R, int PAY>
+__device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
+                                          const LevelParams &p)
+{
+    const R K = R(p.K), disc = R(p.disc), S0 = R(p.S0);
+    if constexpr (PAY == kEuropean) {
+        return disc * fmax(Sn - K, R(0));
+    } else if constexpr (PAY == kAsian) {
+        // (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 = (1/n) (sum_{i=1..n} S_i + (S_0 - S_n) / 2)
+        const R A = (post + R(0.5) * (S0 - Sn)) * inv_n;
+        return disc * fmax(A - K, R(0));
+    } else if constexpr (PAY == kLookback) {
+        return disc * fmax(hi - K, R(0));
+    } else if constexpr (PAY == kDigital) {
+        const R Q = R(p.Q);
+        return Sn > K ? disc * Q : (Sn == K ? R(0.5) * disc * Q : R(0));
+    } else if constexpr (PAY == kLinear) {
+        return Sn;
+    } else {  // kGeoAsian
+        const R lg = (lpost + R(0.5) * (PathAcc<R, PAY, false>::log_r(S0) -
+                                        PathAcc<R, PAY, false>::log_r(Sn))) * inv_n;
+        const R G = sizeof(R) == 4 ? R(expf(float(lg))) : R(exp(double(lg)));
+        return disc * fmax(G - K, R(0));
+    }
+}
+
+// Fine and coarse paths of one sample on a level with M^l >= 8 (one normal per fine step),
+// over the Philox calls [j0, j1) (4 fine steps per call).
+template <typename R, int MT, int PAY, bool SPLIT>
+__device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t slo, uint32_t shi,
+                                               int j0, int j1, PathAcc<R, PAY, SPLIT> &fa,
+                                               PathAcc<R, PAY, SPLIT> &ca)
+{
+    const R a = R(p.a), rh = R(p.rh);
+    R fS = fa.S, fsum = fa.sum, fhi = fa.hi, flo = fa.lo, fls = fa.lsum;
+    R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
+    R dc = R(0);
+    int q = 0;
+    const int M = MT ? MT : p.M;
+    for (int j = j0; j < j1; ++j) {
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
+        R rho, c, s;
+        R d[4];
+        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
+        R ra = rho * a;
+        d[0] = fma(ra, c, rh);
+        d[1] = fma(ra, s, rh);
+        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
+        ra = rho * a;
+        d[2] = fma(ra, c, rh);
+        d[3] = fma(ra, s, rh);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            em_step<R, PAY, SPLIT>(fS, fsum, fhi, flo, fls, d[k]);
+            dc += d[k];
+            if constexpr (MT != 0) {
+                if ((k + 1) % MT == 0) {
+                    em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dc);
+                    dc = R(0);
+                }
+            } else {
+                if (++q == M) {
+                    em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dc);
+                    dc = R(0);
+                    q = 0;
+                }
+            }
+        }
+    }
+    fa.S = fS; fa.sum = fsum; fa.hi = fhi; fa.lo = flo; fa.lsum = fls;
+    ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
+}
+
+// Levels with M^l < 8: the sample draws 8 normals (the T/8 grid) and fine step k sums the
+// 8 / M^l normals that fall inside it.
+template <typename R, int PAY>
+__device__ __forceinline__ void simulate_small(const LevelParams &p, uint32_t slo, uint32_t shi,
+                                               PathAcc<R, PAY, false> &fa,
+                                               PathAcc<R, PAY, false> &ca)
+{
+    const R a = R(p.a), rh = R(p.rh);
+    R z[8];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
+        R rho, c, s;
+        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
+        z[4 * j + 0] = rho * c;
+        z[4 * j + 1] = rho * s;
+        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
+        z[4 * j + 2] = rho * c;
+        z[4 * j + 3] = rho * s;
+    }
+    R fS = fa.S, fsum = fa.sum, fhi = fa.hi, flo = fa.lo, fls = fa.lsum;
+    R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
+    const int per_mask = 8 / p.nf - 1;  // 8 / M^l normals per fine step (a power of two)
+    const bool coupled = p.level > 0;
+    R zs = R(0), dc = R(0);
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        zs += z[i];
+        if (((i + 1) & per_mask) == 0) {
+            const R d = fma(a, zs, rh);
+            zs = R(0);
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d);
+            if (coupled) {
+                dc += d;
+                if (++q == p.M) {
+                    em_step<R, PAY, false>(cS, csum, chi, clo, cls, dc);
+                    dc = R(0);
+                    q = 0;
+                }
+            }
+        }
+    }
+    fa.S = fS; fa.sum = fsum; fa.hi = fhi; fa.lo = flo; fa.lsum = fls;
+    ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum four doubles over the block; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum4(double v[4])
+{
+    __shared__ double sm[32][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();  // sm may still be read by an earlier call
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sm[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = warp_sum(lane < nw ? sm[lane][k] : 0.0);
+    }
+}
+
+// Block partials -> workspace; the last block adds them in block order and writes p.out.
+__device__ __forceinline__ void finish_sums(double m[4], const LevelParams &p)
+{
+    __shared__ bool is_last;
+    block_sum4(m);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p.partials[4 * blockIdx.x + k] = m[k];
+        __threadfence();
+        const unsigned done = atomicAdd(p.ticket, 1u);
+        is_last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += __ldcg(p.partials + 4 * b + k);
+    }
+    block_sum4(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p.out[k] = acc[k];
+        *p.ticket = 0u;  // leave the workspace ready for the next launch
+    }
+}
+
+// Join the chunks of one sample split over P lanes: an exclusive product scan of the chunk
+// factors gives each chunk's starting value relative to S0; the path totals are then sums and
+// maxima over the lanes.  Every lane of the group receives the totals.
+template <typename R, int PAY>
+__device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int lig, int P, R S0,
+                                            R steps, R &total, R &post, R &hi, R &lpost)
+{
+    R incl = A.S;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (o < P) {
+            const R t = __shfl_up_sync(0xffffffffu, incl, o, P);
+            if (lig >= o) incl *= t;
+        }
+    }
+    R excl = __shfl_up_sync(0xffffffffu, incl, 1, P);
+    if (lig == 0) excl = R(1);
+    total = S0 * __shfl_sync(0xffffffffu, incl, P - 1, P);
+    const R start = S0 * excl;
+    R ps = start * A.sum;
+    R ph = start >= R(0) ? start * A.hi : start * A.lo;
+    R pl = R(0);
+    if constexpr (PAY == kGeoAsian) pl = steps * PathAcc<R, PAY, true>::log_r(start) + A.lsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (o < P) {
+            ps += __shfl_xor_sync(0xffffffffu, ps, o, P);
+            ph = fmax(ph, __shfl_xor_sync(0xffffffffu, ph, o, P));
+            if constexpr (PAY == kGeoAsian) pl += __shfl_xor_sync(0xffffffffu, pl, o, P);
+        }
+    }
+    post = ps;
+    hi = ph;
+    lpost = pl;
+}
+
+template <typename R, int MT, int PAY, bool SPLIT>
+__global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
+{
+    const int P = SPLIT ? p.lanes : 1;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / P;
+    const uint64_t g = tid / P;
+    const uint64_t g_warp = (tid & ~uint64_t(31)) / P;  // first group of this warp
+    const int lig = SPLIT ? (int)(threadIdx.x % P) : 0;
+    const R S0 = R(p.S0);
+    const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+
+    for (uint64_t base = 0; base + g_warp < p.N; base += groups) {
+        const uint64_t idx = base + g;
+        const bool valid = idx < p.N;
+        const uint64_t s = p.first + (valid ? idx : p.N - 1);
+        const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
+
+        // Paths run relative to S0 (start value 1) and are scaled once per sample: the running
+        // sums then hold values of order one, which keeps the FP32 sums of many steps accurate.
+        PathAcc<R, PAY, SPLIT> fa, ca;
+        fa.init(R(1));
+        ca.init(R(1));
+        R Y;
+        if constexpr (!SPLIT) {
+            if (p.small) {
+                simulate_small<R, PAY>(p, slo, shi, fa, ca);
+            } else {
+                simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
+            }
+            const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
+            const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
+                                              R(p.nf) * logS0 + fa.lsum, inv_nf, p);
+            const R Pc = p.level > 0
+                             ? payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
+                                                    R(p.nf / p.M) * logS0 + ca.lsum, inv_nc, p)
+                             : R(0);
+            Y = Pf - Pc;
+        } else {
+            const int calls = (p.nf >> 2) / P;
+            simulate_steps<R, MT, PAY, true>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+            const R steps_f = R(4 * calls);
+            R tf, pf, hf, lf, tc, pc, hc, lc;
+            join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
+            join_chunks<R, PAY>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
+            const R Pf = payoff_value<R, PAY>(tf, pf, hf, lf, inv_nf, p);
+            const R Pc = payoff_value<R, PAY>(tc, pc, hc, lc, inv_nc, p);
+            Y = Pf - Pc;
+        }
+        if (valid && lig == 0) {
+            const double y = (double)Y;
+            const double y2 = y * y;
+            m[0] += y;
+            m[1] += y2;
+            m[2] = fma(y2, y, m[2]);
+            m[3] = fma(y2, y2, m[3]);
+            if (p.y_out) p.y_out[idx] = y;
+        }
+    }
+    finish_sums(m, p);
+}
+
+}  // namespace mlmcgb
+
+namespace mlmcgb {
+
+// Kernel for (payoff, M specialisation, split) at precision R; nullptr for an unknown payoff.
+template <typename R, int MT, bool SPLIT> const void *select_by_payoff(int payoff)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, SPLIT>;
+    case kAsian: return (const void *)level_kernel<R, MT, kAsian, SPLIT>;
+    case kLookback: return (const void *)level_kernel<R, MT, kLookback, SPLIT>;
+    case kDigital: return (const void *)level_kernel<R, MT, kDigital, SPLIT>;
+    case kLinear: return (const void *)level_kernel<R, MT, kLinear, SPLIT>;
+    case kGeoAsian: return (const void *)level_kernel<R, MT, kGeoAsian, SPLIT>;
+    default: return nullptr;
+    }
+}
+
+template <typename R> const void *select_level_kernel(int payoff, int mt, bool split)
+{
+    if (mt == 4) return split ? select_by_payoff<R, 4, true>(payoff) : select_by_payoff<R, 4, false>(payoff);
+    return split ? select_by_payoff<R, 0, true>(payoff) : select_by_payoff<R, 0, false>(payoff);
+}
+
+}  // namespace mlmcgb

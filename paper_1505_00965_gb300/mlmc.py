@@ -1,0 +1,232 @@
+"""Python binding of the GB300 multilevel Monte Carlo level engine (include/mlmc.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library
+``libmlmc_gb300.so`` built from ``csrc/`` for sm_103a.  The functions keep the C names; they
+raise ``MLMCError`` for a non-zero status and return the outputs.  Importing this package
+fails loudly if the library has not been built; there is no CPU fallback.
+
+Device buffers and streams for the ``_async`` entry point come from PyTorch (any object with
+``data_ptr()``, or a raw integer address; a ``torch.cuda.Stream`` or a raw handle).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmlmc_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first (python -m paper_1505_00965_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ETIMEOUT, MLMC_ENOTIMPL = range(7)
+MLMC_MODEL_GBM = 0
+PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "linear": 100, "geo_asian": 101}
+MLMC_FP64, MLMC_FP32_PATH = 0, 1
+PRECISIONS = {"fp64": MLMC_FP64, "fp32": MLMC_FP32_PATH}
+MLMC_TAG_PATHS, MLMC_TAG_CV_MEAN, MLMC_TAG_CV_TRAIN = 0, 1, 2
+MLMC_MAX_LEVELS = 16
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mlmc status {status}: {message}")
+        self.status = status
+
+
+class mlmc_model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("S0", ctypes.c_double),
+                ("r", ctypes.c_double), ("sigma", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+class mlmc_payoff(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("K", ctypes.c_double),
+                ("cash", ctypes.c_double)]
+
+
+class mlmc_launch(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("lanes_per_path", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class mlmc_result(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_double), ("eps", ctypes.c_double), ("L", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("N", ctypes.c_uint64 * MLMC_MAX_LEVELS),
+                ("sums", (ctypes.c_double * 4) * MLMC_MAX_LEVELS),
+                ("mean", ctypes.c_double * MLMC_MAX_LEVELS), ("var", ctypes.c_double * MLMC_MAX_LEVELS),
+                ("cost", ctypes.c_double * MLMC_MAX_LEVELS), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("total_cost", ctypes.c_double), ("path_steps", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+
+_u64, _i32, _dbl, _vp, _sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_dptr = ctypes.POINTER(ctypes.c_double)
+_pm, _pp, _pl = ctypes.POINTER(mlmc_model), ctypes.POINTER(mlmc_payoff), ctypes.POINTER(mlmc_launch)
+
+_SIGNATURES = {
+    "mlmc_last_error": ([], ctypes.c_char_p),
+    "mlmc_version": ([], ctypes.c_char_p),
+    "mlmc_device_sm_count": ([], _i32),
+    "mlmc_shutdown": ([], _i32),
+    "mlmc_level_sums": ([_i32, _i32, _u64, _pm, _pp, _u64, _dptr, _dptr], _i32),
+    "mlmc_level_sums_ex": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _dptr, _dptr], _i32),
+    "mlmc_level_workspace_bytes": ([_i32, _i32, _u64, _i32, _pl], _sz),
+    "mlmc_level_sums_async": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _sz, _vp, _vp],
+                              _i32),
+    "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
+}
+for _name, (_args, _res) in _SIGNATURES.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _check(status: int) -> None:
+    if status != MLMC_OK:
+        raise MLMCError(status, mlmc_last_error())
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "cuda_stream"):
+        return x.cuda_stream
+    raise TypeError(f"cannot take a device address of {type(x)!r}")
+
+
+@dataclass(frozen=True)
+class Problem:
+    """GBM dS = r S dt + sigma S dW and a discounted payoff (the C structs in Python form)."""
+
+    S0: float = 100.0
+    r: float = 0.05
+    sigma: float = 0.2
+    T: float = 1.0
+    payoff: str = "european"
+    K: float = 100.0
+    cash: float = 1.0
+
+    def model(self) -> mlmc_model:
+        return mlmc_model(MLMC_MODEL_GBM, 0, self.S0, self.r, self.sigma, self.T)
+
+    def payoff_struct(self) -> mlmc_payoff:
+        return mlmc_payoff(PAYOFFS[self.payoff], 0, self.K, self.cash)
+
+
+def _launch(launch) -> mlmc_launch | None:
+    if launch is None:
+        return None
+    if isinstance(launch, mlmc_launch):
+        return launch
+    return mlmc_launch(int(launch.get("threads_per_block", 0)), int(launch.get("lanes_per_path", 0)),
+                       int(launch.get("blocks", 0)), 0)
+
+
+def _prec(precision) -> int:
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def mlmc_last_error() -> str:
+    return (_lib.mlmc_last_error() or b"").decode()
+
+
+def mlmc_version() -> str:
+    return _lib.mlmc_version().decode()
+
+
+def mlmc_device_sm_count() -> int:
+    n = _lib.mlmc_device_sm_count()
+    if n < 0:
+        raise MLMCError(MLMC_ECUDA, mlmc_last_error())
+    return n
+
+
+def mlmc_shutdown() -> None:
+    _check(_lib.mlmc_shutdown())
+
+
+def mlmc_level_sums(level: int, M: int, N: int, problem: Problem, seed: int):
+    """(sums[4], cost): FP32 paths, samples [0, N), default stream."""
+    sums = (ctypes.c_double * 4)()
+    cost = ctypes.c_double()
+    m, p = problem.model(), problem.payoff_struct()
+    _check(_lib.mlmc_level_sums(level, M, N, ctypes.byref(m), ctypes.byref(p), seed, sums, ctypes.byref(cost)))
+    return list(sums), cost.value
+
+
+def mlmc_level_sums_ex(level: int, M: int, N: int, first: int, problem: Problem, seed: int,
+                       precision="fp32", tag: int = MLMC_TAG_PATHS, launch=None, stream=None):
+    """(sums[4], cost) over samples [first, first + N); synchronises `stream`."""
+    sums = (ctypes.c_double * 4)()
+    cost = ctypes.c_double()
+    m, p, ln = problem.model(), problem.payoff_struct(), _launch(launch)
+    _check(_lib.mlmc_level_sums_ex(level, M, N, first, ctypes.byref(m), ctypes.byref(p), seed, _prec(precision),
+                                   tag, ctypes.byref(ln) if ln is not None else None, _addr(stream), sums,
+                                   ctypes.byref(cost)))
+    return list(sums), cost.value
+
+
+def mlmc_level_workspace_bytes(level: int, M: int, N: int, precision="fp32", launch=None) -> int:
+    ln = _launch(launch)
+    n = _lib.mlmc_level_workspace_bytes(level, M, N, _prec(precision), ctypes.byref(ln) if ln is not None else None)
+    if n == 0:
+        raise MLMCError(MLMC_EINVAL, mlmc_last_error())
+    return n
+
+
+def mlmc_level_sums_async(level: int, M: int, N: int, first: int, problem: Problem, seed: int, d_sums,
+                          d_workspace, workspace_bytes: int, precision="fp32", tag: int = MLMC_TAG_PATHS,
+                          launch=None, d_y=None, stream=None) -> None:
+    """Queue the level on `stream`; d_sums (4 doubles), d_workspace and d_y are device buffers."""
+    m, p, ln = problem.model(), problem.payoff_struct(), _launch(launch)
+    _check(_lib.mlmc_level_sums_async(level, M, N, first, ctypes.byref(m), ctypes.byref(p), seed, _prec(precision),
+                                      tag, ctypes.byref(ln) if ln is not None else None, _addr(d_sums),
+                                      _addr(d_workspace), workspace_bytes, _addr(d_y), _addr(stream)))
+
+
+@dataclass
+class Estimate:
+    status: int
+    P: float
+    eps: float
+    L: int
+    converged: bool
+    rounds: int
+    N: list = field(default_factory=list)
+    sums: list = field(default_factory=list)
+    mean: list = field(default_factory=list)
+    var: list = field(default_factory=list)
+    cost: list = field(default_factory=list)
+    alpha: float = 0.0
+    beta: float = 0.0
+    total_cost: float = 0.0
+    path_steps: float = 0.0
+    kernel_ms: float = 0.0
+    wall_ms: float = 0.0
+
+
+def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int = 2, Lmax: int = 8,
+                  N0: int = 10_000, precision="fp32", stream=None) -> Estimate:
+    """Adaptive estimate to RMS accuracy eps.  Returns the estimate also when Lmax was reached
+    before the bias test passed (status MLMC_ENOTCONV, converged False)."""
+    r = mlmc_result()
+    m, p = problem.model(), problem.payoff_struct()
+    st = _lib.mlmc_estimate(eps, M, Lmin, Lmax, N0, ctypes.byref(m), ctypes.byref(p), seed, _prec(precision),
+                            _addr(stream), ctypes.byref(r))
+    if st not in (MLMC_OK, MLMC_ENOTCONV):
+        _check(st)
+    L = r.L
+    return Estimate(status=st, P=r.P, eps=r.eps, L=L, converged=bool(r.converged), rounds=r.rounds,
+                    N=[int(r.N[l]) for l in range(L + 1)], sums=[list(r.sums[l]) for l in range(L + 1)],
+                    mean=[r.mean[l] for l in range(L + 1)], var=[r.var[l] for l in range(L + 1)],
+                    cost=[r.cost[l] for l in range(L + 1)], alpha=r.alpha, beta=r.beta, total_cost=r.total_cost,
+                    path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms)

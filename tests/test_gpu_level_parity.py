@@ -1,0 +1,181 @@
+"""Parity of the CUDA level kernels with the FP64 CPU oracle on the identical random stream.
+
+Both sides draw the same Philox4x32-10 words for every sample (the stream of include/mlmc.h),
+so every sample's Y = P_l - P_{l-1} (Sec. 5, Eq. Yldef) is compared one by one, and the four
+moment sums after them.
+
+Tolerances (written from the arithmetic, u = unit roundoff of the path precision):
+  * level means: |m_gpu - m_oracle| <= rtol * max(|m|, sbar) with rtol = 1e-12 (FP64 paths) and
+    1e-5 (FP32 paths), the per-level mean tolerances set for this engine; sbar, the mean
+    |P_l| of the level's fine payoffs, is the price scale the level means add up to.
+  * per sample: each Euler--Maruyama step rounds once (relative u), the n = M^l roundings of a
+    path add up like a random walk, and the normals carry the error of the logarithm, square
+    root, sine and cosine (below 1e-15 in FP64; below 2e-6 for the FP32 hardware
+    approximations).  |Y_gpu - Y_oracle| <= 8 (u sqrt(n + 1) + e_z) S0 e^{rT}.
+  * higher moments follow from the per-sample bound: |d sum Y^k| <= k sum |Y|^{k-1} * bound.
+  * digital payoff in FP32: a sample whose final value lies within the per-sample bound of K may
+    land on the other side of K; such flips are listed, each is checked to lie within the bound,
+    and the means are compared over the remaining samples.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+from gpu_helpers import moment_sums, oracle_problem, run_level
+
+pytestmark = pytest.mark.gpu
+
+GBM = dict(S0=100.0, r=0.05, sigma=0.2, T=1.0, K=100.0, cash=1.0)
+U = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
+EZ = {"fp64": 1e-15, "fp32": 2e-6}
+RTOL_MEAN = {"fp64": 1e-12, "fp32": 1e-5}
+PAYOFFS = ["european", "asian", "lookback", "digital", "linear", "geo_asian"]
+# (level, N, first): several blocks and a ragged tail on every level, sized for the oracle
+LEVELS_M4 = [(0, 20011, 0), (1, 20011, 977), (2, 8191, 5), (3, 4001, 123456789), (4, 3001, 7),
+             (5, 1201, 2 ** 33 + 3), (6, 601, 11), (7, 257, 0)]
+
+
+@pytest.fixture(scope="module")
+def mlmc():
+    from paper_1505_00965_gb300 import build
+
+    build.build()
+    from paper_1505_00965_gb300 import mlmc as binding
+
+    return binding
+
+
+def _bound(precision, level, M, p):
+    n = M ** level
+    return 8.0 * (U[precision] * math.sqrt(n + 1) + EZ[precision]) * p.S0 * math.exp(p.r * p.T)
+
+
+def _check_level(mlmc, level, M, N, first, payoff, precision, launch=None, seed=20240601):
+    p = mlmc.Problem(payoff=payoff, **GBM)
+    op = oracle_problem(oracle, p)
+    sums, y = run_level(mlmc, level, M, N, first, p, seed, precision, launch=launch)
+    yo = oracle.level_samples(level, M, N, op, seed=seed, first=first, stream=precision)
+    fine = oracle.level_samples(level, M, N, op, seed=seed, first=first, stream=precision,
+                                mode=oracle.MODE_FINE_ONLY)
+    sbar = max(np.mean(np.abs(fine)), 1e-300)
+    bound = _bound(precision, level, M, p)
+    diff = np.abs(y - yo)
+    keep = np.ones(N, dtype=bool)
+    if payoff == "digital" and precision == "fp32":
+        flips = np.nonzero(diff > 0.25 * p.cash)[0]
+        for i in flips:
+            _, fpath, cpath = oracle.sample_paths(level, M, first + int(i), op, seed=seed, stream=precision)
+            near = abs(fpath[-1] - p.K) <= bound or (cpath is not None and abs(cpath[-1] - p.K) <= bound)
+            assert near, f"digital flip at sample {first + i} with S_n far from K"
+        keep[flips] = False
+        assert len(flips) <= max(2, N // 1000)
+    assert np.all(np.isfinite(y))
+    worst = float(diff[keep].max()) if keep.any() else 0.0
+    assert worst <= bound, f"{payoff} {precision} l={level}: max |dY| = {worst:.3e} > {bound:.3e}"
+    # the device's four sums against the same sums of the device's own Y (reduction check)
+    own = moment_sums(y)
+    absy = np.abs(y)
+    for k in range(4):
+        scale = np.sum(absy ** (k + 1)) + 1e-300
+        assert abs(sums[k] - own[k]) <= 1e-12 * scale, (k, sums[k], own[k])
+    # level mean and higher moments against the oracle
+    m_gpu, m_orc = np.mean(y[keep]), np.mean(yo[keep])
+    tol = RTOL_MEAN[precision] * max(abs(m_orc), sbar)
+    assert abs(m_gpu - m_orc) <= tol, f"mean {m_gpu!r} vs {m_orc!r} (tol {tol:.3e})"
+    ref = moment_sums(yo[keep])
+    got = moment_sums(y[keep])
+    for k in range(1, 4):
+        allowed = (k + 1) * np.sum(np.abs(yo[keep]) ** k) * bound + 1e-13 * abs(ref[k])
+        assert abs(got[k] - ref[k]) <= allowed, (k, got[k], ref[k], allowed)
+    return worst / bound
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("payoff", PAYOFFS)
+@pytest.mark.parametrize("level,N,first", LEVELS_M4)
+def test_level_matches_oracle_M4(mlmc, level, N, first, payoff, precision):
+    _check_level(mlmc, level, 4, N, first, payoff, precision, launch={"lanes_per_path": 1})
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("payoff", ["european", "asian", "lookback", "geo_asian"])
+@pytest.mark.parametrize("level,N,lanes", [(3, 1001, 4), (4, 1001, 8), (5, 601, 32), (6, 301, 16), (7, 129, 32)])
+def test_split_lanes_match_oracle(mlmc, level, N, lanes, payoff, precision):
+    """Time-parallel form: lanes of a warp split each path and join by a product scan."""
+    _check_level(mlmc, level, 4, N, 31, payoff, precision, launch={"lanes_per_path": lanes, "threads_per_block": 128})
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("M,level,N,lanes", [(2, 1, 5001, 1), (2, 2, 5001, 1), (2, 3, 3001, 1), (2, 7, 999, 1),
+                                             (2, 9, 301, 16), (8, 0, 4001, 1), (8, 1, 4001, 1), (8, 2, 2001, 1),
+                                             (8, 4, 301, 1), (8, 4, 301, 32)])
+@pytest.mark.parametrize("payoff", ["asian", "lookback", "linear"])
+def test_other_refinement_factors(mlmc, M, level, N, lanes, payoff, precision):
+    """Eq. (mlmc:Dtl) with M = 2 (the paper's example) and M = 8."""
+    _check_level(mlmc, level, M, N, 3, payoff, precision, launch={"lanes_per_path": lanes})
+
+
+@pytest.mark.parametrize("threads,blocks", [(32, 1), (64, 3), (1024, 0), (256, 7)])
+def test_launch_shapes_agree(mlmc, threads, blocks):
+    """Grid-stride loops and the two-stage reduction: any launch shape gives the same samples
+    and sums equal to the sums of its own samples."""
+    p = mlmc.Problem(payoff="asian", **GBM)
+    ref_sums, ref_y = run_level(mlmc, 3, 4, 5003, 0, p, 9, "fp32")
+    sums, y = run_level(mlmc, 3, 4, 5003, 0, p, 9, "fp32", launch={"threads_per_block": threads, "blocks": blocks})
+    assert np.array_equal(y, ref_y)
+    np.testing.assert_allclose(sums, ref_sums, rtol=1e-13)
+
+
+def test_zero_samples_and_repeat_launches(mlmc):
+    p = mlmc.Problem(payoff="european", **GBM)
+    sums, _ = run_level(mlmc, 2, 4, 0, 0, p, 1, "fp32")
+    assert list(sums) == [0, 0, 0, 0]
+    a, ya = run_level(mlmc, 2, 4, 1000, 0, p, 1, "fp32")
+    b, yb = run_level(mlmc, 2, 4, 1000, 0, p, 1, "fp32")
+    assert np.array_equal(a, b) and np.array_equal(ya, yb)
+
+
+def test_host_entry_points_agree_with_async(mlmc):
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    sums_a, y = run_level(mlmc, 4, 4, 3000, 0, p, 1, "fp32")
+    sums_b, cost = mlmc.mlmc_level_sums(4, 4, 3000, p, 1)
+    np.testing.assert_allclose(sums_b, sums_a, rtol=1e-12)
+    assert cost == 3000 * (256 + 64)
+    sums_c, _ = mlmc.mlmc_level_sums_ex(4, 4, 3000, 0, p, 1, precision="fp32")
+    np.testing.assert_allclose(sums_c, sums_a, rtol=1e-12)
+
+
+def test_resume_offsets_compose(mlmc):
+    """Samples are addressed by index: [0, N) = [0, a) + [a, N) sample by sample (Sec. 5's
+    fresh samples per round come from advancing `first`)."""
+    p = mlmc.Problem(payoff="asian", **GBM)
+    _, y = run_level(mlmc, 5, 4, 900, 0, p, 4, "fp64")
+    _, y1 = run_level(mlmc, 5, 4, 400, 0, p, 4, "fp64")
+    _, y2 = run_level(mlmc, 5, 4, 500, 400, p, 4, "fp64")
+    assert np.array_equal(y, np.concatenate([y1, y2]))
+
+
+def test_config_plain_fp64_european_full(mlmc):
+    """Plain MLMC in FP64: European call, M = 4, levels 0..4, N_l = 10^4, seed 1 -- the whole
+    workload against the oracle, and the telescoped sum against Black--Scholes (10.4506)."""
+    from closed_forms import black_scholes_call
+
+    p = mlmc.Problem(payoff="european", **GBM)
+    op = oracle_problem(oracle, p)
+    total, var = 0.0, 0.0
+    for level in range(5):
+        sums, cost = mlmc.mlmc_level_sums_ex(level, 4, 10_000, 0, p, 1, precision="fp64")
+        ref, ref_cost = oracle.level_sums(level, 4, 10_000, op, seed=1, stream="fp64")
+        assert cost == ref_cost
+        fine = oracle.level_samples(level, 4, 2000, op, seed=1, stream="fp64", mode=oracle.MODE_FINE_ONLY)
+        sbar = np.mean(np.abs(fine))
+        assert abs(sums[0] - ref[0]) / 1e4 <= 1e-12 * max(abs(ref[0]) / 1e4, sbar)
+        np.testing.assert_allclose(sums[1], ref[1], rtol=1e-11)
+        m = sums[0] / 1e4
+        total += m
+        var += (sums[1] / 1e4 - m * m) / 1e4
+    bs = black_scholes_call(100, 100, 0.05, 0.2, 1.0)
+    assert abs(total - bs) < 4 * math.sqrt(var) + 0.02
