@@ -28,10 +28,13 @@
  *     u = 1 - (x mod 2^23) 2^-23 (the low 23 bits, exactly a float mantissa).  Both lie in
  *     (0, 1], so log(u) is finite.
  *   - Box--Muller: rho = sqrt(-2 log u1), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
- *   - Each sample draws G = max(M^l, 8) normals; fine step k takes the G / M^l consecutive
- *     normals starting at k G / M^l, dW = sqrt(T / G) * (their sum).  This keeps the Brownian
- *     path on the T/8 grid available at every level (the learned control variate's inputs) and
- *     leaves every fine increment exactly N(0, dt_l).
+ *   - Fine step k of sample s (k < M^l) takes normal k of the sample: dW_k = sqrt(dt_l) z_k.
+ *     A level-0 sample therefore uses one normal.
+ *   - The Brownian path on the T/8 grid (the learned control variate's inputs) is the running
+ *     sum of the fine increments when M^l >= 8.  On coarser levels it is refined from the
+ *     fine-grid values by Brownian-bridge midpoints, stage by stage and left to right; stage
+ *     midpoints take the normals that follow the path's own Philox blocks (starting at normal
+ *     4 ceil(M^l / 4)).  The fine path never depends on whether the grid is built.
  *   - Arithmetic Asian: trapezoid average (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 on each path's own
  *     grid.  Lookback: fixed strike, max over the grid points S_0..S_n.  Both discounted.
  *   - Cost of one level-l sample: C_0 = 1, C_l = M^l + M^{l-1} Euler--Maruyama steps.
@@ -103,11 +106,11 @@ void oracle_normals(uint64_t seed, int level, int tag, uint64_t s, int stream, i
 
 static long ipow(long b, int e) { long p = 1; while (e-- > 0) p *= b; return p; }
 
-/* Normals drawn per sample at level l: G = max(M^l, 8). */
+/* Normals a level-l sample's path uses: one per fine step, rounded up to whole Philox blocks. */
 long oracle_normals_per_sample(int level, int M)
 {
     long nf = ipow(M, level);
-    return nf > 8 ? nf : 8;
+    return (nf + 3) / 4 * 4;
 }
 
 /* Euler--Maruyama for GBM over n steps of size h driven by the given increments (Eq. em). */
@@ -177,16 +180,11 @@ int oracle_sample_paths(int level, int M, uint64_t s, int tag, const oracle_prob
 {
     long nf = ipow(M, level);
     long G = oracle_normals_per_sample(level, M);
-    long per = G / nf;
     double *z = (double *)malloc(sizeof(double) * (size_t)G);
     oracle_normals(seed, level, tag, s, stream, (int)G, z);
-    double sqrt_dt_grid = sqrt(p->T / (double)G);
-    for (long k = 0; k < nf; ++k) {
-        double acc = 0.0;
-        for (long q = 0; q < per; ++q)
-            acc += z[k * per + q];
-        dWf[k] = sqrt_dt_grid * acc;
-    }
+    double sqrt_h = sqrt(p->T / (double)nf);
+    for (long k = 0; k < nf; ++k)
+        dWf[k] = sqrt_h * z[k];
     free(z);
     double hf = p->T / (double)nf;
     oracle_em_path((int)nf, p->S0, p->r, p->sigma, hf, dWf, fine);
@@ -209,16 +207,40 @@ int oracle_sample_paths(int level, int M, uint64_t s, int tag, const oracle_prob
 void oracle_grid_brownian(int level, int M, uint64_t s, int tag, double T, uint64_t seed,
                           int stream, double W8[8])
 {
+    long nf = ipow(M, level);
     long G = oracle_normals_per_sample(level, M);
-    double *z = (double *)malloc(sizeof(double) * (size_t)G);
-    oracle_normals(seed, level, tag, s, stream, (int)G, z);
-    double sqrt_dt_grid = sqrt(T / (double)G);
-    long per8 = G / 8;
-    double W = 0.0;
-    for (int k = 0; k < 8; ++k) {
-        for (long q = 0; q < per8; ++q)
-            W += sqrt_dt_grid * z[k * per8 + q];
-        W8[k] = W;
+    double *z = (double *)malloc(sizeof(double) * (size_t)(G + 8));
+    oracle_normals(seed, level, tag, s, stream, (int)(G + 8), z);
+    double sqrt_h = sqrt(T / (double)nf);
+    if (nf >= 8) {
+        long per8 = nf / 8;
+        double W = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            for (long q = 0; q < per8; ++q)
+                W += sqrt_h * z[k * per8 + q];
+            W8[k] = W;
+        }
+    } else {
+        /* grid[i] = W(i T / 8), i = 0..8; known at multiples of 8 / nf, then bridged */
+        double grid[9];
+        long step = 8 / nf;
+        double W = 0.0;
+        grid[0] = 0.0;
+        for (long k = 0; k < nf; ++k) {
+            W += sqrt_h * z[k];
+            grid[(k + 1) * step] = W;
+        }
+        long next = G;  /* first bridge normal */
+        for (long width = step; width > 1; width /= 2) {
+            double dt_half = T / 8.0 * (double)(width / 2);
+            for (long left = 0; left < 8; left += width) {
+                long mid = left + width / 2;
+                grid[mid] = 0.5 * (grid[left] + grid[left + width]) +
+                            sqrt(dt_half / 2.0) * z[next++];
+            }
+        }
+        for (int k = 0; k < 8; ++k)
+            W8[k] = grid[k + 1];
     }
     free(z);
 }

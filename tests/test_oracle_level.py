@@ -42,9 +42,9 @@ def test_level0_is_single_step_of_size_T():
     dW, fine, coarse = oracle.sample_paths(0, 4, 17, p, seed=5)
     assert coarse is None and len(fine) == 2 and len(dW) == 1
     assert fine[1] == pytest.approx(100 * (1 + 0.05 * 1.0 + 0.2 * dW[0]), rel=1e-15)
-    # and dW is sqrt(T/8) times the sum of the sample's first 8 normals
-    z = oracle.normals(5, 0, 17, 8)
-    assert dW[0] == pytest.approx(math.sqrt(1 / 8) * z.sum(), rel=1e-14)
+    # and dW is sqrt(T) times the sample's first normal
+    z = oracle.normals(5, 0, 17, 4)
+    assert dW[0] == math.sqrt(1.0) * z[0]
     Y = oracle.level_samples(0, 4, 1, p, seed=5, first=17)
     assert Y[0] == fine[1]
 
@@ -74,17 +74,40 @@ def test_coarse_path_is_em_driven_by_summed_fine_increments(M, level):
         assert coarse[-1] == X
 
 
-def test_fine_increments_are_grouped_stream_normals():
-    """Fine step k takes the normals [k G / n, (k + 1) G / n) of the sample, scaled by sqrt(T/G)."""
+def test_fine_increments_are_stream_normals():
+    """Fine step k takes normal k of the sample, scaled by sqrt(h)."""
     p = Problem(payoff="european", **GBM)
-    for level, M in [(1, 4), (2, 4), (3, 4), (1, 2), (4, 2)]:
+    for level, M in [(0, 4), (1, 4), (2, 4), (3, 4), (1, 2), (4, 2), (1, 8)]:
         n = M ** level
-        G = oracle.normals_per_sample(level, M)
-        z = oracle.normals(42, level, 7, G)
+        z = oracle.normals(42, level, 7, n)
         dW, _, _ = oracle.sample_paths(level, M, 7, p, seed=42)
-        per = G // n
-        want = [math.sqrt(p.T / G) * sum(z[k * per:(k + 1) * per]) for k in range(n)]
-        np.testing.assert_allclose(dW, want, rtol=1e-14, atol=1e-15)
+        np.testing.assert_array_equal(dW, math.sqrt(p.T / n) * z)
+
+
+@pytest.mark.parametrize("M,level", [(4, 0), (4, 1), (4, 2), (4, 3), (2, 1), (2, 2), (8, 1)])
+def test_grid_brownian_law(M, level):
+    """The T/8 grid values are a Brownian path: Cov(W(s), W(t)) = min(s, t), on the levels whose
+    grid is the fine path and on those refined by Brownian-bridge midpoints; W(T) and the grid
+    points the level's own grid contains equal the running sums of its fine increments."""
+    T = 1.0
+    n = 20000
+    W = np.array([oracle.grid_brownian(level, M, s, T, seed=13) for s in range(n)])
+    t = (np.arange(8) + 1) * T / 8
+    cov = np.cov(W.T, bias=True)
+    want = np.minimum.outer(t, t)
+    assert np.max(np.abs(cov - want)) < 5 * math.sqrt(2.0 / n) * T
+    assert np.max(np.abs(W.mean(axis=0))) < 5 * math.sqrt(T / n)
+    p = Problem(payoff="european", T=T, **{k: v for k, v in GBM.items() if k != "T"})
+    nf = M ** level
+    for s in range(5):
+        dW, _, _ = oracle.sample_paths(level, M, s, p, seed=13)
+        Wg = oracle.grid_brownian(level, M, s, T, seed=13)
+        cum = np.cumsum(dW)
+        for k in range(nf):
+            idx = (k + 1) * 8 // nf - 1 if nf <= 8 else None
+            if idx is not None:
+                assert Wg[idx] == pytest.approx(cum[k], rel=1e-13, abs=1e-14)
+        assert Wg[7] == pytest.approx(cum[-1], rel=1e-12, abs=1e-14)
 
 
 def test_payoffs_hand_evaluated():

@@ -76,7 +76,7 @@ def test_normals_independent_across_levels_tags_and_slots():
 
 
 def test_normals_per_sample_rule():
-    """G = max(M^l, 8): the T/8 grid exists at every level."""
-    assert [oracle.normals_per_sample(l, 4) for l in range(4)] == [8, 8, 16, 64]
-    assert [oracle.normals_per_sample(l, 2) for l in range(5)] == [8, 8, 8, 8, 16]
-    assert [oracle.normals_per_sample(l, 8) for l in range(3)] == [8, 8, 64]
+    """One normal per fine step, rounded up to whole Philox blocks of four."""
+    assert [oracle.normals_per_sample(l, 4) for l in range(4)] == [4, 4, 16, 64]
+    assert [oracle.normals_per_sample(l, 2) for l in range(5)] == [4, 4, 4, 8, 16]
+    assert [oracle.normals_per_sample(l, 8) for l in range(3)] == [4, 8, 64]
