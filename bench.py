@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark: adaptive multilevel Monte Carlo on GB300, one JSON line on rank 0.
+
+Workload (one step): adaptive MLMC estimates to root-mean-square accuracy eps = 1e-3 of the
+arithmetic-Asian call and the fixed-strike lookback call on GBM (S0 = K = 100, r = 0.05,
+sigma = 0.2, T = 1), M = 4, levels up to 8, 10^4 warm-up samples per level, FP32 paths with
+FP64 moment sums, seeds 1..8 (rank r takes seeds 8r+1..8r+8: per-GPU work is fixed).
+
+  value  coupled path-steps/s of the whole step (sum over estimates of sum_l N_l M^l), timed
+         with CUDA events on the stream the engine runs on
+  e2e    the same metric through the public C ABI (mlmc_estimate: host arguments, host result,
+         the per-round device-to-host copies inside) timed by the host clock
+
+`--impl reference` times the FP64 CPU oracle instead (a bounded sample of the workload on the
+host cores).  Under torchrun only rank 0 runs that arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLMC time-to-ε (ε=1e-3) & coupled path-steps/s vs plain FP64 GPU MLMC"
+UNIT = "coupled path-steps/s"
+GBM = dict(S0=100.0, r=0.05, sigma=0.2, T=1.0, K=100.0)
+PAYOFFS = ("asian", "lookback")
+M, LMIN, LMAX, N0, EPS = 4, 2, 8, 10_000, 1e-3
+SEEDS_PER_RANK = 8
+WORKLOAD = ("adaptive MLMC to eps=1e-3: arithmetic-Asian and fixed-strike lookback calls, GBM S0=K=100 "
+            "r=0.05 sigma=0.2 T=1, M=4, L<=8, N0=1e4, FP32 paths + FP64 sums, seeds 1..8 per GPU")
+# GB300 issue limit: 4 schedulers per SM, each issuing one warp instruction (32 lanes) per clock.
+SCHEDULERS_PER_SM, WARP = 4, 32
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+# ------------------------------------------------------------------ helpers (CPU-testable)
+
+def rank_seeds(rank: int, n: int = SEEDS_PER_RANK) -> list[int]:
+    """Seeds of one rank: ranks draw disjoint seeds, so the estimates are independent."""
+    return [rank * n + i + 1 for i in range(n)]
+
+
+def level_instructions(level: int, m: int, payoff: str) -> float:
+    """Algorithmic instructions of one FP32 sample on level l:
+    Philox4x32-10 = 40 per block (10 rounds of 2 widening multiplies + 2 three-input xors);
+    Box--Muller = 7 ALU + 4 MUFU per pair; per fine step 2 (increment, step) + 1 (coarse sum);
+    per coarse step 1; running payoff functional 1 per fine and per coarse step (Asian,
+    lookback); per sample 11 (payoffs, difference, moment updates)."""
+    nf = m ** level
+    blocks = -(-nf // 4)
+    pairs = max(1, nf // 2)
+    per_fine = 2 + (1 if level > 0 else 0) + (1 if payoff in ("asian", "lookback") else 0)
+    coarse = (nf // m) * (1 + (1 if payoff in ("asian", "lookback") else 0)) if level > 0 else 0
+    return 40.0 * blocks + 11.0 * pairs + per_fine * nf + coarse + 11.0
+
+
+def estimate_instructions(N: list[int], m: int, payoff: str) -> float:
+    return sum(n * level_instructions(l, m, payoff) for l, n in enumerate(N))
+
+
+def parse_clock_lines(lines: list[str]) -> dict:
+    """Median SM clock, max clock and the throttle reasons seen, from nvidia-smi CSV lines of
+    index, clocks.sm, clocks.max.sm, power.draw, active, hw_slowdown, hw_thermal, sw_thermal,
+    sw_power_cap."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, val in zip(names, f[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def combine_over_ranks(dev_s: float, wall_s: float, steps: float, launches: float, group=None) -> tuple:
+    """Max of the times and sum of the work over ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if group is None and not (dist.is_available() and dist.is_initialized()):
+        return dev_s, wall_s, steps, launches
+    t = torch.tensor([dev_s, wall_s], dtype=torch.float64)
+    w = torch.tensor([steps, launches], dtype=torch.float64)
+    if dist.get_backend(group) == "nccl":
+        t, w = t.cuda(), w.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM, group=group)
+    return float(t[0]), float(t[1]), float(w[0]), float(w[1])
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def _oracle_job(args):
+    payoff, seed, eps = args
+    sys.path.insert(0, ROOT)
+    from oracle import Problem, driver
+
+    t = time.perf_counter()
+    e = driver.estimate(eps, Problem(payoff=payoff, Q=1.0, **GBM), seed, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0,
+                        stream="fp32")
+    dt = time.perf_counter() - t
+    return sum(n * M ** l for l, n in enumerate(e.N)), dt
+
+
+ORACLE_SAMPLE = dict(eps=2e-2, seeds=(1, 2, 3, 4))
+ORACLE_SAMPLE_TEXT = ("oracle adaptive MLMC of the same two options and model at eps=2e-2 (not 1e-3), "
+                      "seeds 1..4, FP32 stream; estimates run in parallel processes")
+
+
+def run_oracle_sample(pool_size: int) -> tuple[float, float, int]:
+    """(path-steps, wall seconds, processes) of the bounded oracle sample."""
+    import multiprocessing as mp
+
+    jobs = [(p, s, ORACLE_SAMPLE["eps"]) for p in PAYOFFS for s in ORACLE_SAMPLE["seeds"]]
+    procs = max(1, min(pool_size, len(jobs)))
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_job, jobs)
+    wall = time.perf_counter() - t
+    return float(sum(r[0] for r in res)), wall, procs
+
+
+def cpu_baseline(pool_size: int) -> dict:
+    steps, wall, procs = run_oracle_sample(pool_size)
+    return {"value": steps / wall, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT,
+            "wall_s": round(wall, 3)}
+
+
+def reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    pool = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle_sample(pool)
+    tot_steps, tot_wall, procs = 0.0, 0.0, 1
+    for _ in range(args.steps):
+        s, w, procs = run_oracle_sample(pool)
+        tot_steps += s
+        tot_wall += w
+    value = tot_steps / tot_wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": ORACLE_SAMPLE_TEXT},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": ORACLE_SAMPLE_TEXT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return parse_clock_lines([])
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        return parse_clock_lines(out.splitlines())
+
+
+def gpu_arm(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1505_00965_gb300 import mlmc
+
+    stream = torch.cuda.current_stream()
+    seeds = rank_seeds(rank)
+    problems = {p: mlmc.Problem(payoff=p, cash=1.0, **GBM) for p in PAYOFFS}
+
+    def one_step():
+        out = []
+        for p in PAYOFFS:
+            for s in seeds:
+                out.append((p, mlmc.mlmc_estimate(EPS, problems[p], s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0,
+                                                  precision="fp32", stream=stream)))
+        return out
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_ms, wall_s, steps, instr, kern_ms, launches, d2h = 0.0, 0.0, 0.0, 0.0, 0.0, 0, 0
+    tte = {p: [] for p in PAYOFFS}
+    conv = {p: [] for p in PAYOFFS}
+    last = None
+    for _ in range(args.steps):
+        flush.zero_()                     # L2 flushed between timed steps, outside their events
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        res = one_step()
+        t1 = time.perf_counter()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+        wall_s += t1 - t0
+        for p, r in res:
+            steps += r.path_steps
+            instr += estimate_instructions(r.N, M, p)
+            kern_ms += r.kernel_ms
+            launches += r.launches
+            d2h += r.d2h_bytes
+            tte[p].append(r.wall_ms)
+            conv[p].append(r.converged)
+        last = res
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    dev_s, wall_max, steps_all, launches_all = combine_over_ranks(dev_ms / 1e3, wall_s, steps, float(launches))
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    sms = mlmc.mlmc_device_sm_count()
+    run_mhz = (clocks or {}).get("sm_mhz") or None
+    max_mhz = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
+    peak = sms * SCHEDULERS_PER_SM * WARP * max_mhz * 1e6 / 1e9          # G instructions / s
+    achieved = instr / (kern_ms / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginstr/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "level_kernel (FP32 paths, all levels of the step)",
+                "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz (max SM clock), "
+                              "one warp instruction per scheduler per clock",
+                "frac_at_run_clock": (achieved / (sms * 128 * run_mhz * 1e6 / 1e9)) if run_mhz else None,
+                "kernel_path_steps_per_s": steps / (kern_ms / 1e3)}
+
+    # plain FP64 GPU MLMC on the same GPU, same eps (outside the timed region; Asian, first seed)
+    fp64 = mlmc.mlmc_estimate(EPS, problems["asian"], seeds[0], M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64",
+                              stream=stream)
+    fp32_asian_median = statistics.median(tte["asian"][:len(seeds)])
+    value = steps_all / dev_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "eps": EPS, "payoffs": list(PAYOFFS), "M": M, "Lmax": LMAX, "N0": N0,
+                   "seeds_per_gpu": SEEDS_PER_RANK, "precision": "FP32 paths, FP64 moment sums",
+                   "l2": "512 MiB buffer written before every timed step, outside its events (the kernels read "
+                         "no input arrays; they are compute bound)"},
+        "time_to_eps_ms": {p: statistics.median(v) for p, v in tte.items()},
+        "converged_fraction": {p: sum(v) / len(v) for p, v in conv.items()},
+        "fp64_gpu_time_to_eps_ms": {"asian": fp64.wall_ms},
+        "fp64_vs_fp32_time_to_eps": {"asian": fp64.wall_ms / fp32_asian_median},
+        "estimates": {p: [r.P for q, r in last if q == p] for p in PAYOFFS},
+        "gpu_launches": int(launches_all),
+        "e2e": {"value": steps_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h / args.steps),
+                "note": "mlmc_estimate through the C ABI: arguments by value (kernel parameters), results "
+                        "copied device to host every round"},
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(os.cpu_count() or 1)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300":
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -22,8 +22,9 @@
  *   - All floating-point arguments are FP64; the path arithmetic precision is chosen by an
  *     mlmc_precision argument.
  *   - Random numbers: sample s of level l draws Philox4x32-10 blocks with key = (seed low,
- *     seed high) and counter = (j, s low, s high, (tag << 16) | l), j = 0, 1, ...  Each block
- *     gives two Box--Muller pairs.  Every level and every sample index therefore has its own,
+ *     seed high) and counter = (j, s low, s high, (tag << 16) | l), j = 0, 1, ...  Block j
+ *     gives normals 4j..4j+3 by two Box--Muller pairs; fine step k takes normal k,
+ *     dW_k = sqrt(T / M^l) z_k.  Every level and every sample index therefore has its own,
  *     independent numbers (Sec. 5: fresh random numbers on every level), and a sample range
  *     [first, first + N) can be computed in any order, on any device, with identical results.
  */
@@ -174,6 +175,8 @@ typedef struct mlmc_result {
     double path_steps;               /* sum_l N_l M^l: coupled fine steps simulated */
     double kernel_ms;                /* device time of the level kernels */
     double wall_ms;                  /* host wall time of the call */
+    uint64_t launches;               /* level-kernel launches made */
+    uint64_t d2h_bytes;              /* bytes copied device to host (the round sums) */
 } mlmc_result;
 
 /*

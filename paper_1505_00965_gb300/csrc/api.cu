@@ -162,8 +162,8 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.K = pay->K;
     p.Q = pay->cash;
     const double h = m->T / (double)nf;
-    p.small = nf < 8 ? 1 : 0;
-    p.a = m->sigma * std::sqrt(p.small ? m->T / 8.0 : h);
+    p.small = nf < 4 ? 1 : 0;
+    p.a = m->sigma * std::sqrt(h);
     p.rh = m->r * h;
     p.inv_nf = 1.0 / (double)nf;
     p.inv_nc = level > 0 ? (double)M / (double)nf : 0.0;
@@ -454,6 +454,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     std::vector<uint64_t> dN(Lmin + 1, N0);
     double kernel_ms = 0.0;
     int rounds = 0;
+    uint64_t launches = 0, d2h_bytes = 0;
     while (std::any_of(dN.begin(), dN.end(), [](uint64_t v) { return v > 0; })) {
         ++rounds;
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -474,9 +475,11 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
                 cleanup();
                 return rc;
             }
+            ++launches;
         }
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         e = cudaMemcpyAsync(h_sums, d_sums, (d.L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        d2h_bytes += (d.L + 1) * 4 * sizeof(double);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "level round");
         float ms = 0.f;
@@ -535,6 +538,8 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     out->total_cost = total;
     out->path_steps = steps;
     out->kernel_ms = kernel_ms;
+    out->launches = launches;
+    out->d2h_bytes = d2h_bytes;
     out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (!converged) {
         fail(MLMC_ENOTCONV, "bias test still failing at Lmax = %d", Lmax);

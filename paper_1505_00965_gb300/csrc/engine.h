@@ -13,7 +13,7 @@ struct LevelParams {
     double S0;        // initial value
     double disc;      // exp(-r T)
     double K, Q;      // strike, digital cash
-    double a;         // sigma * sqrt(grid step): grid step = T / M^l, or T / 8 on small levels
+    double a;         // sigma * sqrt(h), h = T / M^l
     double rh;        // r * fine step
     double inv_nf;    // 1 / M^l
     double inv_nc;    // 1 / M^(l-1)
@@ -24,7 +24,7 @@ struct LevelParams {
     int level, M;
     int nf;           // fine steps M^l
     int lanes;        // lanes per sample (1 = one thread per sample)
-    int small;        // 1 when M^l < 8: the sample draws 8 normals on the T/8 grid
+    int small;        // 1 when M^l < 4: the path uses part of one Philox block
     double *partials; // [gridDim.x][4] block partial sums (workspace)
     double *out;      // [4] level sums (device)
     unsigned *ticket; // completion counter (workspace), zero between launches

@@ -136,51 +136,30 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
 }
 
-// Levels with M^l < 8: the sample draws 8 normals (the T/8 grid) and fine step k sums the
-// 8 / M^l normals that fall inside it.
+// Levels with M^l < 4 (level 0, and level 1 when M = 2): the fine steps take the first one or
+// two normals of the sample's first Philox block.
 template <typename R, int PAY>
 __device__ __forceinline__ void simulate_small(const LevelParams &p, uint32_t slo, uint32_t shi,
                                                PathAcc<R, PAY, false> &fa,
                                                PathAcc<R, PAY, false> &ca)
 {
     const R a = R(p.a), rh = R(p.rh);
-    R z[8];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const uint4 x = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
-        R rho, c, s;
-        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
-        z[4 * j + 0] = rho * c;
-        z[4 * j + 1] = rho * s;
-        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
-        z[4 * j + 2] = rho * c;
-        z[4 * j + 3] = rho * s;
-    }
+    const uint4 x = philox4x32_10(make_uint4(0u, slo, shi, p.ctr3), p.key0, p.key1);
+    R rho, c, s;
+    BoxMuller<R>::pair(x.x, x.y, rho, c, s);
+    const R ra = rho * a;
     R fS = fa.S, fsum = fa.sum, fhi = fa.hi, flo = fa.lo, fls = fa.lsum;
-    R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
-    const int per_mask = 8 / p.nf - 1;  // 8 / M^l normals per fine step (a power of two)
-    const bool coupled = p.level > 0;
-    R zs = R(0), dc = R(0);
-    int q = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        zs += z[i];
-        if (((i + 1) & per_mask) == 0) {
-            const R d = fma(a, zs, rh);
-            zs = R(0);
-            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d);
-            if (coupled) {
-                dc += d;
-                if (++q == p.M) {
-                    em_step<R, PAY, false>(cS, csum, chi, clo, cls, dc);
-                    dc = R(0);
-                    q = 0;
-                }
-            }
-        }
+    const R d0 = fma(ra, c, rh);
+    em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
+    if (p.nf == 2) {
+        const R d1 = fma(ra, s, rh);
+        em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
+        // level 1 with M = 2: one coarse step driven by both fine increments
+        R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
+        em_step<R, PAY, false>(cS, csum, chi, clo, cls, d0 + d1);
+        ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
     }
     fa.S = fS; fa.sum = fsum; fa.hi = fhi; fa.lo = flo; fa.lsum = fls;
-    ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -286,6 +265,8 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
     const R S0 = R(p.S0);
     const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
     double m[4] = {0.0, 0.0, 0.0, 0.0};
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
+    int nb = 0;
 
     for (uint64_t base = 0; base + g_warp < p.N; base += groups) {
         const uint64_t idx = base + g;
@@ -325,14 +306,31 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
             Y = Pf - Pc;
         }
         if (valid && lig == 0) {
-            const double y = (double)Y;
-            const double y2 = y * y;
-            m[0] += y;
-            m[1] += y2;
-            m[2] = fma(y2, y, m[2]);
-            m[3] = fma(y2, y2, m[3]);
-            if (p.y_out) p.y_out[idx] = y;
+            if (p.y_out) p.y_out[idx] = (double)Y;
+            if constexpr (sizeof(R) == 4) {
+                // FP32 paths: power sums of a batch of at most 32 samples in FP32, each batch
+                // then added to the FP64 sums (FP64 stays off the per-sample path).
+                const float y = Y, y2 = y * y;
+                b1 += y;
+                b2 += y2;
+                b3 = fmaf(y2, y, b3);
+                b4 = fmaf(y2, y2, b4);
+                if (++nb == 32) {
+                    m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
+                    b1 = b2 = b3 = b4 = 0.f;
+                    nb = 0;
+                }
+            } else {
+                const double y = Y, y2 = y * y;
+                m[0] += y;
+                m[1] += y2;
+                m[2] = fma(y2, y, m[2]);
+                m[3] = fma(y2, y2, m[3]);
+            }
         }
+    }
+    if constexpr (sizeof(R) == 4) {
+        m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
     }
     finish_sums(m, p);
 }

@@ -61,7 +61,8 @@ class mlmc_result(ctypes.Structure):
                 ("mean", ctypes.c_double * MLMC_MAX_LEVELS), ("var", ctypes.c_double * MLMC_MAX_LEVELS),
                 ("cost", ctypes.c_double * MLMC_MAX_LEVELS), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("total_cost", ctypes.c_double), ("path_steps", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("wall_ms", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64)]
 
 
 _u64, _i32, _dbl, _vp, _sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -212,6 +213,8 @@ class Estimate:
     path_steps: float = 0.0
     kernel_ms: float = 0.0
     wall_ms: float = 0.0
+    launches: int = 0
+    d2h_bytes: int = 0
 
 
 def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int = 2, Lmax: int = 8,
@@ -229,4 +232,5 @@ def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int
                     N=[int(r.N[l]) for l in range(L + 1)], sums=[list(r.sums[l]) for l in range(L + 1)],
                     mean=[r.mean[l] for l in range(L + 1)], var=[r.var[l] for l in range(L + 1)],
                     cost=[r.cost[l] for l in range(L + 1)], alpha=r.alpha, beta=r.beta, total_cost=r.total_cost,
-                    path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms)
+                    path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms, launches=int(r.launches),
+                    d2h_bytes=int(r.d2h_bytes))

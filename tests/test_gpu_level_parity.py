@@ -75,12 +75,15 @@ def _check_level(mlmc, level, M, N, first, payoff, precision, launch=None, seed=
     assert np.all(np.isfinite(y))
     worst = float(diff[keep].max()) if keep.any() else 0.0
     assert worst <= bound, f"{payoff} {precision} l={level}: max |dY| = {worst:.3e} > {bound:.3e}"
-    # the device's four sums against the same sums of the device's own Y (reduction check)
+    # the device's four sums against the same sums of the device's own Y (reduction check):
+    # FP64 paths add in FP64; FP32 paths add batches of at most 32 samples in FP32 first,
+    # a relative error of at most 32 u of the sum of |Y|^k
     own = moment_sums(y)
     absy = np.abs(y)
+    red_tol = 1e-12 if precision == "fp64" else 32 * U["fp32"]
     for k in range(4):
         scale = np.sum(absy ** (k + 1)) + 1e-300
-        assert abs(sums[k] - own[k]) <= 1e-12 * scale, (k, sums[k], own[k])
+        assert abs(sums[k] - own[k]) <= red_tol * scale, (k, sums[k], own[k])
     # level mean and higher moments against the oracle
     m_gpu, m_orc = np.mean(y[keep]), np.mean(yo[keep])
     tol = RTOL_MEAN[precision] * max(abs(m_orc), sbar)
@@ -126,7 +129,7 @@ def test_launch_shapes_agree(mlmc, threads, blocks):
     ref_sums, ref_y = run_level(mlmc, 3, 4, 5003, 0, p, 9, "fp32")
     sums, y = run_level(mlmc, 3, 4, 5003, 0, p, 9, "fp32", launch={"threads_per_block": threads, "blocks": blocks})
     assert np.array_equal(y, ref_y)
-    np.testing.assert_allclose(sums, ref_sums, rtol=1e-13)
+    np.testing.assert_allclose(sums, ref_sums, rtol=1e-6)
 
 
 def test_zero_samples_and_repeat_launches(mlmc):
@@ -152,7 +155,7 @@ def test_resume_offsets_compose(mlmc):
     """Samples are addressed by index: [0, N) = [0, a) + [a, N) sample by sample (Sec. 5's
     fresh samples per round come from advancing `first`)."""
     p = mlmc.Problem(payoff="asian", **GBM)
-    _, y = run_level(mlmc, 5, 4, 900, 0, p, 4, "fp64")
+    _, y = run_level(mlmc, 5, 4, 900, 0, p, 4, "fp64")  # per-sample values are launch independent
     _, y1 = run_level(mlmc, 5, 4, 400, 0, p, 4, "fp64")
     _, y2 = run_level(mlmc, 5, 4, 500, 400, p, 4, "fp64")
     assert np.array_equal(y, np.concatenate([y1, y2]))
