@@ -156,6 +156,31 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first,
                           int precision, int tag, const mlmc_launch *launch, double *d_sums,
                           void *d_workspace, size_t workspace_bytes, double *d_y, void *stream);
 
+/*
+ * mlmc_level_sums_noalloc -- mlmc_level_sums_async for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of the level estimator.
+ * Some callers must not allocate at run time: latency-critical loops where a cudaMalloc or
+ * cudaFree would synchronise the device or take an unpredictable time, processes whose device
+ * memory is already claimed by another allocator, and deployments whose rules forbid dynamic
+ * allocation after start-up.  This entry point allocates nothing: its reduction scratch is a
+ * fixed array in the library's device memory, 2048 blocks of partial sums plus a completion
+ * word (64 KiB + 256 bytes), which every GPU that loads the library holds until the process
+ * exits.
+ *   Arguments as mlmc_level_sums_async, without the workspace.  d_sums (device, 4 doubles)
+ *   is overwritten; d_y (device or NULL) receives Y per sample.
+ *   The first call on each device looks up the array's device address (with that device
+ *   current) and caches it; make that first call before any stream capture.
+ *   All calls share the one array: each call clears the completion word on `stream` before
+ *   its launch, and calls whose work overlaps on the GPU (different streams, or different
+ *   host threads without ordering) race on it.
+ * Errors: MLMC_EINVAL as mlmc_level_sums_async, and for an explicit launch->blocks above 2048
+ * (the message states the scratch needed and the scratch held); MLMC_ECUDA for a failed lookup
+ * or launch.
+ */
+int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,
+                            const mlmc_payoff *payoff, uint64_t seed, int precision, int tag,
+                            const mlmc_launch *launch, double *d_sums, double *d_y, void *stream);
+
 /* Result of one adaptive estimate (Sec. 5).  Arrays are indexed by level 0..L. */
 #define MLMC_MAX_LEVELS 16
 typedef struct mlmc_result {

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -266,6 +267,82 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const ml
     p.out = d_sums;
     p.y_out = d_y;
     return launch_level(plan, p, d_workspace, st);
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+//
+// Scratch of the allocation-free entry point: block partials for at most kNoAllocMaxBlocks
+// blocks and the completion ticket, in a file-scope device array.  Every GPU that loads this
+// library holds it until the process exits.
+}  // extern "C"
+
+namespace {
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(double) + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the array's name
+// only stands in for the symbol, so the address is looked up once per device, with that device
+// current, and cached.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(MLMC_EINVAL, "device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(MLMC_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MLMC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,
+                            const mlmc_payoff *payoff, uint64_t seed, int precision, int tag,
+                            const mlmc_launch *launch, double *d_sums, double *d_y, void *stream)
+{
+    int rc = check_level(level, M);
+    if (!rc) rc = check_problem(model, payoff);
+    if (!rc) rc = check_tag(tag);
+    if (rc) return rc;
+    if (!d_sums) return fail(MLMC_EINVAL, "d_sums must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    if (launch && launch->blocks > kNoAllocMaxBlocks)
+        return fail(MLMC_EINVAL, "%d blocks need %zu bytes of scratch; the static scratch holds %d blocks "
+                    "(%zu bytes)", launch->blocks, workspace_bytes_for_blocks(launch->blocks),
+                    kNoAllocMaxBlocks, kNoAllocScratchBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan plan;
+    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    if (rc) return rc;
+    if (N == 0) {
+        CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
+        return MLMC_OK;
+    }
+    plan.blocks = std::min(plan.blocks, kNoAllocMaxBlocks);
+    void *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    LevelParams p;
+    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+    p.out = d_sums;
+    p.y_out = d_y;
+    // The ticket keeps whatever the last call left; clear it on the stream before the launch.
+    const size_t partial_bytes = workspace_bytes_for_blocks(plan.blocks) - 256;
+    CUDA_TRY(cudaMemsetAsync((char *)scratch + partial_bytes, 0, sizeof(unsigned), st));
+    return launch_level(plan, p, scratch, st);
 }
 
 int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_model *model,

@@ -79,6 +79,7 @@ _SIGNATURES = {
     "mlmc_level_workspace_bytes": ([_i32, _i32, _u64, _i32, _pl], _sz),
     "mlmc_level_sums_async": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _sz, _vp, _vp],
                               _i32),
+    "mlmc_level_sums_noalloc": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _vp], _i32),
     "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
@@ -192,6 +193,16 @@ def mlmc_level_sums_async(level: int, M: int, N: int, first: int, problem: Probl
     _check(_lib.mlmc_level_sums_async(level, M, N, first, ctypes.byref(m), ctypes.byref(p), seed, _prec(precision),
                                       tag, ctypes.byref(ln) if ln is not None else None, _addr(d_sums),
                                       _addr(d_workspace), workspace_bytes, _addr(d_y), _addr(stream)))
+
+
+def mlmc_level_sums_noalloc(level: int, M: int, N: int, first: int, problem: Problem, seed: int, d_sums,
+                            precision="fp32", tag: int = MLMC_TAG_PATHS, launch=None, d_y=None, stream=None) -> None:
+    """Queue the level on `stream` with the library's fixed device scratch (no allocation).
+    The first call on a device looks up the scratch address; calls that overlap on the GPU race."""
+    m, p, ln = problem.model(), problem.payoff_struct(), _launch(launch)
+    _check(_lib.mlmc_level_sums_noalloc(level, M, N, first, ctypes.byref(m), ctypes.byref(p), seed,
+                                        _prec(precision), tag, ctypes.byref(ln) if ln is not None else None,
+                                        _addr(d_sums), _addr(d_y), _addr(stream)))
 
 
 @dataclass
