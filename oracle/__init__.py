@@ -70,8 +70,8 @@ def _load():
             lib.oracle_uniform.restype = dbl
             lib.oracle_normals.argtypes = [u64, i32, i32, u64, i32, i32, dptr]
             lib.oracle_normals.restype = None
-            lib.oracle_normals_per_sample.argtypes = [i32, i32]
-            lib.oracle_normals_per_sample.restype = ctypes.c_long
+            lib.oracle_sample_normals.argtypes = [u64, i32, i32, i32, u64, i32, dptr]
+            lib.oracle_sample_normals.restype = None
             lib.oracle_em_path.argtypes = [i32, dbl, dbl, dbl, dbl, dptr, dptr]
             lib.oracle_em_path.restype = None
             lib.oracle_payoff.argtypes = [i32, dbl, dbl, dbl, dbl, dptr, i32]
@@ -121,8 +121,11 @@ def uniform(x: int, stream: str = "fp64") -> float:
     return _load().oracle_uniform(int(x) & 0xFFFFFFFF, STREAMS[stream])
 
 
-def normals_per_sample(level: int, M: int) -> int:
-    return int(_load().oracle_normals_per_sample(level, M))
+def sample_normals(seed: int, level: int, M: int, s: int, stream: str = "fp64", tag: int = TAG_PATHS) -> np.ndarray:
+    """The M^l normals that drive sample s's fine increments."""
+    z = np.empty(M ** level, dtype=np.float64)
+    _load().oracle_sample_normals(seed, level, M, tag, s, STREAMS[stream], _dp(z))
+    return z
 
 
 def normals(seed: int, level: int, s: int, n: int, stream: str = "fp64", tag: int = TAG_PATHS) -> np.ndarray:

@@ -28,13 +28,16 @@
  *     u = 1 - (x mod 2^23) 2^-23 (the low 23 bits, exactly a float mantissa).  Both lie in
  *     (0, 1], so log(u) is finite.
  *   - Box--Muller: rho = sqrt(-2 log u1), z0 = rho cos(2 pi u2), z1 = rho sin(2 pi u2).
- *   - Fine step k of sample s (k < M^l) takes normal k of the sample: dW_k = sqrt(dt_l) z_k.
- *     A level-0 sample therefore uses one normal.
+ *   - Fine step k of sample s (k < M^l) takes normal k of the sample: dW_k = sqrt(dt_l) z_k,
+ *     where the sample's normals are those of its blocks j = 0, 1, ... in order.  When
+ *     M^l < 4 (level 0, and level 1 for M = 2), G = 4 / M^l consecutive samples share one
+ *     block: sample s takes normals (s mod G) M^l .. (s mod G) M^l + M^l - 1 of block j = 0 of
+ *     counter index floor(s / G) (in place of s).
  *   - The Brownian path on the T/8 grid (the learned control variate's inputs) is the running
  *     sum of the fine increments when M^l >= 8.  On coarser levels it is refined from the
- *     fine-grid values by Brownian-bridge midpoints, stage by stage and left to right; stage
- *     midpoints take the normals that follow the path's own Philox blocks (starting at normal
- *     4 ceil(M^l / 4)).  The fine path never depends on whether the grid is built.
+ *     fine-grid values by Brownian-bridge midpoints, stage by stage and left to right; the
+ *     midpoints take the normals of blocks j = 1, 2 of the sample's own counter.  The fine path
+ *     never depends on whether the grid is built.
  *   - Arithmetic Asian: trapezoid average (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 on each path's own
  *     grid.  Lookback: fixed strike, max over the grid points S_0..S_n.  Both discounted.
  *   - Cost of one level-l sample: C_0 = 1, C_l = M^l + M^{l-1} Euler--Maruyama steps.
@@ -106,11 +109,21 @@ void oracle_normals(uint64_t seed, int level, int tag, uint64_t s, int stream, i
 
 static long ipow(long b, int e) { long p = 1; while (e-- > 0) p *= b; return p; }
 
-/* Normals a level-l sample's path uses: one per fine step, rounded up to whole Philox blocks. */
-long oracle_normals_per_sample(int level, int M)
+/* The M^l normals of sample s's fine increments (the packing rule above). */
+void oracle_sample_normals(uint64_t seed, int level, int M, int tag, uint64_t s, int stream,
+                           double *z)
 {
     long nf = ipow(M, level);
-    return (nf + 3) / 4 * 4;
+    if (nf < 4) {
+        long group = 4 / nf;
+        double z4[4];
+        oracle_normals(seed, level, tag, s / (uint64_t)group, stream, 4, z4);
+        long slot = (long)(s % (uint64_t)group);
+        for (long k = 0; k < nf; ++k)
+            z[k] = z4[slot * nf + k];
+    } else {
+        oracle_normals(seed, level, tag, s, stream, (int)nf, z);
+    }
 }
 
 /* Euler--Maruyama for GBM over n steps of size h driven by the given increments (Eq. em). */
@@ -179,9 +192,8 @@ int oracle_sample_paths(int level, int M, uint64_t s, int tag, const oracle_prob
                         uint64_t seed, int stream, double *dWf, double *fine, double *coarse)
 {
     long nf = ipow(M, level);
-    long G = oracle_normals_per_sample(level, M);
-    double *z = (double *)malloc(sizeof(double) * (size_t)G);
-    oracle_normals(seed, level, tag, s, stream, (int)G, z);
+    double *z = (double *)malloc(sizeof(double) * (size_t)nf);
+    oracle_sample_normals(seed, level, M, tag, s, stream, z);
     double sqrt_h = sqrt(p->T / (double)nf);
     for (long k = 0; k < nf; ++k)
         dWf[k] = sqrt_h * z[k];
@@ -208,9 +220,8 @@ void oracle_grid_brownian(int level, int M, uint64_t s, int tag, double T, uint6
                           int stream, double W8[8])
 {
     long nf = ipow(M, level);
-    long G = oracle_normals_per_sample(level, M);
-    double *z = (double *)malloc(sizeof(double) * (size_t)(G + 8));
-    oracle_normals(seed, level, tag, s, stream, (int)(G + 8), z);
+    double *z = (double *)malloc(sizeof(double) * (size_t)(nf > 8 ? nf : 8));
+    oracle_sample_normals(seed, level, M, tag, s, stream, z);
     double sqrt_h = sqrt(T / (double)nf);
     if (nf >= 8) {
         long per8 = nf / 8;
@@ -222,7 +233,8 @@ void oracle_grid_brownian(int level, int M, uint64_t s, int tag, double T, uint6
         }
     } else {
         /* grid[i] = W(i T / 8), i = 0..8; known at multiples of 8 / nf, then bridged */
-        double grid[9];
+        double grid[9], zb[12];
+        oracle_normals(seed, level, tag, s, stream, 12, zb);  /* blocks 0..2 of the sample */
         long step = 8 / nf;
         double W = 0.0;
         grid[0] = 0.0;
@@ -230,13 +242,13 @@ void oracle_grid_brownian(int level, int M, uint64_t s, int tag, double T, uint6
             W += sqrt_h * z[k];
             grid[(k + 1) * step] = W;
         }
-        long next = G;  /* first bridge normal */
+        long next = 4;  /* first normal of block 1 */
         for (long width = step; width > 1; width /= 2) {
             double dt_half = T / 8.0 * (double)(width / 2);
             for (long left = 0; left < 8; left += width) {
                 long mid = left + width / 2;
                 grid[mid] = 0.5 * (grid[left] + grid[left + width]) +
-                            sqrt(dt_half / 2.0) * z[next++];
+                            sqrt(dt_half / 2.0) * zb[next++];
             }
         }
         for (int k = 0; k < 8; ++k)

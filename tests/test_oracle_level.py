@@ -42,9 +42,9 @@ def test_level0_is_single_step_of_size_T():
     dW, fine, coarse = oracle.sample_paths(0, 4, 17, p, seed=5)
     assert coarse is None and len(fine) == 2 and len(dW) == 1
     assert fine[1] == pytest.approx(100 * (1 + 0.05 * 1.0 + 0.2 * dW[0]), rel=1e-15)
-    # and dW is sqrt(T) times the sample's first normal
-    z = oracle.normals(5, 0, 17, 4)
-    assert dW[0] == math.sqrt(1.0) * z[0]
+    # and dW is sqrt(T) times the sample's normal: slot 17 mod 4 of block 17 div 4
+    z = oracle.normals(5, 0, 17 // 4, 4)
+    assert dW[0] == math.sqrt(1.0) * z[17 % 4]
     Y = oracle.level_samples(0, 4, 1, p, seed=5, first=17)
     assert Y[0] == fine[1]
 
@@ -79,7 +79,7 @@ def test_fine_increments_are_stream_normals():
     p = Problem(payoff="european", **GBM)
     for level, M in [(0, 4), (1, 4), (2, 4), (3, 4), (1, 2), (4, 2), (1, 8)]:
         n = M ** level
-        z = oracle.normals(42, level, 7, n)
+        z = oracle.sample_normals(42, level, M, 7)
         dW, _, _ = oracle.sample_paths(level, M, 7, p, seed=42)
         np.testing.assert_array_equal(dW, math.sqrt(p.T / n) * z)
 

@@ -75,8 +75,23 @@ def test_normals_independent_across_levels_tags_and_slots():
     assert np.array_equal(oracle.normals(3, 2, 5, 16), oracle.normals(3, 2, 5, 16))
 
 
-def test_normals_per_sample_rule():
-    """One normal per fine step, rounded up to whole Philox blocks of four."""
-    assert [oracle.normals_per_sample(l, 4) for l in range(4)] == [4, 4, 16, 64]
-    assert [oracle.normals_per_sample(l, 2) for l in range(5)] == [4, 4, 4, 8, 16]
-    assert [oracle.normals_per_sample(l, 8) for l in range(3)] == [4, 8, 64]
+def test_sample_normals_packing_rule():
+    """Fine step k of a sample takes the sample's normal k; below four fine steps, 4 / M^l
+    consecutive samples share one Philox block."""
+    for s in [0, 1, 2, 3, 4, 17, 2 ** 33 + 5]:
+        # level 0: four samples per block
+        assert oracle.sample_normals(9, 0, 4, s)[0] == oracle.normals(9, 0, s // 4, 4)[s % 4]
+        # level 1 with M = 2: two samples per block, two normals each
+        np.testing.assert_array_equal(oracle.sample_normals(9, 1, 2, s),
+                                      oracle.normals(9, 1, s // 2, 4)[2 * (s % 2):2 * (s % 2) + 2])
+        # four or more fine steps: the sample's own blocks
+        np.testing.assert_array_equal(oracle.sample_normals(9, 2, 4, s), oracle.normals(9, 2, s, 16))
+
+
+def test_packed_level0_samples_independent():
+    """Samples sharing a block (and a Box--Muller pair) are independent standard normals."""
+    z = np.array([oracle.sample_normals(21, 0, 4, s)[0] for s in range(80_000)])
+    n = len(z)
+    for lag in (1, 2, 3, 4):
+        assert abs(np.corrcoef(z[:-lag], z[lag:])[0, 1]) < 4.5 / np.sqrt(n)
+    assert abs(z.mean()) < 4.5 / np.sqrt(n) and abs(z.var() - 1) < 4.5 * np.sqrt(2 / n)
