@@ -50,17 +50,18 @@ def rank_seeds(rank: int, n: int = SEEDS_PER_RANK) -> list[int]:
 
 
 def level_instructions(level: int, m: int, payoff: str) -> float:
-    """Algorithmic instructions of one FP32 sample on level l:
-    Philox4x32-10 = 40 per block (10 rounds of 2 widening multiplies + 2 three-input xors);
-    Box--Muller = 7 ALU + 4 MUFU per pair; per fine step 2 (increment, step) + 1 (coarse sum);
+    """Algorithmic instructions of one FP32 sample on level l, with n = M^l fine steps:
+    Philox4x32-10 = 40 per block of 4 normals (10 rounds of 2 widening multiplies + 2
+    three-input xors) and n / 4 blocks per sample (on levels with n < 4, 4 / n samples share a
+    block); Box--Muller = 11 per pair of normals (2 mantissa builds, 2 subtractions, 3
+    multiplies, 4 MUFU), n / 2 pairs; per fine step 2 (increment, step) + 1 (coarse sum, l > 0);
     per coarse step 1; running payoff functional 1 per fine and per coarse step (Asian,
     lookback); per sample 11 (payoffs, difference, moment updates)."""
     nf = m ** level
-    blocks = -(-nf // 4)
-    pairs = max(1, nf // 2)
-    per_fine = 2 + (1 if level > 0 else 0) + (1 if payoff in ("asian", "lookback") else 0)
-    coarse = (nf // m) * (1 + (1 if payoff in ("asian", "lookback") else 0)) if level > 0 else 0
-    return 40.0 * blocks + 11.0 * pairs + per_fine * nf + coarse + 11.0
+    functional = 1 if payoff in ("asian", "lookback") else 0
+    per_fine = 2 + (1 if level > 0 else 0) + functional
+    coarse = (nf // m) * (1 + functional) if level > 0 else 0
+    return 40.0 * nf / 4 + 11.0 * nf / 2 + per_fine * nf + coarse + 11.0
 
 
 def estimate_instructions(N: list[int], m: int, payoff: str) -> float:

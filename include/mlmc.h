@@ -144,9 +144,11 @@ size_t mlmc_level_workspace_bytes(int level, int M, uint64_t N, int precision,
 /*
  * mlmc_level_sums_async -- queue the level estimator on `stream` with device outputs:
  *   d_sums       device, 4 doubles overwritten with sum Y^k, k = 1..4
- *   d_workspace  device, at least mlmc_level_workspace_bytes(...) bytes, 256-byte aligned,
- *                zero-filled before its first use; every launch leaves it zero-filled again.
- *                Launches that share one workspace must be ordered (same stream).
+ *   d_workspace  device, at least mlmc_level_workspace_bytes(...) bytes, 256-byte aligned.
+ *                Its first 256 bytes hold a completion counter that must be zero before the
+ *                first launch; every launch leaves it zero again.  The rest holds per-block
+ *                partial sums and needs no initial value.  One workspace may serve launches of
+ *                any level and grid size as long as they are ordered (same stream).
  *   d_y          device or NULL: if not NULL, N doubles receive Y of each sample in order
  * Never synchronises and allocates nothing.  Errors: MLMC_EINVAL (also for a workspace that is
  * too small or misaligned), MLMC_ECUDA for a failed launch.

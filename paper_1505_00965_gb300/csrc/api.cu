@@ -134,7 +134,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
             lanes *= 2;
     }
     const bool split = lanes > 1;
-    const int mt = M == 4 ? 4 : 0;
+    const bool small = nf < 4;
+    const int mt = small ? -1 : (M == 4 ? 4 : 0);
     plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split)
                                                : level_kernel_fp64(payoff, mt, split);
     if (!plan->kernel) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
@@ -144,7 +145,10 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
     int blocks = launch && launch->blocks ? launch->blocks : 0;
     if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
     if (!blocks) {
-        const double need = std::ceil((double)std::max<uint64_t>(N, 1) * lanes / threads);
+        // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels
+        const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
+                                   : (double)std::max<uint64_t>(N, 1) * lanes;
+        const double need = std::ceil(items / threads);
         blocks = (int)std::min<double>(need, max_blocks);
     }
     blocks = std::max(blocks, 1);
@@ -196,9 +200,8 @@ int check_tag(int tag)
 
 int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st)
 {
-    p.partials = (double *)ws;
-    const size_t partial_bytes = workspace_bytes_for_blocks(plan.blocks) - 256;
-    p.ticket = (unsigned *)((char *)ws + partial_bytes);
+    p.ticket = (unsigned *)ws;
+    p.partials = (double *)((char *)ws + kTicketBytes);
     void *args[] = {&p};
     CUDA_TRY(cudaLaunchKernel(plan.kernel, dim3(plan.blocks), dim3(plan.threads), args, 0, st));
     return MLMC_OK;
@@ -278,7 +281,7 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const ml
 
 namespace {
 constexpr int kNoAllocMaxBlocks = 2048;
-constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(double) + 256;
+constexpr size_t kNoAllocScratchBytes = kTicketBytes + (size_t)kNoAllocMaxBlocks * 4 * sizeof(double);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -340,8 +343,7 @@ int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const 
     p.out = d_sums;
     p.y_out = d_y;
     // The ticket keeps whatever the last call left; clear it on the stream before the launch.
-    const size_t partial_bytes = workspace_bytes_for_blocks(plan.blocks) - 256;
-    CUDA_TRY(cudaMemsetAsync((char *)scratch + partial_bytes, 0, sizeof(unsigned), st));
+    CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(unsigned), st));
     return launch_level(plan, p, scratch, st);
 }
 
@@ -361,13 +363,13 @@ int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_
     if (rc) return rc;
     double out[4] = {0.0, 0.0, 0.0, 0.0};
     if (N > 0) {
-        const size_t ws_bytes = workspace_bytes_for_blocks(plan.blocks) + 256;
+        const size_t ws_bytes = workspace_bytes_for_blocks(plan.blocks) + 64;
         void *ws = nullptr;
         CUDA_TRY(cudaMallocAsync(&ws, ws_bytes, st));
         cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, st);
         LevelParams p;
         fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
-        p.out = (double *)((char *)ws + ws_bytes - 256);
+        p.out = (double *)((char *)ws + workspace_bytes_for_blocks(plan.blocks));
         if (e == cudaSuccess) rc = launch_level(plan, p, ws, st);
         else rc = fail(MLMC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
         if (!rc) {

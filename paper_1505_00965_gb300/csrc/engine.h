@@ -24,22 +24,24 @@ struct LevelParams {
     int level, M;
     int nf;           // fine steps M^l
     int lanes;        // lanes per sample (1 = one thread per sample)
-    int small;        // 1 when M^l < 4: the path uses part of one Philox block
+    int small;        // 1 when M^l < 4: 4 / M^l samples share one Philox block
     double *partials; // [gridDim.x][4] block partial sums (workspace)
     double *out;      // [4] level sums (device)
     unsigned *ticket; // completion counter (workspace), zero between launches
     double *y_out;    // optional per-sample Y, NULL = off
 };
 
-// Workspace layout: partial sums of `blocks` blocks, then the ticket word.
+// Workspace layout: the completion ticket in the first 256 bytes, then the FP64 partial sums
+// of `blocks` blocks.  The ticket sits at a fixed offset so that launches of any grid size can
+// share one workspace: it is zero between launches, while the partials need no initial value.
+constexpr size_t kTicketBytes = 256;
 inline size_t workspace_bytes_for_blocks(int blocks)
 {
-    size_t partial = (size_t)blocks * 4 * sizeof(double);
-    partial = (partial + 255) / 256 * 256;
-    return partial + 256;
+    return kTicketBytes + (size_t)blocks * 4 * sizeof(double);
 }
 
-// Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel.
+// Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel and
+// -1 for the kernel of levels with M^l < 4.
 const void *level_kernel_fp32(int payoff, int mt, bool split);
 const void *level_kernel_fp64(int payoff, int mt, bool split);
 

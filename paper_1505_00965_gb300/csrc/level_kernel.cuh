@@ -136,32 +136,6 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
 }
 
-// Levels with M^l < 4 (level 0, and level 1 when M = 2): the fine steps take the first one or
-// two normals of the sample's first Philox block.
-template <typename R, int PAY>
-__device__ __forceinline__ void simulate_small(const LevelParams &p, uint32_t slo, uint32_t shi,
-                                               PathAcc<R, PAY, false> &fa,
-                                               PathAcc<R, PAY, false> &ca)
-{
-    const R a = R(p.a), rh = R(p.rh);
-    const uint4 x = philox4x32_10(make_uint4(0u, slo, shi, p.ctr3), p.key0, p.key1);
-    R rho, c, s;
-    BoxMuller<R>::pair(x.x, x.y, rho, c, s);
-    const R ra = rho * a;
-    R fS = fa.S, fsum = fa.sum, fhi = fa.hi, flo = fa.lo, fls = fa.lsum;
-    const R d0 = fma(ra, c, rh);
-    em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
-    if (p.nf == 2) {
-        const R d1 = fma(ra, s, rh);
-        em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
-        // level 1 with M = 2: one coarse step driven by both fine increments
-        R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
-        em_step<R, PAY, false>(cS, csum, chi, clo, cls, d0 + d1);
-        ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
-    }
-    fa.S = fS; fa.sum = fsum; fa.hi = fhi; fa.lo = flo; fa.lsum = fls;
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -215,6 +189,33 @@ __device__ __forceinline__ void finish_sums(double m[4], const LevelParams &p)
         for (int k = 0; k < 4; ++k) p.out[k] = acc[k];
         *p.ticket = 0u;  // leave the workspace ready for the next launch
     }
+}
+
+// Add Y, Y^2, Y^3, Y^4 of one sample.  FP64 paths add into the FP64 sums m directly.  FP32
+// paths sum a batch of at most 32 samples in FP32 (b1..b4, nb counts the batch) and add each
+// batch into m, which keeps FP64 off the per-sample path.
+__device__ __forceinline__ void add_moments(float Y, double m[4], float &b1, float &b2, float &b3,
+                                            float &b4, int &nb)
+{
+    const float y2 = Y * Y;
+    b1 += Y;
+    b2 += y2;
+    b3 = fmaf(y2, Y, b3);
+    b4 = fmaf(y2, y2, b4);
+    if (++nb == 32) {
+        m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
+        b1 = b2 = b3 = b4 = 0.f;
+        nb = 0;
+    }
+}
+__device__ __forceinline__ void add_moments(double Y, double m[4], float &, float &, float &,
+                                            float &, int &)
+{
+    const double y2 = Y * Y;
+    m[0] += Y;
+    m[1] += y2;
+    m[2] = fma(y2, Y, m[2]);
+    m[3] = fma(y2, y2, m[3]);
 }
 
 // Join the chunks of one sample split over P lanes: an exclusive product scan of the chunk
@@ -281,11 +282,7 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
         ca.init(R(1));
         R Y;
         if constexpr (!SPLIT) {
-            if (p.small) {
-                simulate_small<R, PAY>(p, slo, shi, fa, ca);
-            } else {
-                simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
-            }
+            simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
             const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
             const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
                                               R(p.nf) * logS0 + fa.lsum, inv_nf, p);
@@ -307,26 +304,71 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
         }
         if (valid && lig == 0) {
             if (p.y_out) p.y_out[idx] = (double)Y;
-            if constexpr (sizeof(R) == 4) {
-                // FP32 paths: power sums of a batch of at most 32 samples in FP32, each batch
-                // then added to the FP64 sums (FP64 stays off the per-sample path).
-                const float y = Y, y2 = y * y;
-                b1 += y;
-                b2 += y2;
-                b3 = fmaf(y2, y, b3);
-                b4 = fmaf(y2, y2, b4);
-                if (++nb == 32) {
-                    m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
-                    b1 = b2 = b3 = b4 = 0.f;
-                    nb = 0;
-                }
-            } else {
-                const double y = Y, y2 = y * y;
-                m[0] += y;
-                m[1] += y2;
-                m[2] = fma(y2, y, m[2]);
-                m[3] = fma(y2, y2, m[3]);
+            add_moments(Y, m, b1, b2, b3, b4, nb);
+        }
+    }
+    if constexpr (sizeof(R) == 4) {
+        m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
+    }
+    finish_sums(m, p);
+}
+
+// Levels with M^l < 4 (level 0, and level 1 when M = 2).  G = 4 / M^l consecutive samples share
+// one Philox block: thread t takes block q = first / G + t (grid-stride) and the G samples
+// q G .. q G + G - 1 that fall in [first, first + N); sample slot r takes normals
+// r M^l .. r M^l + M^l - 1 of the block.
+template <typename R, int PAY>
+__global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
+{
+    const int nf = p.nf;
+    const uint32_t G = 4u / (uint32_t)nf;
+    const uint64_t end = p.first + p.N;
+    const uint64_t q0 = p.first / G;
+    const uint64_t nq = (end - 1) / G - q0 + 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const R a = R(p.a), rh = R(p.rh), S0 = R(p.S0);
+    const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
+    int nb = 0;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += stride) {
+        const uint64_t q = q0 + t;
+        const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3),
+                                      p.key0, p.key1);
+        R rho, c, s, d[4];
+        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
+        R ra = rho * a;
+        d[0] = fma(ra, c, rh);
+        d[1] = fma(ra, s, rh);
+        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
+        ra = rho * a;
+        d[2] = fma(ra, c, rh);
+        d[3] = fma(ra, s, rh);
+#pragma unroll
+        for (uint32_t r = 0; r < 4; ++r) {
+            if (r >= G) break;
+            const uint64_t sample = q * G + r;
+            if (sample < p.first || sample >= end) continue;
+            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+            R cS = R(1), csum = R(0), chi = R(1), clo = R(1), cls = R(0);
+            R Y;
+            if (nf == 1) {
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
+                Y = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            } else {  // nf == 2, level 1 with M = 2: two fine steps, one coarse step
+                const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
+                em_step<R, PAY, false>(cS, csum, chi, clo, cls, d0 + d1);
+                const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
+                const R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls,
+                                                  inv_nf, p);
+                const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
+                Y = Pf - Pc;
             }
+            if (p.y_out) p.y_out[sample - p.first] = (double)Y;
+            add_moments(Y, m, b1, b2, b3, b4, nb);
         }
     }
     if constexpr (sizeof(R) == 4) {
@@ -353,8 +395,23 @@ template <typename R, int MT, bool SPLIT> const void *select_by_payoff(int payof
     }
 }
 
+template <typename R> const void *select_small_kernel(int payoff)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)level_small_kernel<R, kEuropean>;
+    case kAsian: return (const void *)level_small_kernel<R, kAsian>;
+    case kLookback: return (const void *)level_small_kernel<R, kLookback>;
+    case kDigital: return (const void *)level_small_kernel<R, kDigital>;
+    case kLinear: return (const void *)level_small_kernel<R, kLinear>;
+    case kGeoAsian: return (const void *)level_small_kernel<R, kGeoAsian>;
+    default: return nullptr;
+    }
+}
+
+// mt = -1 selects the kernel of levels with M^l < 4.
 template <typename R> const void *select_level_kernel(int payoff, int mt, bool split)
 {
+    if (mt < 0) return select_small_kernel<R>(payoff);
     if (mt == 4) return split ? select_by_payoff<R, 4, true>(payoff) : select_by_payoff<R, 4, false>(payoff);
     return split ? select_by_payoff<R, 0, true>(payoff) : select_by_payoff<R, 0, false>(payoff);
 }

@@ -18,8 +18,8 @@ def test_rank_seeds_disjoint_and_first_rank_is_1_to_8():
 
 
 def test_level_instruction_model():
-    # level 0: one Philox block, one Box--Muller pair, one step (no coarse sum), per-sample work
-    assert bench.level_instructions(0, 4, "european") == 40 + 11 + 2 + 11
+    # level 0: a quarter Philox block, half a Box--Muller pair, one step, per-sample work
+    assert bench.level_instructions(0, 4, "european") == 40 / 4 + 11 / 2 + 2 + 11
     # level l >= 1 with a running functional: 20 M^l + 11 ... plus the coarse terms
     nf = 4 ** 3
     want = 40 * nf / 4 + 11 * nf / 2 + 4 * nf + 2 * (nf // 4) + 11

@@ -182,3 +182,24 @@ def test_config_plain_fp64_european_full(mlmc):
         var += (sums[1] / 1e4 - m * m) / 1e4
     bs = black_scholes_call(100, 100, 0.05, 0.2, 1.0)
     assert abs(total - bs) < 4 * math.sqrt(var) + 0.02
+
+
+def test_workspace_reuse_across_grid_sizes(mlmc):
+    """One workspace serves launches of any level and grid size in stream order (the adaptive
+    driver reuses one): grids that shrink and grow give the sums of fresh workspaces."""
+    import torch
+
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    shapes = [(0, 400_003, 300), (1, 200_001, 7), (2, 50_001, 64), (0, 9_999, 1), (3, 20_001, 33), (1, 77_777, 129),
+              (5, 3_001, 2)]
+    ws_bytes = max(mlmc.mlmc_level_workspace_bytes(l, 4, n, "fp32", {"blocks": b}) for l, n, b in shapes)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    outs = torch.zeros(len(shapes), 4, dtype=torch.float64, device="cuda")
+    for i, (l, n, b) in enumerate(shapes):
+        mlmc.mlmc_level_sums_async(l, 4, n, 11, p, 3, outs[i], ws, ws_bytes, precision="fp32",
+                                   launch={"blocks": b}, stream=stream)
+    torch.cuda.synchronize()
+    for i, (l, n, b) in enumerate(shapes):
+        ref, _ = run_level(mlmc, l, 4, n, 11, p, 3, "fp32", launch={"blocks": b})
+        np.testing.assert_array_equal(outs[i].cpu().numpy(), ref)
