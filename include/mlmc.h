@@ -227,6 +227,34 @@ int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc
                   const mlmc_payoff *payoff, uint64_t seed, int precision, void *stream,
                   mlmc_result *out);
 
+/* One problem of a batch: model, payoff, accuracy and seed. */
+typedef struct mlmc_problem {
+    mlmc_model model;
+    mlmc_payoff payoff;
+    double eps;                      /* requested root-mean-square accuracy, > 0 */
+    uint64_t seed;                   /* Philox key of this problem's samples */
+} mlmc_problem;
+
+/*
+ * mlmc_estimate_batch -- n independent adaptive estimates (each as mlmc_estimate, Sec. 5),
+ * computed together.  Every round gathers the new samples of all unfinished problems on all
+ * their levels into one list of chunks of about equal work; one persistent kernel works through
+ * the list (each block claims the next chunk from a counter; deep levels with few samples split
+ * every path over several lanes), and a second kernel adds each (problem, level)'s chunk sums in
+ * a fixed order, so results do not depend on scheduling.  The round's upload, both kernels and
+ * the download are captured once in a CUDA graph and replayed every round.
+ *   n >= 1; problems host [n], read only; M, Lmin, Lmax, N0, precision as mlmc_estimate and
+ *   shared by all problems; stream as mlmc_estimate (the batch runs on its own stream after
+ *   `stream` has drained, and is finished on return).
+ *   results host [n], written for every problem.  kernel_ms, wall_ms, launches and d2h_bytes
+ *   describe the whole batch (the same values in every result).
+ * Returns MLMC_OK when every problem converged, MLMC_ENOTCONV when some reached Lmax first
+ * (their results carry converged = 0 and the estimate at Lmax), MLMC_EINVAL for a bad argument
+ * (the message names the problem), MLMC_ECUDA or MLMC_ENOMEM for device failures.
+ */
+int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, int Lmin, int Lmax, uint64_t N0,
+                        int precision, void *stream, mlmc_result *results);
+
 /* Number of streaming multiprocessors of the current device, or -1 with an error message. */
 int mlmc_device_sm_count(void);
 

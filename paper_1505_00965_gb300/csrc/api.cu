@@ -13,7 +13,9 @@
 #include <string>
 #include <vector>
 
+#include "driver.h"
 #include "engine.h"
+#include "host.h"
 #include "mlmc.h"
 
 using namespace mlmcgb;
@@ -21,6 +23,10 @@ using namespace mlmcgb;
 namespace {
 
 thread_local std::string g_error;
+
+}  // namespace
+
+namespace mlmcgb {
 
 int fail(int code, const char *fmt, ...)
 {
@@ -33,12 +39,6 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
-#define CUDA_TRY(expr)                                                                          \
-    do {                                                                                        \
-        cudaError_t e_ = (expr);                                                                \
-        if (e_ != cudaSuccess)                                                                  \
-            return fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));            \
-    } while (0)
 
 long ipow(long b, int e)
 {
@@ -76,11 +76,6 @@ int check_level(int level, int M)
         return fail(MLMC_EINVAL, "level %d out of range for M = %d (need M^level <= 2^24)", level, M);
     return MLMC_OK;
 }
-
-struct Plan {
-    const void *kernel;
-    int threads, lanes, blocks;
-};
 
 int device_sms(int *sms)
 {
@@ -181,6 +176,7 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.M = M;
     p.nf = (int)nf;
     p.lanes = lanes;
+    p.payoff = pay->kind;
     p.partials = nullptr;
     p.out = nullptr;
     p.ticket = nullptr;
@@ -207,7 +203,7 @@ int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st)
     return MLMC_OK;
 }
 
-}  // namespace
+}  // namespace mlmcgb
 
 extern "C" {
 
@@ -397,85 +393,21 @@ int mlmc_level_sums(int level, int M, uint64_t N, const mlmc_model *model,
 
 // ------------------------------------------------------------------ adaptive driver (Sec. 5)
 
-namespace {
+namespace mlmcgb {
 
-double lsq_slope(const std::vector<double> &x, const std::vector<double> &y)
+int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int precision)
 {
-    const size_t n = x.size();
-    double mx = 0, my = 0;
-    for (size_t i = 0; i < n; ++i) {
-        mx += x[i];
-        my += y[i];
-    }
-    mx /= n;
-    my /= n;
-    double sxy = 0, sxx = 0;
-    for (size_t i = 0; i < n; ++i) {
-        sxy += (x[i] - mx) * (y[i] - my);
-        sxx += (x[i] - mx) * (x[i] - mx);
-    }
-    return sxy / sxx;
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(MLMC_EINVAL, "eps must be positive and finite");
+    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
+    if (Lmin < 1 || Lmax < Lmin || Lmax >= MLMC_MAX_LEVELS || ipow(M, Lmax) > (1L << 24))
+        return fail(MLMC_EINVAL, "need 1 <= Lmin <= Lmax < %d and M^Lmax <= 2^24", MLMC_MAX_LEVELS);
+    if (N0 < 2) return fail(MLMC_EINVAL, "N0 must be at least 2");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    return MLMC_OK;
 }
 
-struct DriverState {
-    int M, L;
-    std::vector<uint64_t> N;
-    std::vector<std::array<double, 4>> S;
-    std::vector<double> mean, var, C;
-    double alpha = 0.5, beta = 0.5;
-};
-
-// Weak and variance rates: least-squares slopes of log_M |m_l| and log_M V_l over l = 1..L,
-// floored at 1/2.
-void fit_rates(DriverState &d)
-{
-    const double tiny = 1e-300, lnM = std::log((double)d.M);
-    std::vector<double> ls, lm, lv;
-    for (int l = 1; l <= d.L; ++l) {
-        ls.push_back(l);
-        lm.push_back(std::log(std::max(std::fabs(d.mean[l]), tiny)) / lnM);
-        lv.push_back(std::log(std::max(d.var[l], tiny)) / lnM);
-    }
-    d.alpha = std::max(0.5, -lsq_slope(ls, lm));
-    d.beta = std::max(0.5, -lsq_slope(ls, lv));
-}
-
-// Means and variances used by the formulas: for l >= 2, at least half the extrapolation
-// from the level below.
-void floored(const DriverState &d, std::vector<double> &mf, std::vector<double> &vf)
-{
-    mf = d.mean;
-    vf = d.var;
-    const double Ma = std::pow((double)d.M, d.alpha), Mb = std::pow((double)d.M, d.beta);
-    for (size_t l = 2; l < mf.size(); ++l) {
-        mf[l] = std::max(std::fabs(mf[l]), 0.5 * std::fabs(mf[l - 1]) / Ma);
-        vf[l] = std::max(vf[l], 0.5 * vf[l - 1] / Mb);
-    }
-}
-
-double bias_estimate(const std::vector<double> &mf, int M, double alpha)
-{
-    const int L = (int)mf.size() - 1;
-    const double Ma = std::pow((double)M, alpha);
-    return std::max(std::fabs(mf[L]), std::fabs(mf[L - 1]) / Ma) / (Ma - 1.0);
-}
-
-// N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)); dN_l = max(0, N_l - done_l).
-std::vector<uint64_t> extra_samples(const std::vector<double> &V, const std::vector<double> &C,
-                                    const std::vector<uint64_t> &done, double eps)
-{
-    double tot = 0;
-    for (size_t l = 0; l < V.size(); ++l) tot += std::sqrt(V[l] * C[l]);
-    std::vector<uint64_t> dN(V.size(), 0);
-    for (size_t l = 0; l < V.size(); ++l) {
-        const double n = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * tot);
-        const uint64_t want = n > 9.0e18 ? (uint64_t)9.0e18 : (uint64_t)n;
-        dN[l] = want > done[l] ? want - done[l] : 0;
-    }
-    return dN;
-}
-
-}  // namespace
+}  // namespace mlmcgb
 
 extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
                              const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
@@ -485,13 +417,8 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     int rc = check_problem(model, payoff);
     if (rc) return rc;
     if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
-    if (!(eps > 0) || !std::isfinite(eps)) return fail(MLMC_EINVAL, "eps must be positive and finite");
-    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
-    if (Lmin < 1 || Lmax < Lmin || Lmax >= MLMC_MAX_LEVELS || ipow(M, Lmax) > (1L << 24))
-        return fail(MLMC_EINVAL, "need 1 <= Lmin <= Lmax < %d and M^Lmax <= 2^24", MLMC_MAX_LEVELS);
-    if (N0 < 2) return fail(MLMC_EINVAL, "N0 must be at least 2");
-    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
-        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    rc = check_estimate_args(eps, M, Lmin, Lmax, N0, precision);
+    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
 
     // One workspace for every launch of this call: launches are ordered on `st`.
@@ -523,21 +450,14 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (e == cudaSuccess) e = cudaEventCreate(&ev1);
     if (e != cudaSuccess) return cuda_fail(e, "driver setup");
 
-    DriverState d;
-    d.M = M;
-    d.L = Lmin;
-    d.N.assign(Lmin + 1, 0);
-    d.S.assign(Lmin + 1, {0.0, 0.0, 0.0, 0.0});
-    d.C.clear();
-    for (int l = 0; l <= Lmin; ++l) d.C.push_back(level_cost(l, M));
-    std::vector<uint64_t> dN(Lmin + 1, N0);
+    AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
     double kernel_ms = 0.0;
-    int rounds = 0;
     uint64_t launches = 0, d2h_bytes = 0;
-    while (std::any_of(dN.begin(), dN.end(), [](uint64_t v) { return v > 0; })) {
-        ++rounds;
+    while (drv.active()) {
+        const std::vector<uint64_t> dN = drv.next_samples();
+        const int L = drv.finest_level();
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        for (int l = 0; l <= d.L; ++l) {
+        for (int l = 0; l <= L; ++l) {
             if (!dN[l]) continue;
             Plan plan;
             rc = plan_level(l, M, dN[l], precision, payoff->kind, nullptr, &plan);
@@ -547,7 +467,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
                 return rc;
             }
             LevelParams p;
-            fill_params(p, l, M, dN[l], d.N[l], model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+            fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
             p.out = d_sums + 4 * l;
             rc = launch_level(plan, p, ws, st);
             if (rc) {
@@ -557,70 +477,23 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
             ++launches;
         }
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        e = cudaMemcpyAsync(h_sums, d_sums, (d.L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
-        d2h_bytes += (d.L + 1) * 4 * sizeof(double);
+        e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        d2h_bytes += (L + 1) * 4 * sizeof(double);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "level round");
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) kernel_ms += ms;
-        for (int l = 0; l <= d.L; ++l) {
-            if (!dN[l]) continue;
-            for (int k = 0; k < 4; ++k) d.S[l][k] += h_sums[4 * l + k];
-            d.N[l] += dN[l];
-        }
-        d.mean.assign(d.L + 1, 0.0);
-        d.var.assign(d.L + 1, 0.0);
-        for (int l = 0; l <= d.L; ++l) {
-            d.mean[l] = d.S[l][0] / (double)d.N[l];
-            d.var[l] = std::max(d.S[l][1] / (double)d.N[l] - d.mean[l] * d.mean[l], 0.0);
-        }
-        fit_rates(d);
-        std::vector<double> mf, vf;
-        floored(d, mf, vf);
-        dN = extra_samples(vf, d.C, d.N, eps);
-        bool settled = true;
-        for (int l = 0; l <= d.L; ++l)
-            if ((double)dN[l] > 0.01 * (double)d.N[l]) settled = false;
-        if (settled && bias_estimate(mf, M, d.alpha) > eps / std::sqrt(2.0) && d.L < Lmax) {
-            d.L += 1;
-            vf.push_back(vf.back() / std::pow((double)M, d.beta));
-            d.N.push_back(0);
-            d.S.push_back({0.0, 0.0, 0.0, 0.0});
-            d.C.push_back(level_cost(d.L, M));
-            dN = extra_samples(vf, d.C, d.N, eps);
-        }
+        drv.absorb(h_sums);
     }
-    std::vector<double> mf, vf;
-    floored(d, mf, vf);
-    const bool converged = bias_estimate(mf, M, d.alpha) <= eps / std::sqrt(2.0);
     cleanup();
 
     std::memset(out, 0, sizeof(*out));
-    out->eps = eps;
-    out->L = d.L;
-    out->converged = converged ? 1 : 0;
-    out->rounds = rounds;
-    double P = 0.0, total = 0.0, steps = 0.0;
-    for (int l = 0; l <= d.L; ++l) {
-        out->N[l] = d.N[l];
-        for (int k = 0; k < 4; ++k) out->sums[l][k] = d.S[l][k];
-        out->mean[l] = d.mean[l];
-        out->var[l] = d.var[l];
-        out->cost[l] = (double)d.N[l] * d.C[l];
-        P += d.mean[l];
-        total += out->cost[l];
-        steps += (double)d.N[l] * (double)ipow(M, l);
-    }
-    out->P = P;
-    out->alpha = d.alpha;
-    out->beta = d.beta;
-    out->total_cost = total;
-    out->path_steps = steps;
+    drv.fill(out);
     out->kernel_ms = kernel_ms;
     out->launches = launches;
     out->d2h_bytes = d2h_bytes;
     out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-    if (!converged) {
+    if (!out->converged) {
         fail(MLMC_ENOTCONV, "bias test still failing at Lmax = %d", Lmax);
         return MLMC_ENOTCONV;
     }

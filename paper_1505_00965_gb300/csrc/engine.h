@@ -25,6 +25,7 @@ struct LevelParams {
     int nf;           // fine steps M^l
     int lanes;        // lanes per sample (1 = one thread per sample)
     int small;        // 1 when M^l < 4: 4 / M^l samples share one Philox block
+    int payoff;       // payoff code (the batched kernel selects its code path from it)
     double *partials; // [gridDim.x][4] block partial sums (workspace)
     double *out;      // [4] level sums (device)
     unsigned *ticket; // completion counter (workspace), zero between launches
@@ -44,5 +45,24 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 // -1 for the kernel of levels with M^l < 4.
 const void *level_kernel_fp32(int payoff, int mt, bool split);
 const void *level_kernel_fp64(int payoff, int mt, bool split);
+
+// Batched rounds: one chunk of samples of one task (a level of one problem).
+struct BatchChunk {
+    uint64_t first;   // first sample of the chunk
+    uint32_t task;    // index into the task array
+    uint32_t count;   // samples in the chunk
+};
+// Chunks [begin, end) belong to one task; the header counts tasks and chunks of the round.
+struct BatchRange {
+    uint32_t begin, end;
+};
+struct BatchHeader {
+    uint32_t n_tasks, n_chunks;
+};
+// Persistent batch kernel and its fixed-order reduction, per precision and M specialisation
+// (mt = 4 or 0).
+const void *batch_kernel_fp32(int mt);
+const void *batch_kernel_fp64(int mt);
+const void *batch_reduce_kernel();
 
 }  // namespace mlmcgb

@@ -1,0 +1,43 @@
+// host.h -- host-side helpers shared by the C ABI translation units (defined in api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "engine.h"
+#include "mlmc.h"
+
+namespace mlmcgb {
+
+// Record a message for mlmc_last_error() on this host thread and return `code`.
+int fail(int code, const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return ::mlmcgb::fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));  \
+    } while (0)
+
+long ipow(long b, int e);
+int check_problem(const mlmc_model *model, const mlmc_payoff *payoff);
+int check_level(int level, int M);
+int check_tag(int tag);
+int device_sms(int *sms);
+int max_resident_blocks(const void *kernel, int threads, int *out);
+
+// Launch shape and kernel of one level.
+struct Plan {
+    const void *kernel;
+    int threads, lanes, blocks;
+};
+int plan_level(int level, int M, uint64_t N, int precision, int payoff, const mlmc_launch *launch,
+               Plan *plan);
+void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
+                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes);
+double level_cost(int level, int M);
+int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st);
+int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int precision);
+
+}  // namespace mlmcgb

@@ -6,4 +6,8 @@ const void *level_kernel_fp32(int payoff, int mt, bool split)
 {
     return select_level_kernel<float>(payoff, mt, split);
 }
+const void *batch_kernel_fp32(int mt)
+{
+    return select_batch_kernel<float>(mt);
+}
 }  // namespace mlmcgb

@@ -6,4 +6,8 @@ const void *level_kernel_fp64(int payoff, int mt, bool split)
 {
     return select_level_kernel<double>(payoff, mt, split);
 }
+const void *batch_kernel_fp64(int mt)
+{
+    return select_batch_kernel<double>(mt);
+}
 }  // namespace mlmcgb

@@ -254,85 +254,85 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
     lpost = pl;
 }
 
+// Y of sample s on a level with M^l >= 4, computed by the P lanes of one group (lane lig);
+// every lane of the group returns the same Y.
 template <typename R, int MT, int PAY, bool SPLIT>
-__global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
+__device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig, int P)
 {
-    const int P = SPLIT ? p.lanes : 1;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / P;
-    const uint64_t g = tid / P;
-    const uint64_t g_warp = (tid & ~uint64_t(31)) / P;  // first group of this warp
-    const int lig = SPLIT ? (int)(threadIdx.x % P) : 0;
+    const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
     const R S0 = R(p.S0);
     const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
-    double m[4] = {0.0, 0.0, 0.0, 0.0};
-    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
-    int nb = 0;
+    // Paths run relative to S0 (start value 1) and are scaled once per sample: the running sums
+    // then hold values of order one, which keeps the FP32 sums of many steps accurate.
+    PathAcc<R, PAY, SPLIT> fa, ca;
+    fa.init(R(1));
+    ca.init(R(1));
+    if constexpr (!SPLIT) {
+        simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
+        const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
+        const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
+                                          R(p.nf) * logS0 + fa.lsum, inv_nf, p);
+        const R Pc = payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
+                                          R(p.nf / p.M) * logS0 + ca.lsum, inv_nc, p);
+        return Pf - Pc;
+    } else {
+        const int calls = (p.nf >> 2) / P;
+        simulate_steps<R, MT, PAY, true>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+        const R steps_f = R(4 * calls);
+        R tf, pf, hf, lf, tc, pc, hc, lc;
+        join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
+        join_chunks<R, PAY>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
+        const R Pf = payoff_value<R, PAY>(tf, pf, hf, lf, inv_nf, p);
+        const R Pc = payoff_value<R, PAY>(tc, pc, hc, lc, inv_nc, p);
+        return Pf - Pc;
+    }
+}
 
-    for (uint64_t base = 0; base + g_warp < p.N; base += groups) {
+// Samples [first, first + N) of a level with M^l >= 4, shared by T threads of which this is
+// thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
+// Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
+// sample first + i into y_out[i] when y_out is not NULL.
+template <typename R, int MT, int PAY, bool SPLIT>
+__device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
+                                              uint64_t t, uint64_t T, double m[4], float &b1,
+                                              float &b2, float &b3, float &b4, int &nb,
+                                              double *y_out)
+{
+    const int P = SPLIT ? p.lanes : 1;
+    const uint64_t groups = T / P;
+    const uint64_t g = t / P;
+    const uint64_t g_warp = (t & ~uint64_t(31)) / P;  // first group of this warp
+    const int lig = SPLIT ? (int)(t % P) : 0;
+    for (uint64_t base = 0; base + g_warp < N; base += groups) {
         const uint64_t idx = base + g;
-        const bool valid = idx < p.N;
-        const uint64_t s = p.first + (valid ? idx : p.N - 1);
-        const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
-
-        // Paths run relative to S0 (start value 1) and are scaled once per sample: the running
-        // sums then hold values of order one, which keeps the FP32 sums of many steps accurate.
-        PathAcc<R, PAY, SPLIT> fa, ca;
-        fa.init(R(1));
-        ca.init(R(1));
-        R Y;
-        if constexpr (!SPLIT) {
-            simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
-            const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
-            const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
-                                              R(p.nf) * logS0 + fa.lsum, inv_nf, p);
-            const R Pc = p.level > 0
-                             ? payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
-                                                    R(p.nf / p.M) * logS0 + ca.lsum, inv_nc, p)
-                             : R(0);
-            Y = Pf - Pc;
-        } else {
-            const int calls = (p.nf >> 2) / P;
-            simulate_steps<R, MT, PAY, true>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
-            const R steps_f = R(4 * calls);
-            R tf, pf, hf, lf, tc, pc, hc, lc;
-            join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
-            join_chunks<R, PAY>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
-            const R Pf = payoff_value<R, PAY>(tf, pf, hf, lf, inv_nf, p);
-            const R Pc = payoff_value<R, PAY>(tc, pc, hc, lc, inv_nc, p);
-            Y = Pf - Pc;
-        }
+        const bool valid = idx < N;
+        const uint64_t s = first + (valid ? idx : N - 1);
+        const R Y = sample_Y<R, MT, PAY, SPLIT>(p, s, lig, P);
         if (valid && lig == 0) {
-            if (p.y_out) p.y_out[idx] = (double)Y;
+            if (y_out) y_out[idx] = (double)Y;
             add_moments(Y, m, b1, b2, b3, b4, nb);
         }
     }
-    if constexpr (sizeof(R) == 4) {
-        m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
-    }
-    finish_sums(m, p);
 }
 
-// Levels with M^l < 4 (level 0, and level 1 when M = 2).  G = 4 / M^l consecutive samples share
-// one Philox block: thread t takes block q = first / G + t (grid-stride) and the G samples
-// q G .. q G + G - 1 that fall in [first, first + N); sample slot r takes normals
-// r M^l .. r M^l + M^l - 1 of the block.
+// Samples [first, first + N) of a level with M^l < 4.  G = 4 / M^l consecutive samples share
+// one Philox block: thread t takes blocks q = first / G + t, + T, ... and the G samples
+// q G .. q G + G - 1 that fall in the range; sample slot r takes normals r M^l .. of the block.
 template <typename R, int PAY>
-__global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
+__device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first, uint64_t N,
+                                            uint64_t t, uint64_t T, double m[4], float &b1,
+                                            float &b2, float &b3, float &b4, int &nb,
+                                            double *y_out)
 {
     const int nf = p.nf;
     const uint32_t G = 4u / (uint32_t)nf;
-    const uint64_t end = p.first + p.N;
-    const uint64_t q0 = p.first / G;
+    const uint64_t end = first + N;
+    const uint64_t q0 = first / G;
     const uint64_t nq = (end - 1) / G - q0 + 1;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const R a = R(p.a), rh = R(p.rh), S0 = R(p.S0);
     const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
-    double m[4] = {0.0, 0.0, 0.0, 0.0};
-    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
-    int nb = 0;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += stride) {
-        const uint64_t q = q0 + t;
+    for (uint64_t u = t; u < nq; u += T) {
+        const uint64_t q = q0 + u;
         const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3),
                                       p.key0, p.key1);
         R rho, c, s, d[4];
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
         for (uint32_t r = 0; r < 4; ++r) {
             if (r >= G) break;
             const uint64_t sample = q * G + r;
-            if (sample < p.first || sample >= end) continue;
+            if (sample < first || sample >= end) continue;
             R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
             R cS = R(1), csum = R(0), chi = R(1), clo = R(1), cls = R(0);
             R Y;
@@ -367,14 +367,111 @@ __global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
                 const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
                 Y = Pf - Pc;
             }
-            if (p.y_out) p.y_out[sample - p.first] = (double)Y;
+            if (y_out) y_out[sample - first] = (double)Y;
             add_moments(Y, m, b1, b2, b3, b4, nb);
         }
     }
+}
+
+template <typename R>
+__device__ __forceinline__ void fold_batch(double m[4], float b1, float b2, float b3, float b4)
+{
     if constexpr (sizeof(R) == 4) {
         m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
     }
+}
+
+// One level, one thread (or P lanes) per sample, grid-stride over the samples.
+template <typename R, int MT, int PAY, bool SPLIT>
+__global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
+{
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
+    int nb = 0;
+    regular_range<R, MT, PAY, SPLIT>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                     (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
+    fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
+}
+
+// Levels with M^l < 4 (level 0, and level 1 when M = 2).
+template <typename R, int PAY>
+__global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
+{
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
+    int nb = 0;
+    small_range<R, PAY>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                        (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
+    fold_batch<R>(m, b1, b2, b3, b4);
+    finish_sums(m, p);
+}
+
+// ------------------------------------------------------------------ batched rounds
+
+// All samples of one chunk, by the threads of one block, on the code path of the chunk's task.
+template <typename R, int MT>
+__device__ __forceinline__ void batch_chunk(const LevelParams &p, uint64_t first, uint64_t count,
+                                            double m[4], float &b1, float &b2, float &b3, float &b4,
+                                            int &nb)
+{
+    const uint64_t t = threadIdx.x, T = blockDim.x;
+#define MLMC_BATCH_CASES(CALL)                                                                  \
+    switch (p.payoff) {                                                                         \
+    case kEuropean: CALL(kEuropean); break;                                                     \
+    case kAsian: CALL(kAsian); break;                                                           \
+    case kLookback: CALL(kLookback); break;                                                     \
+    case kDigital: CALL(kDigital); break;                                                       \
+    case kLinear: CALL(kLinear); break;                                                         \
+    case kGeoAsian: CALL(kGeoAsian); break;                                                     \
+    default: break;                                                                             \
+    }
+#define MLMC_SMALL(PAY) small_range<R, PAY>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+    if (p.small) {
+        MLMC_BATCH_CASES(MLMC_SMALL)
+    } else if (p.lanes > 1) {
+        MLMC_BATCH_CASES(MLMC_SPLIT)
+    } else {
+        MLMC_BATCH_CASES(MLMC_PLAIN)
+    }
+#undef MLMC_SMALL
+#undef MLMC_SPLIT
+#undef MLMC_PLAIN
+#undef MLMC_BATCH_CASES
+}
+
+// Persistent kernel of one batched round: each block claims chunks from `counter` until none
+// are left and writes the chunk's four power sums to chunk_sums[chunk].  A chunk is always
+// processed by one whole block with the same thread-to-sample mapping, so its sums do not
+// depend on which block claimed it.
+template <typename R, int MT>
+__global__ void __launch_bounds__(256) batch_kernel(const LevelParams *__restrict__ tasks,
+                                                    const BatchChunk *__restrict__ chunks,
+                                                    const BatchHeader *__restrict__ header,
+                                                    unsigned *counter, double *chunk_sums)
+{
+    __shared__ unsigned s_chunk;
+    const unsigned n_chunks = header->n_chunks;
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned c = s_chunk;
+        __syncthreads();
+        if (c >= n_chunks) break;
+        const BatchChunk ch = chunks[c];
+        double m[4] = {0.0, 0.0, 0.0, 0.0};
+        float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
+        int nb = 0;
+        batch_chunk<R, MT>(tasks[ch.task], ch.first, ch.count, m, b1, b2, b3, b4, nb);
+        fold_batch<R>(m, b1, b2, b3, b4);
+        block_sum4(m);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) chunk_sums[4 * (size_t)c + k] = m[k];
+        }
+    }
 }
 
 }  // namespace mlmcgb
@@ -409,6 +506,11 @@ template <typename R> const void *select_small_kernel(int payoff)
 }
 
 // mt = -1 selects the kernel of levels with M^l < 4.
+template <typename R> const void *select_batch_kernel(int mt)
+{
+    return mt == 4 ? (const void *)batch_kernel<R, 4> : (const void *)batch_kernel<R, 0>;
+}
+
 template <typename R> const void *select_level_kernel(int payoff, int mt, bool split)
 {
     if (mt < 0) return select_small_kernel<R>(payoff);

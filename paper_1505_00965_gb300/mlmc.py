@@ -53,6 +53,10 @@ class mlmc_launch(ctypes.Structure):
                 ("blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class mlmc_problem(ctypes.Structure):
+    _fields_ = [("model", mlmc_model), ("payoff", mlmc_payoff), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class mlmc_result(ctypes.Structure):
     _fields_ = [("P", ctypes.c_double), ("eps", ctypes.c_double), ("L", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -80,6 +84,7 @@ _SIGNATURES = {
     "mlmc_level_sums_async": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _sz, _vp, _vp],
                               _i32),
     "mlmc_level_sums_noalloc": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _vp], _i32),
+    "mlmc_estimate_batch": ([_i32, ctypes.c_void_p, _i32, _i32, _i32, _u64, _i32, _vp, ctypes.c_void_p], _i32),
     "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
@@ -228,6 +233,38 @@ class Estimate:
     d2h_bytes: int = 0
 
 
+def _estimate_from(st: int, r: mlmc_result) -> "Estimate":
+    L = r.L
+    return Estimate(status=st, P=r.P, eps=r.eps, L=L, converged=bool(r.converged), rounds=r.rounds,
+                    N=[int(r.N[l]) for l in range(L + 1)], sums=[list(r.sums[l]) for l in range(L + 1)],
+                    mean=[r.mean[l] for l in range(L + 1)], var=[r.var[l] for l in range(L + 1)],
+                    cost=[r.cost[l] for l in range(L + 1)], alpha=r.alpha, beta=r.beta, total_cost=r.total_cost,
+                    path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms, launches=int(r.launches),
+                    d2h_bytes=int(r.d2h_bytes))
+
+
+def mlmc_estimate_batch(problems, M: int = 4, Lmin: int = 2, Lmax: int = 8, N0: int = 10_000, precision="fp32",
+                        stream=None) -> list:
+    """Adaptive estimates of many problems together.  `problems` holds (Problem, eps, seed)
+    triples or dicts with the Problem fields plus eps and seed.  Returns one Estimate each
+    (status MLMC_ENOTCONV on those that reached Lmax first)."""
+    n = len(problems)
+    arr = (mlmc_problem * n)()
+    for i, q in enumerate(problems):
+        if isinstance(q, dict):
+            prob = Problem(**{k: q[k] for k in ("S0", "r", "sigma", "T", "payoff", "K", "cash") if k in q})
+            eps, seed = q["eps"], q["seed"]
+        else:
+            prob, eps, seed = q
+        arr[i] = mlmc_problem(prob.model(), prob.payoff_struct(), eps, seed)
+    res = (mlmc_result * n)()
+    st = _lib.mlmc_estimate_batch(n, ctypes.cast(arr, ctypes.c_void_p), M, Lmin, Lmax, N0, _prec(precision),
+                                  _addr(stream), ctypes.cast(res, ctypes.c_void_p))
+    if st not in (MLMC_OK, MLMC_ENOTCONV):
+        _check(st)
+    return [_estimate_from(MLMC_OK if res[i].converged else MLMC_ENOTCONV, res[i]) for i in range(n)]
+
+
 def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int = 2, Lmax: int = 8,
                   N0: int = 10_000, precision="fp32", stream=None) -> Estimate:
     """Adaptive estimate to RMS accuracy eps.  Returns the estimate also when Lmax was reached
@@ -238,10 +275,4 @@ def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int
                             _addr(stream), ctypes.byref(r))
     if st not in (MLMC_OK, MLMC_ENOTCONV):
         _check(st)
-    L = r.L
-    return Estimate(status=st, P=r.P, eps=r.eps, L=L, converged=bool(r.converged), rounds=r.rounds,
-                    N=[int(r.N[l]) for l in range(L + 1)], sums=[list(r.sums[l]) for l in range(L + 1)],
-                    mean=[r.mean[l] for l in range(L + 1)], var=[r.var[l] for l in range(L + 1)],
-                    cost=[r.cost[l] for l in range(L + 1)], alpha=r.alpha, beta=r.beta, total_cost=r.total_cost,
-                    path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms, launches=int(r.launches),
-                    d2h_bytes=int(r.d2h_bytes))
+    return _estimate_from(st, r)
