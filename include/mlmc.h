@@ -255,6 +255,101 @@ typedef struct mlmc_problem {
 int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, int Lmin, int Lmax, uint64_t N0,
                         int precision, void *stream, mlmc_result *results);
 
+/*
+ * ---------------------------------------------------------------- learned control variate
+ * A control variate replaces E[Y_l] by E[Y_l - g] + E[g] (Sec. 5 "Exploiting Structure":
+ * compute E[X - Y] and add E[Y]).  Here g is a network 8 -> 64 -> 64 -> 1 of the sample's
+ * Brownian path, trained per level on (inputs, Y_l) pairs the method itself generates:
+ *   x_k = (W(k T/8) - W((k-1) T/8)) / sqrt(T/8), k = 1..8 (iid N(0,1)); on levels with
+ *   M^l < 8 the T/8 grid is refined from the path's grid by Brownian-bridge midpoints taken from
+ *   Philox blocks 1 and 2 of the sample's counter;
+ *   g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3, GELU(z) = z/2 (1 + tanh(sqrt(2/pi)
+ *   (z + 0.044715 z^3))); products on the tensor cores with bfloat16 operands and FP32
+ *   accumulation (rounded: x, W1, W2, GELU(z1)); everything else FP32;
+ *   packed parameters (MLMC_CV_PARAMS floats): W1 [64][8] (row = output unit), b1 [64],
+ *   W2 [64][64], b2 [64], w3 [64], b3.
+ * The level estimator with the control variate is mean over N samples of (Y - g(x)) plus the
+ * mean of g over kappa N independent input samples (tag MLMC_TAG_CV_MEAN: eight fresh normals
+ * per sample), so it stays unbiased for any g.  A level uses it only while its measured
+ * work-weighted variance (Var(Y - g) + Var(g) / kappa) (t_cv + kappa t_mean) stays below
+ * Var(Y) t_plain; otherwise the plain estimator runs.  FP32 paths only.
+ */
+#define MLMC_CV_PARAMS 4801
+#define MLMC_CV_MAX_LEVELS 8
+typedef struct mlmc_cv mlmc_cv;   /* opaque; owns device memory */
+
+typedef struct mlmc_cv_options {
+    int32_t levels;        /* train levels 0 .. levels-1, 1..8 (0 = 4) */
+    int32_t epochs;        /* passes over the training set (0 = 20) */
+    int32_t batch;         /* mini-batch rows, a multiple of 256 (0 = 4096) */
+    int32_t reserved;      /* must be 0 */
+    uint64_t n_train;      /* samples per level (0 = 10^6); the last tenth is held out */
+    double lr;             /* Adam step size (0 = 1e-3) */
+    uint64_t init_seed;    /* seed of the initial weights */
+} mlmc_cv_options;
+
+typedef struct mlmc_cv_level_info {
+    int32_t trained;       /* 1 if this level has a network */
+    int32_t used;          /* 1 if the estimator uses the control variate on this level */
+    double var_plain;      /* Var(Y) on the held-out samples */
+    double var_resid;      /* Var(Y - g) on the held-out samples */
+    double var_g;          /* Var(g) on the held-out samples */
+    double kappa;          /* mean-sample ratio N' / N */
+    double t_plain, t_cv, t_mean;   /* measured seconds per sample of the three kernels */
+    double work_ratio;     /* (var_resid + var_g / kappa)(t_cv + kappa t_mean) / (var_plain t_plain) */
+    double train_loss;     /* final mean training loss (standardised targets) */
+} mlmc_cv_level_info;
+
+/* Create a control variate for one problem with no trained level (every level plain).
+ * M as mlmc_estimate; model, payoff host, read only.  *out receives the handle. */
+int mlmc_cv_create(int M, const mlmc_model *model, const mlmc_payoff *payoff, mlmc_cv **out);
+
+/* Train networks for levels 0 .. opts->levels - 1 (opts NULL = defaults) on samples drawn under
+ * tag MLMC_TAG_CV_TRAIN with `seed`, then measure each level's variance ratio and kernel costs
+ * and decide which levels use it.  Synchronises `stream`.  *out receives the handle. */
+int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
+                  const mlmc_cv_options *opts, void *stream, mlmc_cv **out);
+
+/* Release a handle (NULL is ignored). */
+int mlmc_cv_free(mlmc_cv *cv);
+
+/* Statistics of one level (host output). */
+int mlmc_cv_info(const mlmc_cv *cv, int level, mlmc_cv_level_info *out);
+
+/* Read / install the packed FP32 parameters of one level (host arrays of MLMC_CV_PARAMS).
+ * Installing marks the level trained and used (the statistics are left at zero). */
+int mlmc_cv_get_params(const mlmc_cv *cv, int level, float *params);
+int mlmc_cv_set_params(mlmc_cv *cv, int level, const float *params, double kappa);
+
+/* Control-variate level sums over samples [first, first + N) of `level` (tag MLMC_TAG_PATHS):
+ * d_sums8 device, 8 doubles: sum r, r^2, r^3, r^4 (r = Y - g(x)), sum Y, Y^2, sum g, g^2.
+ * d_r, d_g device or NULL: per-sample r and g (float).  Synchronises `stream`. */
+int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
+                       double *d_sums8, float *d_r, float *d_g, void *stream);
+
+/* Sums of g over the independent mean sample [first, first + N) of `level`:
+ * d_sums2 device, 2 doubles (sum g, sum g^2); d_g device or NULL.  Synchronises `stream`. */
+int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
+                      double *d_sums2, float *d_g, void *stream);
+
+/* Training data of `level`: d_X device [N][8] network inputs, d_Y device [N] Y values, for
+ * samples [first, first + N) under tag MLMC_TAG_CV_TRAIN.  Synchronises `stream`. */
+int mlmc_cv_training_data(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
+                          float *d_X, float *d_Y, void *stream);
+
+/* The network on given inputs: params host [MLMC_CV_PARAMS]; d_X device [N][8]; d_G device [N].
+ * mlmc_mlp_grad: loss (1/N) sum (g - Y)^2 and its gradient (host outputs) for rows d_X, d_Y
+ * (device); N a multiple of 32, at most 65536.  Both synchronise `stream`. */
+int mlmc_mlp_forward(const float *params, const float *d_X, uint64_t N, float *d_G, void *stream);
+int mlmc_mlp_grad(const float *params, const float *d_X, const float *d_Y, uint64_t N, float *grad,
+                  double *loss, void *stream);
+
+/* mlmc_estimate with the control variate on the levels `cv` uses (FP32 paths; the problem must be
+ * the one cv was made for).  Level means are mean(Y - g) + mean'(g) on those levels. */
+int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc_model *model,
+                     const mlmc_payoff *payoff, uint64_t seed, const mlmc_cv *cv, void *stream,
+                     mlmc_result *out);
+
 /* Number of streaming multiprocessors of the current device, or -1 with an error message. */
 int mlmc_device_sm_count(void);
 

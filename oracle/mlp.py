@@ -1,0 +1,123 @@
+"""FP64 oracle of the learned control variate (TEST INFRASTRUCTURE ONLY).
+
+A control variate replaces E[Y] by E[Y - g] + E[g] (the control-variate remark of Sec. 5:
+compute E[X - Y] and add E[Y]).  Here g is a small network of the sample's Brownian path:
+
+* inputs x_k = (W(k T / 8) - W((k - 1) T / 8)) / sqrt(T / 8), k = 1..8, the standardised
+  increments of the path on the T/8 grid (iid N(0, 1) whatever the level);
+* g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3, widths 8 -> 64 -> 64 -> 1, with
+  GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
+* parameters packed as W1 [64][8] (row = output unit), b1 [64], W2 [64][64], b2 [64],
+  w3 [64], b3 [1]: 4801 numbers;
+* training loss: the mean of (g(x) - Y)^2 over a batch.
+
+`quantize=True` rounds to bfloat16 (round to nearest, ties to even) the operands of the
+tensor-core products the GPU path uses: x, W1, W2 and the layer-2 input GELU(z1).  All other
+arithmetic here is FP64.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import TAG_CV_MEAN, grid_brownian, normals
+
+H = 64
+D = 8
+N_PARAMS = H * D + H + H * H + H + H + 1
+SQRT_2_OVER_PI = math.sqrt(2.0 / math.pi)
+GELU_C = 0.044715
+
+
+def unpack(theta: np.ndarray):
+    theta = np.asarray(theta, dtype=np.float64)
+    assert theta.shape == (N_PARAMS,)
+    o = 0
+    W1 = theta[o:o + H * D].reshape(H, D); o += H * D
+    b1 = theta[o:o + H]; o += H
+    W2 = theta[o:o + H * H].reshape(H, H); o += H * H
+    b2 = theta[o:o + H]; o += H
+    w3 = theta[o:o + H]; o += H
+    b3 = theta[o]
+    return W1, b1, W2, b2, w3, b3
+
+
+def pack(W1, b1, W2, b2, w3, b3) -> np.ndarray:
+    return np.concatenate([np.ravel(W1), b1, np.ravel(W2), b2, w3, [b3]]).astype(np.float64)
+
+
+def bf16(a) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as FP64 values."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + np.tanh(SQRT_2_OVER_PI * (z + GELU_C * z ** 3)))
+
+
+def gelu_grad(z):
+    t = np.tanh(SQRT_2_OVER_PI * (z + GELU_C * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * SQRT_2_OVER_PI * (1.0 + 3.0 * GELU_C * z * z)
+
+
+def forward(theta, X, quantize: bool = False):
+    """g(x) for the rows of X [B, 8], and the layer values (z1, h1, z2, h2)."""
+    W1, b1, W2, b2, w3, b3 = unpack(theta)
+    X = np.asarray(X, dtype=np.float64)
+    if quantize:
+        X, W1, W2 = bf16(X), bf16(W1), bf16(W2)
+    z1 = X @ W1.T + b1
+    h1 = gelu(z1)
+    h1_in = bf16(h1) if quantize else h1
+    z2 = h1_in @ W2.T + b2
+    h2 = gelu(z2)
+    g = h2 @ w3 + b3
+    return g, (X, z1, h1_in, z2, h2)
+
+
+def loss_and_grad(theta, X, Y, quantize: bool = False):
+    """Mean squared error of g against Y and its gradient with respect to theta (chain rule)."""
+    W1, b1, W2, b2, w3, b3 = unpack(theta)
+    if quantize:
+        W2 = bf16(W2)
+    g, (Xq, z1, h1, z2, h2) = forward(theta, X, quantize)
+    B = len(Y)
+    r = g - np.asarray(Y, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    d = 2.0 * r / B                       # dL/dg
+    db3 = d.sum()
+    dw3 = h2.T @ d
+    dz2 = np.outer(d, w3) * gelu_grad(z2)
+    dW2 = dz2.T @ h1
+    db2 = dz2.sum(axis=0)
+    dz1 = (dz2 @ W2) * gelu_grad(z1)
+    dW1 = dz1.T @ Xq
+    db1 = dz1.sum(axis=0)
+    return loss, pack(dW1, db1, dW2, db2, dw3, db3)
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Seeded initial parameters: weights uniform in +-1/sqrt(fan-in), biases zero."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.uniform(-1, 1, (H, D)) / math.sqrt(D)
+    W2 = rng.uniform(-1, 1, (H, H)) / math.sqrt(H)
+    w3 = rng.uniform(-1, 1, H) / math.sqrt(H)
+    return pack(W1, np.zeros(H), W2, np.zeros(H), w3, 0.0)
+
+
+def features(level: int, M: int, s: int, T: float, seed: int, stream: str = "fp64", tag: int = 0) -> np.ndarray:
+    """The 8 standardised T/8-grid increments of sample s (from the oracle's Brownian grid)."""
+    W = grid_brownian(level, M, s, T, seed, stream=stream, tag=tag)
+    inc = np.diff(np.concatenate([[0.0], W]))
+    return inc / math.sqrt(T / 8.0)
+
+
+def mean_sample_features(s: int, seed: int, level: int, stream: str = "fp64") -> np.ndarray:
+    """Features of sample s of the independent sample that estimates E[g]: eight stream normals
+    (blocks 0 and 1 of counter s under the control-variate-mean tag)."""
+    return normals(seed, level, s, 8, stream=stream, tag=TAG_CV_MEAN)

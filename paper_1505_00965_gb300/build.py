@@ -15,8 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmlmc_gb300.so")
-SOURCES = ["api.cu", "batch.cu", "level_fp32.cu", "level_fp64.cu"]
-HEADERS = ["driver.h", "engine.h", "host.h", "level_kernel.cuh", "rng.cuh"]
+SOURCES = ["api.cu", "batch.cu", "cv.cu", "level_fp32.cu", "level_fp64.cu"]
+HEADERS = ["cv_kernels.cuh", "driver.h", "engine.h", "host.h", "level_kernel.cuh", "mlp.cuh", "rng.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),

@@ -164,6 +164,8 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     const double h = m->T / (double)nf;
     p.small = nf < 4 ? 1 : 0;
     p.a = m->sigma * std::sqrt(h);
+    p.sqrt_h = std::sqrt(h);
+    p.sqrt_t8 = std::sqrt(m->T / 8.0);
     p.rh = m->r * h;
     p.inv_nf = 1.0 / (double)nf;
     p.inv_nc = level > 0 ? (double)M / (double)nf : 0.0;

@@ -1,0 +1,698 @@
+// cv.cu -- the learned control variate: training on the GPU, the control-variate level and mean
+// estimators, and the adaptive driver that uses them (host side of the C ABI).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cv_kernels.cuh"
+#include "driver.h"
+#include "engine.h"
+#include "host.h"
+#include "mlmc.h"
+
+using namespace mlmcgb;
+
+struct mlmc_cv {
+    int M;
+    mlmc_model model;
+    mlmc_payoff payoff;
+    int device;
+    float *d_params[MLMC_CV_MAX_LEVELS];
+    float h_params[MLMC_CV_MAX_LEVELS][kNumParams];
+    mlmc_cv_level_info info[MLMC_CV_MAX_LEVELS];
+};
+
+namespace {
+
+constexpr int kCvThreads = 256;
+
+const void *cv_level_kernel_for(int payoff)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)cv_level_kernel<kEuropean>;
+    case kAsian: return (const void *)cv_level_kernel<kAsian>;
+    case kLookback: return (const void *)cv_level_kernel<kLookback>;
+    case kDigital: return (const void *)cv_level_kernel<kDigital>;
+    case kLinear: return (const void *)cv_level_kernel<kLinear>;
+    case kGeoAsian: return (const void *)cv_level_kernel<kGeoAsian>;
+    default: return nullptr;
+    }
+}
+
+const void *cv_data_kernel_for(int payoff)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)cv_data_kernel<kEuropean>;
+    case kAsian: return (const void *)cv_data_kernel<kAsian>;
+    case kLookback: return (const void *)cv_data_kernel<kLookback>;
+    case kDigital: return (const void *)cv_data_kernel<kDigital>;
+    case kLinear: return (const void *)cv_data_kernel<kLinear>;
+    case kGeoAsian: return (const void *)cv_data_kernel<kGeoAsian>;
+    default: return nullptr;
+    }
+}
+
+int grid_for(const void *kernel, uint64_t items, int *blocks)
+{
+    int resident = 0;
+    int rc = max_resident_blocks(kernel, kCvThreads, &resident);
+    if (rc) return rc;
+    const double need = std::ceil((double)std::max<uint64_t>(items, 1) / kCvThreads);
+    *blocks = (int)std::max(1.0, std::min<double>(need, resident));
+    return MLMC_OK;
+}
+
+// Workspace for a kernel that sums NV doubles: ticket word (256 bytes) then NV per block.
+size_t sums_workspace(int blocks, int nv) { return kTicketBytes + (size_t)blocks * nv * sizeof(double); }
+
+int check_cv_level(const mlmc_cv *cv, int level)
+{
+    if (!cv) return fail(MLMC_EINVAL, "cv must not be NULL");
+    if (level < 0 || level >= MLMC_CV_MAX_LEVELS) return fail(MLMC_EINVAL, "level %d outside 0..%d", level,
+                                                              MLMC_CV_MAX_LEVELS - 1);
+    return MLMC_OK;
+}
+
+int check_trained(const mlmc_cv *cv, int level)
+{
+    int rc = check_cv_level(cv, level);
+    if (rc) return rc;
+    if (!cv->d_params[level]) return fail(MLMC_EINVAL, "level %d has no network", level);
+    return MLMC_OK;
+}
+
+// Launch the control-variate level kernel; ws holds sums_workspace(blocks, 8) bytes with a zero
+// ticket.
+int launch_cv_level(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums8,
+                    float *d_r, float *d_g, void *ws, int blocks, cudaStream_t st)
+{
+    LevelParams p;
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_PATHS, 1);
+    p.ticket = (unsigned *)ws;
+    p.partials = (double *)((char *)ws + kTicketBytes);
+    const float *params = cv->d_params[level];
+    void *args[] = {&p, (void *)&params, &d_sums8, &d_r, &d_g};
+    CUDA_TRY(cudaLaunchKernel(cv_level_kernel_for(cv->payoff.kind), dim3(blocks), dim3(kCvThreads), args, 0, st));
+    return MLMC_OK;
+}
+
+int launch_cv_mean(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums2,
+                   float *d_g, void *ws, int blocks, cudaStream_t st)
+{
+    LevelParams p;
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_MEAN, 1);
+    p.ticket = (unsigned *)ws;
+    p.partials = (double *)((char *)ws + kTicketBytes);
+    const float *params = cv->d_params[level];
+    void *args[] = {&p, (void *)&params, &d_sums2, &d_g};
+    CUDA_TRY(cudaLaunchKernel((const void *)cv_mean_kernel, dim3(blocks), dim3(kCvThreads), args, 0, st));
+    return MLMC_OK;
+}
+
+// Run `body(ws)` with a zeroed stream-ordered workspace of `bytes`, then synchronise.
+template <class F> int with_workspace(size_t bytes, cudaStream_t st, F body)
+{
+    void *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync(&ws, bytes, st));
+    cudaError_t e = cudaMemsetAsync(ws, 0, bytes, st);
+    int rc = e == cudaSuccess ? body(ws) : fail(MLMC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    cudaFreeAsync(ws, st);
+    e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = fail(MLMC_ECUDA, "control-variate kernel failed: %s", cudaGetErrorString(e));
+    return rc;
+}
+
+// Initial weights: uniform in +-1/sqrt(fan-in) from a splitmix64 sequence; biases zero.
+void init_params(float *w, uint64_t seed)
+{
+    uint64_t state = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    auto next = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1p-53 * 2.0 - 1.0;
+    };
+    std::fill(w, w + kNumParams, 0.f);
+    for (int i = 0; i < kHidden * kInputs; ++i) w[kOffW1 + i] = (float)(next() / std::sqrt((double)kInputs));
+    for (int i = 0; i < kHidden * kHidden; ++i) w[kOffW2 + i] = (float)(next() / std::sqrt((double)kHidden));
+    for (int i = 0; i < kHidden; ++i) w[kOffW3 + i] = (float)(next() / std::sqrt((double)kHidden));
+}
+
+struct TrainBuffers {
+    float *Z1 = nullptr, *Z2 = nullptr, *DZ1 = nullptr, *DZ2 = nullptr, *H1 = nullptr, *H2 = nullptr;
+    float *G = nullptr, *D = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *params = nullptr;
+    unsigned *step = nullptr;
+    int alloc(int B)
+    {
+        const size_t act = (size_t)B * kHidden * sizeof(float);
+        for (float **b : {&Z1, &Z2, &DZ1, &DZ2, &H1, &H2}) CUDA_TRY(cudaMalloc(b, act));
+        CUDA_TRY(cudaMalloc(&G, B * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&D, B * sizeof(float)));
+        for (float **b : {&grad, &m1, &m2, &params}) CUDA_TRY(cudaMalloc(b, kNumParams * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&step, sizeof(unsigned)));
+        return MLMC_OK;
+    }
+    void release()
+    {
+        for (float *b : {Z1, Z2, DZ1, DZ2, H1, H2, G, D, grad, m1, m2, params})
+            if (b) cudaFree(b);
+        if (step) cudaFree(step);
+        *this = TrainBuffers();
+    }
+};
+
+// Queue one training step (forward, backward, gradient, Adam) on rows [off, off + B).
+int queue_step(TrainBuffers &tb, const float *X, const float *Y, uint64_t off, int B, float mu, float inv_sd,
+               float lr, cudaStream_t st, bool update)
+{
+    const float *cparams = tb.params;
+    void *fargs[] = {(void *)&cparams, (void *)&X, &off, &B, &tb.Z1, &tb.Z2, &tb.G, &tb.step};
+    CUDA_TRY(cudaLaunchKernel((const void *)train_forward_kernel, dim3((B + 255) / 256), dim3(256), fargs, 0, st));
+    void *bargs[] = {(void *)&cparams, (void *)&Y, &off, &B, &mu, &inv_sd, &tb.Z1, &tb.Z2, &tb.G,
+                     &tb.D, &tb.DZ1, &tb.DZ2, &tb.H1, &tb.H2};
+    CUDA_TRY(cudaLaunchKernel((const void *)train_backward_kernel, dim3((B + 127) / 128), dim3(128), bargs, 0, st));
+    void *gargs[] = {(void *)&X, &off, &B, &tb.D, &tb.DZ1, &tb.DZ2, &tb.H1, &tb.H2, &tb.grad};
+    CUDA_TRY(cudaLaunchKernel((const void *)train_grad_kernel, dim3((kNumParams + 255) / 256), dim3(256), gargs, 0,
+                              st));
+    if (update) {
+        void *aargs[] = {&tb.params, &tb.grad, &tb.m1, &tb.m2, &tb.step, &lr};
+        CUDA_TRY(cudaLaunchKernel((const void *)adam_kernel, dim3((kNumParams + 255) / 256), dim3(256), aargs, 0,
+                                  st));
+    }
+    return MLMC_OK;
+}
+
+double seconds_per_sample(cudaEvent_t a, cudaEvent_t b, uint64_t n)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms * 1e-3 / (double)n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlmc_cv_create(int M, const mlmc_model *model, const mlmc_payoff *payoff, mlmc_cv **out)
+{
+    int rc = check_problem(model, payoff);
+    if (rc) return rc;
+    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
+    if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
+    mlmc_cv *cv = new (std::nothrow) mlmc_cv();
+    if (!cv) return fail(MLMC_ENOMEM, "cannot allocate the control-variate handle");
+    cv->M = M;
+    cv->model = *model;
+    cv->payoff = *payoff;
+    cudaError_t e = cudaGetDevice(&cv->device);
+    if (e != cudaSuccess) {
+        delete cv;
+        return fail(MLMC_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+    }
+    *out = cv;
+    return MLMC_OK;
+}
+
+int mlmc_cv_free(mlmc_cv *cv)
+{
+    if (!cv) return MLMC_OK;
+    for (int l = 0; l < MLMC_CV_MAX_LEVELS; ++l)
+        if (cv->d_params[l]) cudaFree(cv->d_params[l]);
+    delete cv;
+    return MLMC_OK;
+}
+
+int mlmc_cv_info(const mlmc_cv *cv, int level, mlmc_cv_level_info *out)
+{
+    int rc = check_cv_level(cv, level);
+    if (rc) return rc;
+    if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
+    *out = cv->info[level];
+    return MLMC_OK;
+}
+
+int mlmc_cv_get_params(const mlmc_cv *cv, int level, float *params)
+{
+    int rc = check_trained(cv, level);
+    if (rc) return rc;
+    if (!params) return fail(MLMC_EINVAL, "params must not be NULL");
+    std::memcpy(params, cv->h_params[level], sizeof(float) * kNumParams);
+    return MLMC_OK;
+}
+
+int mlmc_cv_set_params(mlmc_cv *cv, int level, const float *params, double kappa)
+{
+    int rc = check_cv_level(cv, level);
+    if (rc) return rc;
+    if (!params) return fail(MLMC_EINVAL, "params must not be NULL");
+    if (!(kappa >= 1.0 && kappa <= 4096.0)) return fail(MLMC_EINVAL, "kappa must lie in [1, 4096]");
+    if (!cv->d_params[level]) CUDA_TRY(cudaMalloc(&cv->d_params[level], sizeof(float) * kNumParams));
+    CUDA_TRY(cudaMemcpy(cv->d_params[level], params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+    std::memcpy(cv->h_params[level], params, sizeof(float) * kNumParams);
+    cv->info[level] = mlmc_cv_level_info();
+    cv->info[level].trained = 1;
+    cv->info[level].used = 1;
+    cv->info[level].kappa = kappa;
+    return MLMC_OK;
+}
+
+int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums8,
+                       float *d_r, float *d_g, void *stream)
+{
+    int rc = check_trained(cv, level);
+    if (rc) return rc;
+    if (!d_sums8) return fail(MLMC_EINVAL, "d_sums8 must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0) {
+        CUDA_TRY(cudaMemsetAsync(d_sums8, 0, 8 * sizeof(double), st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return MLMC_OK;
+    }
+    int blocks = 0;
+    rc = grid_for(cv_level_kernel_for(cv->payoff.kind), N, &blocks);
+    if (rc) return rc;
+    return with_workspace(sums_workspace(blocks, 8), st, [&](void *ws) {
+        return launch_cv_level(cv, level, N, first, seed, d_sums8, d_r, d_g, ws, blocks, st);
+    });
+}
+
+int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums2,
+                      float *d_g, void *stream)
+{
+    int rc = check_trained(cv, level);
+    if (rc) return rc;
+    if (!d_sums2) return fail(MLMC_EINVAL, "d_sums2 must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0) {
+        CUDA_TRY(cudaMemsetAsync(d_sums2, 0, 2 * sizeof(double), st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return MLMC_OK;
+    }
+    int blocks = 0;
+    rc = grid_for((const void *)cv_mean_kernel, N, &blocks);
+    if (rc) return rc;
+    return with_workspace(sums_workspace(blocks, 2), st, [&](void *ws) {
+        return launch_cv_mean(cv, level, N, first, seed, d_sums2, d_g, ws, blocks, st);
+    });
+}
+
+int mlmc_cv_training_data(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, float *d_X,
+                          float *d_Y, void *stream)
+{
+    int rc = check_cv_level(cv, level);
+    if (rc) return rc;
+    if (!d_X || !d_Y) return fail(MLMC_EINVAL, "d_X and d_Y must not be NULL");
+    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    if (ipow(cv->M, level) > (1L << 24)) return fail(MLMC_EINVAL, "level %d too deep", level);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0) return MLMC_OK;
+    const void *k = cv_data_kernel_for(cv->payoff.kind);
+    int blocks = 0;
+    rc = grid_for(k, N, &blocks);
+    if (rc) return rc;
+    LevelParams p;
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_TRAIN, 1);
+    void *args[] = {&p, &d_X, &d_Y};
+    CUDA_TRY(cudaLaunchKernel(k, dim3(blocks), dim3(kCvThreads), args, 0, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MLMC_OK;
+}
+
+int mlmc_mlp_forward(const float *params, const float *d_X, uint64_t N, float *d_G, void *stream)
+{
+    if (!params || !d_X || !d_G) return fail(MLMC_EINVAL, "params, d_X and d_G must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0) return MLMC_OK;
+    int blocks = 0;
+    int rc = grid_for((const void *)mlp_forward_kernel, N, &blocks);
+    if (rc) return rc;
+    float *d_params = nullptr;
+    CUDA_TRY(cudaMallocAsync(&d_params, sizeof(float) * kNumParams, st));
+    cudaError_t e = cudaMemcpyAsync(d_params, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, st);
+    const float *cp = d_params;
+    void *args[] = {(void *)&cp, (void *)&d_X, &N, &d_G};
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)mlp_forward_kernel, dim3(blocks), dim3(kCvThreads), args, 0, st);
+    cudaFreeAsync(d_params, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(MLMC_ECUDA, "network forward failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return MLMC_OK;
+}
+
+int mlmc_mlp_grad(const float *params, const float *d_X, const float *d_Y, uint64_t N, float *grad, double *loss,
+                  void *stream)
+{
+    if (!params || !d_X || !d_Y || !grad || !loss) return fail(MLMC_EINVAL, "NULL argument");
+    if (N == 0 || N % 32 || N > 65536) return fail(MLMC_EINVAL, "N must be a positive multiple of 32, at most 65536");
+    cudaStream_t st = (cudaStream_t)stream;
+    TrainBuffers tb;
+    int rc = tb.alloc((int)N);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(tb.params, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tb.step, 0, sizeof(unsigned), st);
+        rc = e == cudaSuccess ? queue_step(tb, d_X, d_Y, 0, (int)N, 0.f, 1.f, 0.f, st, false)
+                              : fail(MLMC_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+    }
+    std::vector<float> g(N), y(N);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(grad, tb.grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), tb.G, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(y.data(), d_Y, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(MLMC_ECUDA, "network gradient failed: %s", cudaGetErrorString(e));
+    }
+    tb.release();
+    if (rc) return rc;
+    double acc = 0.0;
+    for (uint64_t i = 0; i < N; ++i) acc += ((double)g[i] - y[i]) * ((double)g[i] - y[i]);
+    *loss = acc / (double)N;
+    return MLMC_OK;
+}
+
+int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
+                  const mlmc_cv_options *opts, void *stream, mlmc_cv **out)
+{
+    if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
+    mlmc_cv_options o = opts ? *opts : mlmc_cv_options();
+    if (o.reserved != 0) return fail(MLMC_EINVAL, "mlmc_cv_options.reserved must be 0");
+    const int levels = o.levels ? o.levels : 4;
+    const int epochs = o.epochs ? o.epochs : 20;
+    const int B = o.batch ? o.batch : 4096;
+    const uint64_t n_train = o.n_train ? o.n_train : 1000000;
+    const float lr = (float)(o.lr > 0 ? o.lr : 1e-3);
+    if (levels < 1 || levels > MLMC_CV_MAX_LEVELS) return fail(MLMC_EINVAL, "levels must be 1..%d", MLMC_CV_MAX_LEVELS);
+    if (epochs < 1 || B < 256 || B % 256 || B > 65536) return fail(MLMC_EINVAL, "need epochs >= 1 and batch a multiple of 256 up to 65536");
+    const uint64_t n_fit = n_train / 10 * 9, n_val = n_train - n_fit;
+    if (n_fit < (uint64_t)B || n_val < 256) return fail(MLMC_EINVAL, "n_train too small for the batch size");
+    if (ipow(M, levels - 1) > (1L << 16)) return fail(MLMC_EINVAL, "levels too deep for training");
+    mlmc_cv *cv = nullptr;
+    int rc = mlmc_cv_create(M, model, payoff, &cv);
+    if (rc) return rc;
+    // training runs on a private stream (graph capture needs one) once `stream` has drained
+    cudaStream_t st = nullptr;
+    {
+        cudaError_t e0 = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e0 == cudaSuccess) e0 = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e0 != cudaSuccess) {
+            mlmc_cv_free(cv);
+            return fail(MLMC_ECUDA, "training stream: %s", cudaGetErrorString(e0));
+        }
+    }
+    float *d_X = nullptr, *d_Y = nullptr, *d_Gv = nullptr;
+    TrainBuffers tb;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&](int code) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        if (d_X) cudaFree(d_X);
+        if (d_Y) cudaFree(d_Y);
+        if (d_Gv) cudaFree(d_Gv);
+        tb.release();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (st) cudaStreamDestroy(st);
+        st = nullptr;
+        if (code) mlmc_cv_free(cv);
+        return code;
+    };
+#define CV_TRY(expr)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess) return cleanup(fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_))); \
+    } while (0)
+    CV_TRY(cudaMalloc(&d_X, sizeof(float) * 8 * n_train));
+    CV_TRY(cudaMalloc(&d_Y, sizeof(float) * n_train));
+    CV_TRY(cudaMalloc(&d_Gv, sizeof(float) * n_train));
+    CV_TRY(cudaEventCreate(&ev0));
+    CV_TRY(cudaEventCreate(&ev1));
+    rc = tb.alloc(B);
+    if (rc) return cleanup(rc);
+    std::vector<float> hY(n_train), hG(n_val);
+    for (int l = 0; l < levels; ++l) {
+        // 1. training data from the method itself (independent tag)
+        rc = mlmc_cv_training_data(cv, l, n_train, 0, seed, d_X, d_Y, st);
+        if (rc) return cleanup(rc);
+        CV_TRY(cudaMemcpy(hY.data(), d_Y, sizeof(float) * n_train, cudaMemcpyDeviceToHost));
+        double mu = 0.0, m2 = 0.0;
+        for (uint64_t i = 0; i < n_fit; ++i) mu += hY[i];
+        mu /= (double)n_fit;
+        for (uint64_t i = 0; i < n_fit; ++i) m2 += (hY[i] - mu) * (hY[i] - mu);
+        const double sd = std::sqrt(std::max(m2 / (double)n_fit, 1e-300));
+        // 2. initial weights, Adam state
+        float w[kNumParams];
+        init_params(w, o.init_seed + 7919ull * (uint64_t)l);
+        CV_TRY(cudaMemcpy(tb.params, w, sizeof(w), cudaMemcpyHostToDevice));
+        CV_TRY(cudaMemset(tb.m1, 0, sizeof(float) * kNumParams));
+        CV_TRY(cudaMemset(tb.m2, 0, sizeof(float) * kNumParams));
+        CV_TRY(cudaMemset(tb.step, 0, sizeof(unsigned)));
+        // 3. one epoch of steps captured once, replayed `epochs` times
+        const uint64_t steps = n_fit / B;
+        CV_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (uint64_t s = 0; s < steps && !rc; ++s)
+            rc = queue_step(tb, d_X, d_Y, s * B, B, (float)mu, (float)(1.0 / sd), lr, st, true);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (rc) return cleanup(rc);
+        CV_TRY(ce);
+        CV_TRY(cudaGraphInstantiate(&exec, graph, 0));
+        for (int ep = 0; ep < epochs; ++ep) CV_TRY(cudaGraphLaunch(exec, st));
+        CV_TRY(cudaStreamSynchronize(st));
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        // 4. undo the target standardisation in the last layer: g = sd * net + mu
+        CV_TRY(cudaMemcpy(w, tb.params, sizeof(w), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < kHidden; ++i) w[kOffW3 + i] = (float)(w[kOffW3 + i] * sd);
+        w[kOffB3] = (float)(w[kOffB3] * sd + mu);
+        rc = mlmc_cv_set_params(cv, l, w, 1.0);
+        if (rc) return cleanup(rc);
+        // 5. held-out variance ratio
+        rc = mlmc_mlp_forward(w, d_X + 8 * n_fit, n_val, d_Gv, st);
+        if (rc) return cleanup(rc);
+        CV_TRY(cudaMemcpy(hG.data(), d_Gv, sizeof(float) * n_val, cudaMemcpyDeviceToHost));
+        double sy = 0, syy = 0, sr = 0, srr = 0, sg = 0, sgg = 0;
+        for (uint64_t i = 0; i < n_val; ++i) {
+            const double y = hY[n_fit + i], g = hG[i], r = y - g;
+            sy += y; syy += y * y; sr += r; srr += r * r; sg += g; sgg += g * g;
+        }
+        const double nv = (double)n_val;
+        mlmc_cv_level_info &inf = cv->info[l];
+        inf.var_plain = std::max(syy / nv - (sy / nv) * (sy / nv), 0.0);
+        inf.var_resid = std::max(srr / nv - (sr / nv) * (sr / nv), 0.0);
+        inf.var_g = std::max(sgg / nv - (sg / nv) * (sg / nv), 0.0);
+        inf.train_loss = inf.var_resid / (sd * sd);
+        // 6. measured cost per sample of the plain, control-variate and mean kernels
+        const uint64_t nt = std::max<uint64_t>(1u << 14, (uint64_t)(1u << 22) >> std::min(2 * l, 20));
+        {
+            Plan plan;
+            rc = plan_level(l, M, nt, MLMC_FP32_PATH, payoff->kind, nullptr, &plan);
+            if (rc) return cleanup(rc);
+            int cvb = 0, mb = 0;
+            rc = grid_for(cv_level_kernel_for(payoff->kind), nt, &cvb);
+            if (!rc) rc = grid_for((const void *)cv_mean_kernel, nt, &mb);
+            if (rc) return cleanup(rc);
+            const int wb = std::max(std::max(plan.blocks, cvb), mb);
+            double *d_out = nullptr;
+            CV_TRY(cudaMalloc(&d_out, 16 * sizeof(double)));
+            rc = with_workspace(sums_workspace(wb, 8), st, [&](void *ws) {
+                for (int rep = 0; rep < 2; ++rep) {  // first pass warms up, second is timed
+                    LevelParams p;
+                    fill_params(p, l, M, nt, 0, model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+                    p.out = d_out;
+                    CUDA_TRY(cudaEventRecord(ev0, st));
+                    int r2 = launch_level(plan, p, ws, st);
+                    if (r2) return r2;
+                    CUDA_TRY(cudaEventRecord(ev1, st));
+                    CUDA_TRY(cudaEventSynchronize(ev1));
+                    inf.t_plain = seconds_per_sample(ev0, ev1, nt);
+                    CUDA_TRY(cudaEventRecord(ev0, st));
+                    r2 = launch_cv_level(cv, l, nt, 0, seed, d_out, nullptr, nullptr, ws, cvb, st);
+                    if (r2) return r2;
+                    CUDA_TRY(cudaEventRecord(ev1, st));
+                    CUDA_TRY(cudaEventSynchronize(ev1));
+                    inf.t_cv = seconds_per_sample(ev0, ev1, nt);
+                    CUDA_TRY(cudaEventRecord(ev0, st));
+                    r2 = launch_cv_mean(cv, l, nt, 0, seed, d_out + 8, nullptr, ws, mb, st);
+                    if (r2) return r2;
+                    CUDA_TRY(cudaEventRecord(ev1, st));
+                    CUDA_TRY(cudaEventSynchronize(ev1));
+                    inf.t_mean = seconds_per_sample(ev0, ev1, nt);
+                }
+                return (int)MLMC_OK;
+            });
+            cudaFree(d_out);
+            if (rc) return cleanup(rc);
+        }
+        // 7. mean-sample ratio minimising (Vr + Vg / k)(t_cv + k t_mean), and the decision
+        const double vr = std::max(inf.var_resid, 1e-300);
+        double kappa = std::sqrt(inf.var_g * inf.t_cv / (vr * std::max(inf.t_mean, 1e-15)));
+        kappa = std::min(std::max(kappa, 1.0), 4096.0);
+        inf.kappa = kappa;
+        inf.work_ratio = (inf.var_resid + inf.var_g / kappa) * (inf.t_cv + kappa * inf.t_mean) /
+                         std::max(inf.var_plain * inf.t_plain, 1e-300);
+        inf.used = inf.work_ratio < 1.0 ? 1 : 0;
+        inf.trained = 1;
+    }
+#undef CV_TRY
+    cleanup(MLMC_OK);
+    *out = cv;
+    return MLMC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ estimate with the control variate
+
+extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc_model *model,
+                                const mlmc_payoff *payoff, uint64_t seed, const mlmc_cv *cv, void *stream,
+                                mlmc_result *out)
+{
+    const auto t_start = std::chrono::steady_clock::now();
+    int rc = check_problem(model, payoff);
+    if (rc) return rc;
+    if (!out || !cv) return fail(MLMC_EINVAL, "out and cv must not be NULL");
+    rc = check_estimate_args(eps, M, Lmin, Lmax, N0, MLMC_FP32_PATH);
+    if (rc) return rc;
+    if (cv->M != M || std::memcmp(&cv->model, model, sizeof(*model)) ||
+        std::memcmp(&cv->payoff, payoff, sizeof(*payoff)))
+        return fail(MLMC_EINVAL, "the control variate was made for another problem");
+    cudaStream_t st = (cudaStream_t)stream;
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    const int ws_blocks = sms * 32;
+    const size_t ws_bytes = sums_workspace(ws_blocks, 8);
+    void *ws = nullptr;
+    double *d_sums = nullptr, *h_sums = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    auto cleanup = [&]() {
+        if (ws) cudaFree(ws);
+        if (d_sums) cudaFree(d_sums);
+        if (h_sums) cudaFreeHost(h_sums);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    };
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        cleanup();
+        return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
+    };
+    const int stride = 16;  // doubles per level in the round buffer: 8 level sums + 2 mean sums
+    cudaError_t e = cudaMalloc(&ws, ws_bytes);
+    if (e == cudaSuccess) e = cudaMemset(ws, 0, ws_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sums, MLMC_MAX_LEVELS * stride * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_sums, MLMC_MAX_LEVELS * stride * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "driver setup");
+
+    AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
+    auto uses = [&](int l) { return l < MLMC_CV_MAX_LEVELS && cv->d_params[l] && cv->info[l].used; };
+    // control-variate levels: cumulative sums of r, r^2 (N samples) and g, g^2 (N' mean samples)
+    std::vector<double> sr(MLMC_MAX_LEVELS, 0.0), srr(MLMC_MAX_LEVELS, 0.0), sg(MLMC_MAX_LEVELS, 0.0),
+        sgg(MLMC_MAX_LEVELS, 0.0), vs0(MLMC_MAX_LEVELS, 0.0), vs1(MLMC_MAX_LEVELS, 0.0);
+    std::vector<uint64_t> nmean(MLMC_MAX_LEVELS, 0);
+    for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
+        if (uses(l)) {
+            const mlmc_cv_level_info &inf = cv->info[l];
+            const double t_plain = inf.t_plain > 0 ? inf.t_plain : 1.0;
+            const double t_cv = inf.t_cv > 0 ? inf.t_cv : 1.0, t_mean = inf.t_mean > 0 ? inf.t_mean : 1.0;
+            drv.set_cost_scale(l, inf.t_plain > 0 ? (t_cv + inf.kappa * t_mean) / t_plain : 1.0 + inf.kappa);
+        }
+    std::vector<double> round(MLMC_MAX_LEVELS * 4);
+    double kernel_ms = 0.0;
+    uint64_t launches = 0, d2h_bytes = 0;
+    while (drv.active()) {
+        const std::vector<uint64_t> dN = drv.next_samples();
+        const int L = drv.finest_level();
+        if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (int l = 0; l <= L; ++l) {
+            if (!dN[l]) continue;
+            if (uses(l)) {
+                const uint64_t dm = (uint64_t)std::ceil(cv->info[l].kappa * (double)dN[l]);
+                int cb = 0, mb = 0;
+                rc = grid_for(cv_level_kernel_for(payoff->kind), dN[l], &cb);
+                if (!rc) rc = grid_for((const void *)cv_mean_kernel, dm, &mb);
+                if (!rc)
+                    rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
+                                         nullptr, ws, std::min(cb, ws_blocks), st);
+                if (!rc)
+                    rc = launch_cv_mean(cv, l, dm, nmean[l], seed, d_sums + stride * l + 8, nullptr, ws,
+                                        std::min(mb, ws_blocks), st);
+                launches += 2;
+            } else {
+                Plan plan;
+                rc = plan_level(l, M, dN[l], MLMC_FP32_PATH, payoff->kind, nullptr, &plan);
+                if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
+                if (!rc) {
+                    LevelParams p;
+                    fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+                    p.out = d_sums + stride * l;
+                    rc = launch_level(plan, p, ws, st);
+                }
+                launches += 1;
+            }
+            if (rc) {
+                cleanup();
+                return rc;
+            }
+        }
+        if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * stride * sizeof(double), cudaMemcpyDeviceToHost, st);
+        d2h_bytes += (L + 1) * stride * sizeof(double);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "level round");
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) kernel_ms += ms;
+        std::fill(round.begin(), round.end(), 0.0);
+        for (int l = 0; l <= L; ++l) {
+            if (!dN[l]) continue;
+            const double *h = h_sums + stride * l;
+            if (uses(l)) {
+                // level estimate mean(r) + mean'(g): its variance per path sample is
+                // Var(r) + Var(g) N / N'; hand the driver the sums of a sample with that mean
+                // and variance (as differences from the previous round's totals)
+                sr[l] += h[0];
+                srr[l] += h[1];
+                sg[l] += h[8];
+                sgg[l] += h[9];
+                nmean[l] += (uint64_t)std::ceil(cv->info[l].kappa * (double)dN[l]);
+                const double n = (double)(drv.samples_taken(l) + dN[l]), nm = (double)nmean[l];
+                const double mr = sr[l] / n, mg = sg[l] / nm;
+                const double vr = std::max(srr[l] / n - mr * mr, 0.0), vg = std::max(sgg[l] / nm - mg * mg, 0.0);
+                const double m = mr + mg, v = vr + vg * n / nm;
+                const double s0 = n * m, s1 = n * (v + m * m);
+                round[4 * l + 0] = s0 - vs0[l];
+                round[4 * l + 1] = s1 - vs1[l];
+                vs0[l] = s0;
+                vs1[l] = s1;
+            } else {
+                for (int k = 0; k < 4; ++k) round[4 * l + k] = h[k];
+            }
+        }
+        drv.absorb(round.data());
+    }
+    cleanup();
+    std::memset(out, 0, sizeof(*out));
+    drv.fill(out);
+    out->kernel_ms = kernel_ms;
+    out->launches = launches;
+    out->d2h_bytes = d2h_bytes;
+    out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (!out->converged) {
+        fail(MLMC_ENOTCONV, "bias test still failing at Lmax = %d", Lmax);
+        return MLMC_ENOTCONV;
+    }
+    return MLMC_OK;
+}

@@ -1,0 +1,442 @@
+// cv_kernels.cuh -- device code of the learned control variate (FP32 paths).
+//
+// For a level-l sample the control variate needs Y = P_l - P_{l-1} (Sec. 5, Eq. Yldef) and the
+// network inputs x_k = (W(k T/8) - W((k-1) T/8)) / sqrt(T/8), k = 1..8.  On levels with
+// M^l >= 8 the grid increments are sums of M^l / 8 consecutive fine increments of the path;
+// on coarser levels the grid is refined from the path's own grid by Brownian-bridge midpoints
+// whose normals come from Philox blocks 1 and 2 of the sample's counter (stage by stage, left
+// to right), so the path itself is the one the plain estimator draws.
+#pragma once
+#include <cstdint>
+
+#include "engine.h"
+#include "level_kernel.cuh"
+#include "mlp.cuh"
+#include "rng.cuh"
+
+namespace mlmcgb {
+
+template <int PAY>
+__device__ __forceinline__ void cv_sample(const LevelParams &p, uint64_t s, float &Y, float x[8])
+{
+    const int nf = p.nf, M = p.M;
+    const float a = (float)p.a, rh = (float)p.rh, S0 = (float)p.S0;
+    const float sqrt_h = (float)p.sqrt_h, sqrt_t8 = (float)p.sqrt_t8;
+    float fS = 1.f, fsum = 0.f, fhi = 1.f, flo = 1.f, fls = 0.f;
+    float cS = 1.f, csum = 0.f, chi = 1.f, clo = 1.f, cls = 0.f;
+    float dc = 0.f;
+    int q = 0;
+    float grid[9];  // W at i T / 8 (coarse levels only)
+    auto fine_step = [&](float z) {
+        const float d = fmaf(a, z, rh);
+        em_step<float, PAY, false>(fS, fsum, fhi, flo, fls, d);
+        dc += d;
+        if (++q == M) {
+            em_step<float, PAY, false>(cS, csum, chi, clo, cls, dc);
+            dc = 0.f;
+            q = 0;
+        }
+    };
+    if (nf < 4) {
+        // 4 / nf samples share block 0 of counter index s / G (the packed small levels)
+        const uint32_t G = 4u / (uint32_t)nf;
+        const uint64_t qb = s / G;
+        const uint32_t slot = (uint32_t)(s % G);
+        const uint4 xb = philox4x32_10(make_uint4(0u, (uint32_t)qb, (uint32_t)(qb >> 32), p.ctr3), p.key0, p.key1);
+        float rho, c, sn, z[4];
+        BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
+        z[0] = rho * c;
+        z[1] = rho * sn;
+        BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
+        z[2] = rho * c;
+        z[3] = rho * sn;
+        float W = 0.f;
+        grid[0] = 0.f;
+        for (int k = 0; k < nf; ++k) {
+            const float zk = z[slot * nf + k];
+            if (p.level > 0) {
+                fine_step(zk);
+            } else {
+                em_step<float, PAY, false>(fS, fsum, fhi, flo, fls, fmaf(a, zk, rh));
+            }
+            W = fmaf(sqrt_h, zk, W);
+            grid[(k + 1) * (8 / nf)] = W;
+        }
+    } else {
+        const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
+        const int per8 = nf >= 8 ? nf / 8 : 0;
+        const float scale = sqrt_h / sqrt_t8;
+        float acc = 0.f, W = 0.f;
+        int f = 0, cnt = 0;
+        grid[0] = 0.f;
+        for (int j = 0; j < nf / 4; ++j) {
+            const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
+            float rho, c, sn, z[4];
+            BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
+            z[0] = rho * c;
+            z[1] = rho * sn;
+            BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
+            z[2] = rho * c;
+            z[3] = rho * sn;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                fine_step(z[k]);
+                if (per8) {
+                    acc += z[k];
+                    if (++cnt == per8) {
+                        x[f++] = acc * scale;
+                        acc = 0.f;
+                        cnt = 0;
+                    }
+                } else {  // nf == 4: the path's grid points T/4, T/2, 3T/4, T
+                    W = fmaf(sqrt_h, z[k], W);
+                    grid[(4 * j + k + 1) * 2] = W;
+                }
+            }
+        }
+    }
+    if (nf < 8) {
+        // Brownian-bridge midpoints from blocks 1 and 2 of the sample's own counter
+        const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
+        float zb[8];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint4 xb = philox4x32_10(make_uint4((uint32_t)(j + 1), slo, shi, p.ctr3), p.key0, p.key1);
+            float rho, c, sn;
+            BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
+            zb[4 * j + 0] = rho * c;
+            zb[4 * j + 1] = rho * sn;
+            BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
+            zb[4 * j + 2] = rho * c;
+            zb[4 * j + 3] = rho * sn;
+        }
+        int next = 0;
+        for (int width = 8 / nf; width > 1; width /= 2) {
+            // midpoint variance: (width / 4) T / 8
+            const float sd = sqrt_t8 * sqrtf(0.25f * (float)width);
+            for (int left = 0; left < 8; left += width) {
+                const int mid = left + width / 2;
+                grid[mid] = 0.5f * (grid[left] + grid[left + width]) + sd * zb[next++];
+            }
+        }
+        const float inv = 1.0f / sqrt_t8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = (grid[k + 1] - grid[k]) * inv;
+    }
+    const float logS0 = PAY == kGeoAsian ? logf(S0) : 0.f;
+    const float Pf = payoff_value<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, (float)nf * logS0 + fls,
+                                              (float)p.inv_nf, p);
+    if (p.level == 0) {
+        Y = Pf;
+    } else {
+        const float Pc = payoff_value<float, PAY>(S0 * cS, S0 * csum, S0 * chi, (float)(nf / M) * logS0 + cls,
+                                                  (float)p.inv_nc, p);
+        Y = Pf - Pc;
+    }
+}
+
+// Sum NV doubles over the grid: block partials into `partials`, the last block to finish adds
+// them in block order into out.  The ticket is zero between launches.
+template <int NV>
+__device__ __forceinline__ void finish_sums_n(double m[NV], double *partials, unsigned *ticket, double *out)
+{
+    __shared__ double sm[32][NV];
+    __shared__ bool is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) m[k] = warp_sum(m[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[warp][k] = m[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) m[k] = warp_sum(lane < nw ? sm[lane][k] : 0.0);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) partials[NV * blockIdx.x + k] = m[k];
+            __threadfence();
+            is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (warp == 0) {
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + NV * b + k);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) out[k] = acc[k];
+            *ticket = 0u;
+        }
+    }
+}
+
+// Control-variate level estimator: per sample r = Y - g(x); sums
+// [r, r^2, r^3, r^4, Y, Y^2, g, g^2] (FP64).  One thread per sample, whole warps evaluate g.
+template <int PAY>
+__global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, const float *__restrict__ params,
+                                                       double *out8, float *r_out, float *g_out)
+{
+    __shared__ MlpShared net;
+    __shared__ uint32_t xw_all[8][128];
+    load_mlp(net, params);
+    __syncthreads();
+    uint32_t *xw = xw_all[threadIdx.x >> 5];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t warp_first = tid & ~uint64_t(31);
+    double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint64_t base = 0; base + warp_first < p.N; base += stride) {
+        const uint64_t idx = base + tid;
+        const bool valid = idx < p.N;
+        const uint64_t s = p.first + (valid ? idx : p.N - 1);
+        float Y, x[8];
+        cv_sample<PAY>(p, s, Y, x);
+        const float gv = warp_mlp(net, xw, x);
+        if (valid) {
+            const double y = Y, g = gv, r = y - g, r2 = r * r;
+            m[0] += r;
+            m[1] += r2;
+            m[2] = fma(r2, r, m[2]);
+            m[3] = fma(r2, r2, m[3]);
+            m[4] += y;
+            m[5] = fma(y, y, m[5]);
+            m[6] += g;
+            m[7] = fma(g, g, m[7]);
+            if (r_out) r_out[idx] = (float)r;
+            if (g_out) g_out[idx] = gv;
+        }
+    }
+    finish_sums_n<8>(m, p.partials, p.ticket, out8);
+}
+
+// Independent sample that estimates E[g]: eight stream normals per sample (blocks 0 and 1 of
+// counter s under the control-variate-mean tag) are the network inputs; sums [g, g^2].
+__global__ void __launch_bounds__(256) cv_mean_kernel(const LevelParams p, const float *__restrict__ params,
+                                                      double *out2, float *g_out)
+{
+    __shared__ MlpShared net;
+    __shared__ uint32_t xw_all[8][128];
+    load_mlp(net, params);
+    __syncthreads();
+    uint32_t *xw = xw_all[threadIdx.x >> 5];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t warp_first = tid & ~uint64_t(31);
+    double m[2] = {0, 0};
+    for (uint64_t base = 0; base + warp_first < p.N; base += stride) {
+        const uint64_t idx = base + tid;
+        const bool valid = idx < p.N;
+        const uint64_t s = p.first + (valid ? idx : p.N - 1);
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)s, (uint32_t)(s >> 32), p.ctr3),
+                                           p.key0, p.key1);
+            float rho, c, sn;
+            BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
+            x[4 * j + 0] = rho * c;
+            x[4 * j + 1] = rho * sn;
+            BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
+            x[4 * j + 2] = rho * c;
+            x[4 * j + 3] = rho * sn;
+        }
+        const float gv = warp_mlp(net, xw, x);
+        if (valid) {
+            const double g = gv;
+            m[0] += g;
+            m[1] = fma(g, g, m[1]);
+            if (g_out) g_out[idx] = gv;
+        }
+    }
+    finish_sums_n<2>(m, p.partials, p.ticket, out2);
+}
+
+// Training data: (x, Y) of samples [first, first + N) under the training tag.
+template <int PAY>
+__global__ void __launch_bounds__(256) cv_data_kernel(const LevelParams p, float *X, float *Yout)
+{
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t idx = tid; idx < p.N; idx += stride) {
+        float Y, x[8];
+        cv_sample<PAY>(p, p.first + idx, Y, x);
+        Yout[idx] = Y;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) X[8 * idx + k] = x[k];
+    }
+}
+
+// g(x) for rows of X [N][8] (standalone forward, used for validation and tests).
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restrict__ params, const float *X,
+                                                          uint64_t N, float *G)
+{
+    __shared__ MlpShared net;
+    __shared__ uint32_t xw_all[8][128];
+    load_mlp(net, params);
+    __syncthreads();
+    uint32_t *xw = xw_all[threadIdx.x >> 5];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t warp_first = tid & ~uint64_t(31);
+    for (uint64_t base = 0; base + warp_first < N; base += stride) {
+        const uint64_t idx = base + tid;
+        const bool valid = idx < N;
+        const uint64_t row = valid ? idx : N - 1;
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = X[8 * row + k];
+        const float gv = warp_mlp(net, xw, x);
+        if (valid) G[idx] = gv;
+    }
+}
+
+// ------------------------------------------------------------------ training (one mini-batch)
+
+// Forward pass of a mini-batch of B rows starting at row `off` of (X, Y): stores z1, z2 and g
+// for the backward pass; thread 0 of block 0 advances the Adam step counter.
+__global__ void __launch_bounds__(256) train_forward_kernel(const float *__restrict__ params, const float *X,
+                                                            uint64_t off, int B, float *Z1, float *Z2, float *G,
+                                                            unsigned *step)
+{
+    __shared__ MlpShared net;
+    __shared__ uint32_t xw_all[8][128];
+    load_mlp(net, params);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = (blockIdx.x * 8 + warp) * 32;  // first batch row of this warp
+    if (base >= B) return;                          // whole warps only (B is a multiple of 32)
+    uint32_t *xw = xw_all[warp];
+    const float *xr = X + 8 * (off + base + lane);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xw[lane * 4 + j] = pack_bf16x2(xr[2 * j], xr[2 * j + 1]);
+    __syncwarp();
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int tile = 0; tile < 2; ++tile) {
+        TileActs acts;
+        float r0, r1;
+        mlp_tile(net, xw + tile * 64, r0, r1, &acts);
+        const int row0 = base + tile * 16 + g, row1 = row0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int o = 8 * nt + 2 * t;
+            Z1[row0 * kHidden + o] = acts.z1[nt][0];
+            Z1[row0 * kHidden + o + 1] = acts.z1[nt][1];
+            Z1[row1 * kHidden + o] = acts.z1[nt][2];
+            Z1[row1 * kHidden + o + 1] = acts.z1[nt][3];
+            Z2[row0 * kHidden + o] = acts.z2[nt][0];
+            Z2[row0 * kHidden + o + 1] = acts.z2[nt][1];
+            Z2[row1 * kHidden + o] = acts.z2[nt][2];
+            Z2[row1 * kHidden + o + 1] = acts.z2[nt][3];
+        }
+        if (t == 0) {
+            G[row0] = r0;
+            G[row1] = r1;
+        }
+    }
+}
+
+__device__ __forceinline__ float bf16_round(float v)
+{
+    const uint32_t w = pack_bf16x2(0.f, v);
+    return __uint_as_float(w & 0xFFFF0000u);
+}
+
+// Backward pass per row (FP32): loss (1/B) sum (g - (Y - mu) / sd)^2.  Writes
+// D = dL/dg, DZ2 = dL/dz2, DZ1 = dL/dz1, H1 = bf16(GELU(z1)) (the layer-2 input the forward
+// used) and H2 = GELU(z2).
+__global__ void __launch_bounds__(128) train_backward_kernel(const float *__restrict__ params, const float *Y,
+                                                             uint64_t off, int B, float mu, float inv_sd,
+                                                             const float *Z1, const float *Z2, const float *G,
+                                                             float *D, float *DZ1, float *DZ2, float *H1, float *H2)
+{
+    __shared__ float W2s[kHidden * kHidden];
+    __shared__ float w3s[kHidden];
+    for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) W2s[i] = bf16_round(params[kOffW2 + i]);
+    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) w3s[i] = params[kOffW3 + i];
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= B) return;
+    const float target = (Y[off + row] - mu) * inv_sd;
+    const float d = 2.0f * (G[row] - target) / (float)B;
+    D[row] = d;
+    float dh1[kHidden];
+#pragma unroll
+    for (int i = 0; i < kHidden; ++i) dh1[i] = 0.f;
+    for (int o = 0; o < kHidden; ++o) {
+        const float z2 = Z2[row * kHidden + o];
+        const float dz2 = d * w3s[o] * gelu_grad(z2);
+        DZ2[row * kHidden + o] = dz2;
+        H2[row * kHidden + o] = gelu(z2);
+#pragma unroll
+        for (int i = 0; i < kHidden; ++i) dh1[i] = fmaf(dz2, W2s[o * kHidden + i], dh1[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kHidden; ++i) {
+        const float z1 = Z1[row * kHidden + i];
+        DZ1[row * kHidden + i] = dh1[i] * gelu_grad(z1);
+        H1[row * kHidden + i] = bf16_round(gelu(z1));
+    }
+}
+
+// Parameter gradients: one thread per parameter, sums over the B rows of the batch.
+__global__ void __launch_bounds__(256) train_grad_kernel(const float *X, uint64_t off, int B, const float *D,
+                                                         const float *DZ1, const float *DZ2, const float *H1,
+                                                         const float *H2, float *grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNumParams) return;
+    float acc = 0.f;
+    if (i < kOffB1) {  // W1[u][k]
+        const int u = i / kInputs, k = i % kInputs;
+        for (int r = 0; r < B; ++r) acc = fmaf(DZ1[r * kHidden + u], bf16_round(X[8 * (off + r) + k]), acc);
+    } else if (i < kOffW2) {  // b1[u]
+        const int u = i - kOffB1;
+        for (int r = 0; r < B; ++r) acc += DZ1[r * kHidden + u];
+    } else if (i < kOffB2) {  // W2[o][u]
+        const int o = (i - kOffW2) / kHidden, u = (i - kOffW2) % kHidden;
+        for (int r = 0; r < B; ++r) acc = fmaf(DZ2[r * kHidden + o], H1[r * kHidden + u], acc);
+    } else if (i < kOffW3) {  // b2[o]
+        const int o = i - kOffB2;
+        for (int r = 0; r < B; ++r) acc += DZ2[r * kHidden + o];
+    } else if (i < kOffB3) {  // w3[o]
+        const int o = i - kOffW3;
+        for (int r = 0; r < B; ++r) acc = fmaf(D[r], H2[r * kHidden + o], acc);
+    } else {  // b3
+        for (int r = 0; r < B; ++r) acc += D[r];
+    }
+    grad[i] = acc;
+}
+
+// Adam update of the FP32 master parameters (step counter advanced by the forward kernel).
+__global__ void __launch_bounds__(256) adam_kernel(float *params, const float *grad, float *m1, float *m2,
+                                                   const unsigned *step, float lr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNumParams) return;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float gi = grad[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float t = (float)*step;
+    const float ah = a / (1.f - powf(b1, t));
+    const float vh = v / (1.f - powf(b2, t));
+    params[i] -= lr * ah / (sqrtf(vh) + 1e-8f);
+}
+
+}  // namespace mlmcgb

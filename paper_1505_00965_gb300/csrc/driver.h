@@ -113,13 +113,23 @@ class AdaptiveMLMC {
         out->path_steps = steps;
     }
 
-    // C_l: Euler--Maruyama steps of one level-l sample, fine and coarse (Sec. 3 cost model).
+    // C_l: Euler--Maruyama steps of one level-l sample, fine and coarse (Sec. 3 cost model),
+    // times the level's cost scale (1 unless set_cost_scale changed it).
     double cost_of(int l) const
     {
-        if (l == 0) return 1.0;
         double nf = 1.0;
         for (int i = 0; i < l; ++i) nf *= M_;
-        return nf + nf / M_;
+        const double steps = l == 0 ? 1.0 : nf + nf / M_;
+        return steps * (l < (int)scale_.size() ? scale_[l] : 1.0);
+    }
+
+    // Scale level l's cost, for a level estimator that does more work per sample than the
+    // plain one (the control variate's network and its mean sample).
+    void set_cost_scale(int l, double factor)
+    {
+        if (l < 0 || l >= (int)scale_.size() || !(factor > 0)) return;
+        scale_[l] = factor;
+        if (l < (int)C_.size()) C_[l] = cost_of(l);
     }
 
   private:
@@ -193,6 +203,7 @@ class AdaptiveMLMC {
     std::vector<uint64_t> N_, dN_;
     std::vector<std::array<double, 4>> S_;
     std::vector<double> mean_, var_, C_;
+    std::vector<double> scale_ = std::vector<double>(MLMC_MAX_LEVELS, 1.0);
 };
 
 }  // namespace mlmcgb

@@ -17,6 +17,8 @@ struct LevelParams {
     double rh;        // r * fine step
     double inv_nf;    // 1 / M^l
     double inv_nc;    // 1 / M^(l-1)
+    double sqrt_h;    // sqrt(h): Brownian increment scale of one fine step
+    double sqrt_t8;   // sqrt(T / 8): scale of the control variate's grid increments
     uint64_t first;   // first sample index
     uint64_t N;       // number of samples
     uint32_t key0, key1;  // Philox key (seed low, seed high)

@@ -73,6 +73,24 @@ _u64, _i32, _dbl, _vp, _sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, cty
 _dptr = ctypes.POINTER(ctypes.c_double)
 _pm, _pp, _pl = ctypes.POINTER(mlmc_model), ctypes.POINTER(mlmc_payoff), ctypes.POINTER(mlmc_launch)
 
+MLMC_CV_PARAMS = 4801
+MLMC_CV_MAX_LEVELS = 8
+
+
+class mlmc_cv_options(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n_train", ctypes.c_uint64), ("lr", ctypes.c_double),
+                ("init_seed", ctypes.c_uint64)]
+
+
+class mlmc_cv_level_info(ctypes.Structure):
+    _fields_ = [("trained", ctypes.c_int32), ("used", ctypes.c_int32), ("var_plain", ctypes.c_double),
+                ("var_resid", ctypes.c_double), ("var_g", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("t_plain", ctypes.c_double), ("t_cv", ctypes.c_double), ("t_mean", ctypes.c_double),
+                ("work_ratio", ctypes.c_double), ("train_loss", ctypes.c_double)]
+
+
+_fptr = ctypes.POINTER(ctypes.c_float)
 _SIGNATURES = {
     "mlmc_last_error": ([], ctypes.c_char_p),
     "mlmc_version": ([], ctypes.c_char_p),
@@ -84,6 +102,18 @@ _SIGNATURES = {
     "mlmc_level_sums_async": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _sz, _vp, _vp],
                               _i32),
     "mlmc_level_sums_noalloc": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _vp, _vp], _i32),
+    "mlmc_cv_create": ([_i32, _pm, _pp, ctypes.POINTER(_vp)], _i32),
+    "mlmc_cv_train": ([_i32, _pm, _pp, _u64, ctypes.POINTER(mlmc_cv_options), _vp, ctypes.POINTER(_vp)], _i32),
+    "mlmc_cv_free": ([_vp], _i32),
+    "mlmc_cv_info": ([_vp, _i32, ctypes.POINTER(mlmc_cv_level_info)], _i32),
+    "mlmc_cv_get_params": ([_vp, _i32, _fptr], _i32),
+    "mlmc_cv_set_params": ([_vp, _i32, _fptr, _dbl], _i32),
+    "mlmc_cv_level_sums": ([_vp, _i32, _u64, _u64, _u64, _vp, _vp, _vp, _vp], _i32),
+    "mlmc_cv_mean_sums": ([_vp, _i32, _u64, _u64, _u64, _vp, _vp, _vp], _i32),
+    "mlmc_cv_training_data": ([_vp, _i32, _u64, _u64, _u64, _vp, _vp, _vp], _i32),
+    "mlmc_mlp_forward": ([_fptr, _vp, _u64, _vp, _vp], _i32),
+    "mlmc_mlp_grad": ([_fptr, _vp, _vp, _u64, _fptr, ctypes.POINTER(_dbl), _vp], _i32),
+    "mlmc_estimate_cv": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _vp, _vp, ctypes.POINTER(mlmc_result)], _i32),
     "mlmc_estimate_batch": ([_i32, ctypes.c_void_p, _i32, _i32, _i32, _u64, _i32, _vp, ctypes.c_void_p], _i32),
     "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
 }
@@ -273,6 +303,118 @@ def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int
     m, p = problem.model(), problem.payoff_struct()
     st = _lib.mlmc_estimate(eps, M, Lmin, Lmax, N0, ctypes.byref(m), ctypes.byref(p), seed, _prec(precision),
                             _addr(stream), ctypes.byref(r))
+    if st not in (MLMC_OK, MLMC_ENOTCONV):
+        _check(st)
+    return _estimate_from(st, r)
+
+
+# ------------------------------------------------------------------ learned control variate
+
+def _floats(a, n=MLMC_CV_PARAMS):
+    import numpy as np
+
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if arr.shape != (n,):
+        raise ValueError(f"expected {n} parameters")
+    return arr, arr.ctypes.data_as(_fptr)
+
+
+class ControlVariate:
+    """Owner of an mlmc_cv handle (freed with the object)."""
+
+    def __init__(self, handle: int, M: int, problem: Problem):
+        self.handle = ctypes.c_void_p(handle)
+        self.M = M
+        self.problem = problem
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.mlmc_cv_free(h)
+            self.handle = None
+
+
+def mlmc_cv_create(M: int, problem: Problem) -> ControlVariate:
+    h = ctypes.c_void_p()
+    m, p = problem.model(), problem.payoff_struct()
+    _check(_lib.mlmc_cv_create(M, ctypes.byref(m), ctypes.byref(p), ctypes.byref(h)))
+    return ControlVariate(h.value, M, problem)
+
+
+def mlmc_cv_train(M: int, problem: Problem, seed: int, levels: int = 4, epochs: int = 20, batch: int = 4096,
+                  n_train: int = 1_000_000, lr: float = 1e-3, init_seed: int = 0, stream=None) -> ControlVariate:
+    h = ctypes.c_void_p()
+    m, p = problem.model(), problem.payoff_struct()
+    o = mlmc_cv_options(levels, epochs, batch, 0, n_train, lr, init_seed)
+    _check(_lib.mlmc_cv_train(M, ctypes.byref(m), ctypes.byref(p), seed, ctypes.byref(o), _addr(stream),
+                              ctypes.byref(h)))
+    return ControlVariate(h.value, M, problem)
+
+
+def mlmc_cv_free(cv: ControlVariate) -> None:
+    if cv.handle is not None and cv.handle.value:
+        _check(_lib.mlmc_cv_free(cv.handle))
+        cv.handle = None
+
+
+def mlmc_cv_info(cv: ControlVariate, level: int) -> dict:
+    info = mlmc_cv_level_info()
+    _check(_lib.mlmc_cv_info(cv.handle, level, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in mlmc_cv_level_info._fields_}
+
+
+def mlmc_cv_get_params(cv: ControlVariate, level: int):
+    import numpy as np
+
+    out = np.zeros(MLMC_CV_PARAMS, dtype=np.float32)
+    _check(_lib.mlmc_cv_get_params(cv.handle, level, out.ctypes.data_as(_fptr)))
+    return out
+
+
+def mlmc_cv_set_params(cv: ControlVariate, level: int, params, kappa: float = 1.0) -> None:
+    arr, ptr = _floats(params)
+    _check(_lib.mlmc_cv_set_params(cv.handle, level, ptr, kappa))
+
+
+def mlmc_cv_level_sums(cv: ControlVariate, level: int, N: int, first: int, seed: int, d_sums8, d_r=None, d_g=None,
+                       stream=None) -> None:
+    _check(_lib.mlmc_cv_level_sums(cv.handle, level, N, first, seed, _addr(d_sums8), _addr(d_r), _addr(d_g),
+                                   _addr(stream)))
+
+
+def mlmc_cv_mean_sums(cv: ControlVariate, level: int, N: int, first: int, seed: int, d_sums2, d_g=None,
+                      stream=None) -> None:
+    _check(_lib.mlmc_cv_mean_sums(cv.handle, level, N, first, seed, _addr(d_sums2), _addr(d_g), _addr(stream)))
+
+
+def mlmc_cv_training_data(cv: ControlVariate, level: int, N: int, first: int, seed: int, d_X, d_Y,
+                          stream=None) -> None:
+    _check(_lib.mlmc_cv_training_data(cv.handle, level, N, first, seed, _addr(d_X), _addr(d_Y), _addr(stream)))
+
+
+def mlmc_mlp_forward(params, d_X, N: int, d_G, stream=None) -> None:
+    arr, ptr = _floats(params)
+    _check(_lib.mlmc_mlp_forward(ptr, _addr(d_X), N, _addr(d_G), _addr(stream)))
+
+
+def mlmc_mlp_grad(params, d_X, d_Y, N: int, stream=None):
+    """(loss, gradient) of the mean squared error on device rows d_X [N][8], d_Y [N]."""
+    import numpy as np
+
+    arr, ptr = _floats(params)
+    grad = np.zeros(MLMC_CV_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.mlmc_mlp_grad(ptr, _addr(d_X), _addr(d_Y), N, grad.ctypes.data_as(_fptr), ctypes.byref(loss),
+                              _addr(stream)))
+    return loss.value, grad
+
+
+def mlmc_estimate_cv(eps: float, cv: ControlVariate, seed: int, Lmin: int = 2, Lmax: int = 8, N0: int = 10_000,
+                     stream=None) -> Estimate:
+    r = mlmc_result()
+    m, p = cv.problem.model(), cv.problem.payoff_struct()
+    st = _lib.mlmc_estimate_cv(eps, cv.M, Lmin, Lmax, N0, ctypes.byref(m), ctypes.byref(p), seed, cv.handle,
+                               _addr(stream), ctypes.byref(r))
     if st not in (MLMC_OK, MLMC_ENOTCONV):
         _check(st)
     return _estimate_from(st, r)

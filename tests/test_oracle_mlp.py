@@ -1,0 +1,108 @@
+"""Pins of the oracle's control-variate network: gradients against finite differences, the GELU
+against the exact x Phi(x), bfloat16 rounding against PyTorch's conversion, closed-form special
+cases, and the law of the network inputs."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+import oracle
+from oracle import mlp
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    theta = mlp.init_params(1) + 0.1 * rng.standard_normal(mlp.N_PARAMS)
+    X = rng.standard_normal((40, 8))
+    Y = rng.standard_normal(40) * 2 + 1
+    loss, grad = mlp.loss_and_grad(theta, X, Y)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False).tolist() + [mlp.N_PARAMS - 1, 0, 512, 4800 - 64]
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(mlp.N_PARAMS)
+        e[i] = h
+        lp, _ = mlp.loss_and_grad(theta + e, X, Y)
+        lm, _ = mlp.loss_and_grad(theta - e, X, Y)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+def test_gelu_is_close_to_x_phi_x_and_its_derivative_is_exact():
+    z = np.linspace(-6, 6, 2001)
+    assert np.max(np.abs(mlp.gelu(z) - z * norm.cdf(z))) < 1e-3
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
+
+
+def test_bf16_rounding_matches_pytorch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(5000) * 10 ** rng.uniform(-3, 3, 5000),
+                        [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 0.0, 65504.0, 1e-30]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), want)
+    assert mlp.bf16(np.array([1 + 2 ** -8]))[0] == 1.0               # tie to even
+    assert mlp.bf16(np.array([1 + 3 * 2 ** -8]))[0] == 1 + 2 ** -6   # tie to even, upwards
+
+
+def test_network_special_cases():
+    """With W1 = 0 and b1 = 0 the first layer outputs GELU(0) = 0, so g = w3 . GELU(b2) + b3."""
+    rng = np.random.default_rng(2)
+    b2 = rng.standard_normal(64)
+    w3 = rng.standard_normal(64)
+    theta = mlp.pack(np.zeros((64, 8)), np.zeros(64), rng.standard_normal((64, 64)), b2, w3, 0.7)
+    X = rng.standard_normal((10, 8))
+    g, _ = mlp.forward(theta, X)
+    want = float(w3 @ (0.5 * b2 * (1 + np.tanh(math.sqrt(2 / math.pi) * (b2 + 0.044715 * b2 ** 3))))) + 0.7
+    np.testing.assert_allclose(g, want, rtol=1e-14)
+    # a network that is linear in x for small weights: g ~ b3 + w3 . GELU'(0) W2 GELU'(0) W1 x
+    # (GELU(z) = z / 2 + O(z^2): with |W1 x| ~ 1e-7 the quadratic terms are ~1e-7 relative)
+    small = mlp.pack(rng.standard_normal((64, 8)) * 1e-7, np.zeros(64), rng.standard_normal((64, 64)) * 1e-2,
+                     np.zeros(64), rng.standard_normal(64), 0.0)
+    W1, _, W2, _, w3s, _ = mlp.unpack(small)
+    lin = X @ (0.25 * (w3s @ W2 @ W1))
+    g, _ = mlp.forward(small, X)
+    np.testing.assert_allclose(g, lin, rtol=1e-4, atol=1e-15)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3])
+def test_features_are_iid_standard_normal(level):
+    n = 20000
+    F = np.array([mlp.features(level, 4, s, 1.0, seed=17) for s in range(n)])
+    assert np.max(np.abs(F.mean(axis=0))) < 5 / math.sqrt(n)
+    assert np.max(np.abs(np.cov(F.T, bias=True) - np.eye(8))) < 5 * math.sqrt(2 / n)
+
+
+def test_mean_sample_features_are_independent_normals():
+    n = 20000
+    F = np.array([mlp.mean_sample_features(s, seed=17, level=2) for s in range(n)])
+    assert np.max(np.abs(np.cov(F.T, bias=True) - np.eye(8))) < 5 * math.sqrt(2 / n)
+    # and they are not the path features of the same index
+    P = np.array([mlp.features(2, 4, s, 1.0, seed=17) for s in range(2000)])
+    assert abs(np.corrcoef(F[:2000, 0], P[:, 0])[0, 1]) < 0.1
+
+
+def test_quantised_gradient_uses_the_rounded_forward():
+    """With bf16 rounding on, the gradient is that of the rounded network with straight-through
+    rounding of the weights: finite differences of the rounded forward in directions that do
+    not cross a rounding boundary (b2, b3, w3, b1 are not rounded) agree."""
+    rng = np.random.default_rng(9)
+    theta = mlp.init_params(3)
+    X = rng.standard_normal((30, 8))
+    Y = rng.standard_normal(30)
+    _, grad = mlp.loss_and_grad(theta, X, Y, quantize=True)
+    off_b1 = 64 * 8
+    off_b2 = off_b1 + 64 + 64 * 64
+    for i in [off_b1 + 3, off_b2 + 5, off_b2 + 64 + 7, mlp.N_PARAMS - 1]:
+        e = np.zeros(mlp.N_PARAMS)
+        e[i] = 1e-6
+        lp, _ = mlp.loss_and_grad(theta + e, X, Y, quantize=True)
+        lm, _ = mlp.loss_and_grad(theta - e, X, Y, quantize=True)
+        fd = (lp - lm) / 2e-6
+        # b1 moves z1, whose GELU is rounded to bf16 before layer 2: allow the rounding step
+        tol = 2e-2 if i == off_b1 + 3 else 1e-6
+        assert abs(fd - grad[i]) <= tol * max(1.0, abs(fd)), (i, fd, grad[i])
