@@ -201,6 +201,44 @@ class ClockSampler:
         return parse_clock_lines(out.splitlines())
 
 
+def side_workloads(mlmc, stream) -> dict:
+    """Reports outside the timed region: the 512-problem batch and the learned control variate
+    (Asian call, levels 0..3 trained on 10^6 samples each, applied at eps = 5e-4)."""
+    from paper_1505_00965_gb300 import workloads
+
+    out = {}
+    qs = workloads.batch_problems(512)
+    t = time.perf_counter()
+    res = mlmc.mlmc_estimate_batch(qs, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
+    wall = time.perf_counter() - t
+    steps = sum(r.path_steps for r in res)
+    out["batch_512"] = {"wall_ms": 1e3 * wall, "kernel_ms": res[0].kernel_ms, "rounds": res[0].rounds,
+                        "path_steps": steps, "path_steps_per_s": steps / wall,
+                        "converged": sum(r.converged for r in res), "problems": len(res),
+                        "workload": "K~U[80,120], sigma~U[0.1,0.5], T~U[0.25,2], r=0.05, payoff uniform over "
+                                    "European/Asian/lookback/digital, eps log-uniform in [1e-3,1e-2], seeds 1..512"}
+    prob = mlmc.Problem(payoff="asian", cash=1.0, **GBM)
+    t = time.perf_counter()
+    cv = mlmc.mlmc_cv_train(M, prob, seed=2024, levels=4, epochs=20, n_train=1_000_000, stream=stream)
+    train_s = time.perf_counter() - t
+    levels = []
+    for l in range(4):
+        i = mlmc.mlmc_cv_info(cv, l)
+        levels.append({"level": l, "var_ratio": i["var_resid"] / i["var_plain"], "var_plain": i["var_plain"],
+                       "var_resid": i["var_resid"], "kappa": i["kappa"], "work_ratio": i["work_ratio"],
+                       "used": bool(i["used"]), "ns_per_sample_plain": 1e9 * i["t_plain"],
+                       "ns_per_sample_cv": 1e9 * i["t_cv"], "ns_per_sample_mean": 1e9 * i["t_mean"]})
+    eps_cv = 5e-4
+    a = mlmc.mlmc_estimate_cv(eps_cv, cv, 1, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
+    b = mlmc.mlmc_estimate(eps_cv, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
+    c = mlmc.mlmc_estimate(eps_cv, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64", stream=stream)
+    out["learned_cv"] = {"payoff": "asian", "train_s": train_s, "levels": levels, "eps": eps_cv,
+                         "time_to_eps_ms": {"fp32_cv": a.wall_ms, "fp32_plain": b.wall_ms, "fp64_plain": c.wall_ms},
+                         "estimate": {"fp32_cv": a.P, "fp32_plain": b.P, "fp64_plain": c.P}}
+    mlmc.mlmc_cv_free(cv)
+    return out
+
+
 def gpu_arm(args) -> None:
     import torch
     import torch.distributed as dist
@@ -288,6 +326,7 @@ def gpu_arm(args) -> None:
     fp64 = mlmc.mlmc_estimate(EPS, problems["asian"], seeds[0], M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64",
                               stream=stream)
     fp32_asian_median = statistics.median(tte["asian"][:len(seeds)])
+    extras = {} if args.no_extras else side_workloads(mlmc, stream)
     value = steps_all / dev_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -310,6 +349,7 @@ def gpu_arm(args) -> None:
         "roofline": roofline,
         "clocks": clocks,
     }
+    line.update(extras)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
@@ -324,6 +364,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and control-variate reports")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be at least 3")

@@ -350,6 +350,29 @@ int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t N0, const m
                      const mlmc_payoff *payoff, uint64_t seed, const mlmc_cv *cv, void *stream,
                      mlmc_result *out);
 
+/*
+ * ---------------------------------------------------------------- autotuner
+ * mlmc_autotune -- time candidate launch shapes of the level kernel (threads per block in
+ * {128, 256, 512}, every valid lanes_per_path, one or two waves of resident blocks) for
+ * levels 0..max_level of (precision, payoff, M) at N = 2^10, 2^13, ... (up to 2e9 fine steps per
+ * launch), keeping the fastest per size class.  Whenever a caller leaves launch fields at zero
+ * the library then uses the tuned values of the nearest size class at or below N.  A different
+ * lanes_per_path changes path roundoff, not the samples.  The paper has no counterpart (launch
+ * tuning).  entries (host, may be NULL) receives the number of table entries added.
+ * The table is process-wide.  MLMC_AUTOTUNE_CACHE names a file loaded on first use.
+ */
+int mlmc_autotune(int M, int max_level, int precision, int payoff, void *stream, int *entries);
+/* Write the table as JSON (one entry per line) / read such a file (adds to the table). */
+int mlmc_autotune_save(const char *path);
+int mlmc_autotune_load(const char *path, int *entries);
+/* Empty the table (the library returns to its built-in launch heuristic). */
+int mlmc_autotune_clear(void);
+/* Number of table entries. */
+int mlmc_autotune_entries(void);
+/* Tuned shape for (precision, payoff, M, level, N): threads_per_block, lanes_per_path, and in
+ * `blocks` the number of waves of resident blocks; MLMC_EINVAL if the table has none. */
+int mlmc_autotune_lookup(int precision, int payoff, int M, int level, uint64_t N, mlmc_launch *out);
+
 /* Number of streaming multiprocessors of the current device, or -1 with an error message. */
 int mlmc_device_sm_count(void);
 

@@ -106,10 +106,17 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
     if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
     const long nf = ipow(M, level);
     const int unit = std::max(M, 4);  // a lane's chunk holds whole Philox blocks and coarse steps
-    int threads = launch && launch->threads_per_block ? launch->threads_per_block : 256;
+    // a shape chosen by the autotuner fills the fields the caller left at zero
+    TunedShape tuned;
+    const bool have_tuned = tuned_lookup(precision, payoff, M, level, N, &tuned);
+    int threads = launch && launch->threads_per_block ? launch->threads_per_block
+                                                      : (have_tuned ? tuned.threads : 256);
     if (threads < 32 || threads > 1024 || threads % 32)
         return fail(MLMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
     int lanes = launch && launch->lanes_per_path ? launch->lanes_per_path : 0;
+    if (!lanes && have_tuned && (tuned.lanes == 1 || (nf >= 8 && nf % tuned.lanes == 0 &&
+                                                      (nf / tuned.lanes) % unit == 0)))
+        lanes = tuned.lanes;
     if (lanes) {
         if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
             return fail(MLMC_EINVAL, "lanes_per_path must be a power of two in [1, 32]");
@@ -144,7 +151,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
         const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
                                    : (double)std::max<uint64_t>(N, 1) * lanes;
         const double need = std::ceil(items / threads);
-        blocks = (int)std::min<double>(need, max_blocks);
+        const int oversub = have_tuned ? std::max(1, tuned.oversub) : 1;
+        blocks = (int)std::min<double>(need, (double)max_blocks * oversub);
     }
     blocks = std::max(blocks, 1);
     plan->threads = threads;

@@ -40,4 +40,11 @@ double level_cost(int level, int M);
 int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st);
 int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int precision);
 
+// Launch shape found by the autotuner for (precision, payoff, M, level) at the size class of N.
+struct TunedShape {
+    int threads, lanes, oversub;
+    double ns_per_sample;
+};
+bool tuned_lookup(int precision, int payoff, int M, int level, uint64_t N, TunedShape *out);
+
 }  // namespace mlmcgb

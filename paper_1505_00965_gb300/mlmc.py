@@ -114,6 +114,12 @@ _SIGNATURES = {
     "mlmc_mlp_forward": ([_fptr, _vp, _u64, _vp, _vp], _i32),
     "mlmc_mlp_grad": ([_fptr, _vp, _vp, _u64, _fptr, ctypes.POINTER(_dbl), _vp], _i32),
     "mlmc_estimate_cv": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _vp, _vp, ctypes.POINTER(mlmc_result)], _i32),
+    "mlmc_autotune": ([_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_i32)], _i32),
+    "mlmc_autotune_save": ([ctypes.c_char_p], _i32),
+    "mlmc_autotune_load": ([ctypes.c_char_p, ctypes.POINTER(_i32)], _i32),
+    "mlmc_autotune_clear": ([], _i32),
+    "mlmc_autotune_entries": ([], _i32),
+    "mlmc_autotune_lookup": ([_i32, _i32, _i32, _i32, _u64, _pl], _i32),
     "mlmc_estimate_batch": ([_i32, ctypes.c_void_p, _i32, _i32, _i32, _u64, _i32, _vp, ctypes.c_void_p], _i32),
     "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
 }
@@ -418,3 +424,39 @@ def mlmc_estimate_cv(eps: float, cv: ControlVariate, seed: int, Lmin: int = 2, L
     if st not in (MLMC_OK, MLMC_ENOTCONV):
         _check(st)
     return _estimate_from(st, r)
+
+
+# ------------------------------------------------------------------ autotuner
+
+def mlmc_autotune(M: int = 4, max_level: int = 8, precision="fp32", payoff: str = "asian", stream=None) -> int:
+    """Tune launch shapes; returns the number of table entries added."""
+    n = ctypes.c_int()
+    _check(_lib.mlmc_autotune(M, max_level, _prec(precision), PAYOFFS[payoff], _addr(stream), ctypes.byref(n)))
+    return n.value
+
+
+def mlmc_autotune_save(path: str) -> None:
+    _check(_lib.mlmc_autotune_save(os.fsencode(path)))
+
+
+def mlmc_autotune_load(path: str) -> int:
+    n = ctypes.c_int()
+    _check(_lib.mlmc_autotune_load(os.fsencode(path), ctypes.byref(n)))
+    return n.value
+
+
+def mlmc_autotune_clear() -> None:
+    _check(_lib.mlmc_autotune_clear())
+
+
+def mlmc_autotune_entries() -> int:
+    return int(_lib.mlmc_autotune_entries())
+
+
+def mlmc_autotune_lookup(precision, payoff: str, M: int, level: int, N: int):
+    """(threads_per_block, lanes_per_path, waves) or None."""
+    out = mlmc_launch()
+    st = _lib.mlmc_autotune_lookup(_prec(precision), PAYOFFS[payoff], M, level, N, ctypes.byref(out))
+    if st != MLMC_OK:
+        return None
+    return out.threads_per_block, out.lanes_per_path, out.blocks

@@ -1,0 +1,45 @@
+"""The autotuner on the GPU: it fills the table, and the shapes it picks keep every sample equal
+to the oracle's within the level tolerances (launch shapes never change the samples)."""
+import numpy as np
+import pytest
+
+import oracle
+
+from gpu_helpers import oracle_problem, run_level
+
+pytestmark = pytest.mark.gpu
+
+GBM = dict(S0=100.0, r=0.05, sigma=0.2, T=1.0, K=100.0, cash=1.0)
+
+
+@pytest.fixture()
+def mlmc():
+    from paper_1505_00965_gb300 import build
+
+    build.build()
+    from paper_1505_00965_gb300 import mlmc as binding
+
+    binding.mlmc_autotune_clear()
+    yield binding
+    binding.mlmc_autotune_clear()
+
+
+def test_autotune_then_parity(mlmc, tmp_path):
+    n = mlmc.mlmc_autotune(M=4, max_level=5, precision="fp32", payoff="asian")
+    assert n > 0 and mlmc.mlmc_autotune_entries() == n
+    for level in range(6):
+        shape = mlmc.mlmc_autotune_lookup("fp32", "asian", 4, level, 1 << 16)
+        assert shape is not None and shape[0] in (128, 256, 512) and shape[1] in (1, 2, 4, 8, 16, 32)
+    p = mlmc.Problem(payoff="asian", **GBM)
+    op = oracle_problem(oracle, p)
+    for level, N in [(0, 5000), (3, 2000), (5, 600)]:
+        sums, y = run_level(mlmc, level, 4, N, 9, p, 3, "fp32")
+        yo = oracle.level_samples(level, 4, N, op, seed=3, first=9, stream="fp32")
+        bound = 8.0 * (2.0 ** -24 * np.sqrt(4 ** level + 1) + 2e-6) * 100.0 * np.exp(0.05)
+        assert np.max(np.abs(y - yo)) <= bound
+    path = tmp_path / "t.json"
+    mlmc.mlmc_autotune_save(str(path))
+    mlmc.mlmc_autotune_clear()
+    assert mlmc.mlmc_autotune_load(str(path)) == n
+    est = mlmc.mlmc_estimate(1e-2, p, 1)
+    assert est.converged
