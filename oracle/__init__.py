@@ -11,7 +11,8 @@ Carlo for Option Valuation"):
 * ``philox``, ``normals``           -- the random input dW of Eq. (em); the stream is a reading
                                         (Philox4x32-10 + Box--Muller), see ``mlmc_oracle.c``.
 * ``sample_paths``, ``em_path``     -- Euler--Maruyama (Sec. 2, Eq. em) on the fine and coarse
-                                        grids of one Brownian path (Sec. 5, Fig. 2).
+                                        grids of one Brownian path (Sec. 5, Fig. 2); Problem.scheme
+                                        "milstein" switches both grids to the Milstein step (Sec. 5).
 * ``payoff``                        -- discounted payoffs (Sec. 5 and Sec. 6).
 * ``level_samples``, ``level_sums`` -- the level estimators of Eqs. (mlmc:Yzero) and (Yldef).
 * ``driver.estimate``               -- telescoping sum Eq. (mlmc:ident) with N_l chosen from
@@ -35,6 +36,7 @@ _lib = None
 
 PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "linear": 100, "geo_asian": 101}
 STREAMS = {"fp64": 0, "fp32": 1}
+SCHEMES = {"em": 0, "milstein": 1}
 MODE_COUPLED, MODE_FINE_ONLY = 0, 1
 TAG_PATHS, TAG_CV_MEAN, TAG_CV_TRAIN = 0, 1, 2
 
@@ -52,7 +54,7 @@ def build(force: bool = False) -> str:
 class _Problem(ctypes.Structure):
     _fields_ = [("S0", ctypes.c_double), ("r", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("T", ctypes.c_double), ("payoff", ctypes.c_int), ("K", ctypes.c_double),
-                ("Q", ctypes.c_double)]
+                ("Q", ctypes.c_double), ("scheme", ctypes.c_int)]
 
 
 def _load():
@@ -74,6 +76,8 @@ def _load():
             lib.oracle_sample_normals.restype = None
             lib.oracle_em_path.argtypes = [i32, dbl, dbl, dbl, dbl, dptr, dptr]
             lib.oracle_em_path.restype = None
+            lib.oracle_milstein_path.argtypes = [i32, dbl, dbl, dbl, dbl, dptr, dptr]
+            lib.oracle_milstein_path.restype = None
             lib.oracle_payoff.argtypes = [i32, dbl, dbl, dbl, dbl, dptr, i32]
             lib.oracle_payoff.restype = dbl
             lib.oracle_sample_paths.argtypes = [i32, i32, u64, i32, pp, u64, i32, dptr, dptr, dptr]
@@ -99,9 +103,11 @@ class Problem:
     payoff: str = "european"
     K: float = 100.0
     Q: float = 1.0
+    scheme: str = "em"
 
     def c(self) -> _Problem:
-        return _Problem(self.S0, self.r, self.sigma, self.T, PAYOFFS[self.payoff], self.K, self.Q)
+        return _Problem(self.S0, self.r, self.sigma, self.T, PAYOFFS[self.payoff], self.K, self.Q,
+                        SCHEMES[self.scheme])
 
 
 def _dp(a: np.ndarray):

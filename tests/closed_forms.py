@@ -79,3 +79,29 @@ def central_moments_from_sums(sums, N):
     var = m2 - m1 ** 2
     mu4 = m4 - 4 * m1 * m3 + 6 * m1 ** 2 * m2 - 3 * m1 ** 4
     return m1, var, mu4
+
+
+def milstein_linear_moments(level, M, S0, r, sigma, T):
+    """Exact E[Y_l] and Var[Y_l] of the linear payoff for the Milstein scheme on GBM:
+    factors f = 1 + r h + sigma dW + sigma^2 (dW^2 - h) / 2.  E[f] = 1 + r h and
+    E[f^2] = (1 + r h)^2 + sigma^2 h + sigma^4 h^2 / 2 (dW odd moments vanish, E[dW^4] = 3 h^2).
+    Per coarse block (fine factors A_i, coarse factor B on the summed increment):
+    E[prod A_i B] = (1 + r H) a^M + M sigma^2 h a^(M-1) + sigma^4 h^2 (M a^(M-1) + M (M-1) a^(M-2)) / 2,
+    a = 1 + r h."""
+    n = M ** level
+    h = T / n
+    a = 1 + r * h
+    Ef = S0 * a ** n
+    Ef2 = S0 ** 2 * (a * a + sigma ** 2 * h + 0.5 * sigma ** 4 * h * h) ** n
+    if level == 0:
+        return Ef, Ef2 - Ef ** 2
+    nc = n // M
+    H = M * h
+    b = 1 + r * H
+    Ec = S0 * b ** nc
+    Ec2 = S0 ** 2 * (b * b + sigma ** 2 * H + 0.5 * sigma ** 4 * H * H) ** nc
+    cross = (b * a ** M + M * sigma ** 2 * h * a ** (M - 1)
+             + 0.5 * sigma ** 4 * h * h * (M * a ** (M - 1) + M * (M - 1) * a ** (M - 2)))
+    Efc = S0 ** 2 * cross ** nc
+    EY = Ef - Ec
+    return EY, Ef2 - 2 * Efc + Ec2 - EY ** 2

@@ -208,3 +208,44 @@ def test_invalid_arguments_rejected():
         oracle.level_sums(2, 3, 10, p, 1)
     s, c = oracle.level_sums(2, 4, 0, p, 1)
     assert list(s) == [0, 0, 0, 0] and c == 0
+
+
+@pytest.mark.parametrize("level,N", [(0, 200_000), (1, 200_000), (2, 100_000), (4, 10_000)])
+def test_milstein_linear_payoff_matches_exact_moments(level, N):
+    """Milstein (Sec. 5): E[Y_l] and Var[Y_l] of the linear payoff have closed forms."""
+    from closed_forms import milstein_linear_moments
+
+    p = Problem(payoff="linear", scheme="milstein", **GBM)
+    sums, _ = oracle.level_sums(level, 4, N, p, seed=4242 + level)
+    mean, var, mu4 = central_moments_from_sums(sums, N)
+    EY, VY = milstein_linear_moments(level, 4, **GBM)
+    assert abs(mean - EY) < 4.5 * math.sqrt(VY / N)
+    assert abs(var - VY) < 4.5 * math.sqrt(max(mu4 - var ** 2, 0.0) / N)
+
+
+def test_milstein_coarse_path_rebuilt_step_by_step():
+    p = Problem(payoff="european", scheme="milstein", **GBM)
+    dW, fine, coarse = oracle.sample_paths(2, 4, 3, p, seed=8)
+    h = 1.0 / 16
+    X = 100.0
+    for j in range(4):
+        dWc = 0.0
+        for q in range(4):
+            dWc += dW[4 * j + q]
+        X = X + 0.05 * X * (4 * h) + 0.2 * X * dWc + 0.5 * 0.2 * 0.2 * X * (dWc * dWc - 4 * h)
+        assert coarse[j + 1] == X
+
+
+def test_milstein_variance_decays_twice_as_fast():
+    """Strong order one of Milstein gives V_l = O(h_l^2) for a Lipschitz payoff: beta ~ 2
+    (against ~1 for Euler--Maruyama), which puts MLMC in the eps^-2 regime of the Theorem."""
+    p = Problem(payoff="european", scheme="milstein", **GBM)
+    ls = [2, 3, 4, 5]
+    Ns = {2: 40_000, 3: 20_000, 4: 8_000, 5: 4_000}
+    logv = []
+    for l in ls:
+        s, _ = oracle.level_sums(l, 4, Ns[l], p, seed=31)
+        _, v, _ = central_moments_from_sums(s, Ns[l])
+        logv.append(math.log(v, 4))
+    beta = -np.polyfit(ls, logv, 1)[0]
+    assert 1.5 < beta < 2.6, beta
