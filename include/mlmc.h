@@ -51,9 +51,13 @@ typedef enum mlmc_status {
 /* Model: geometric Brownian motion dS = r S dt + sigma S dW, S(0) = S0, on [0, T]
  * (the SDE of Sec. 2, Eq. sde, with f(x) = r x and g(x) = sigma x as in Sec. 6). */
 typedef enum mlmc_model_kind { MLMC_MODEL_GBM = 0 } mlmc_model_kind;
+/* Time-stepping scheme on both grids: Euler--Maruyama (Sec. 2, Eq. em) or Milstein (Sec. 5,
+ * the strongly more accurate scheme that gives beta > gamma): for GBM the Milstein step adds
+ * sigma^2 X (dW^2 - dt) / 2, the coarse step using the summed increment and its own dt. */
+typedef enum mlmc_scheme { MLMC_EULER_MARUYAMA = 0, MLMC_MILSTEIN = 1 } mlmc_scheme;
 typedef struct mlmc_model {
     int32_t kind;          /* mlmc_model_kind */
-    int32_t reserved;      /* must be 0 */
+    int32_t scheme;        /* mlmc_scheme */
     double S0, r, sigma, T; /* S0 > 0, sigma > 0, T > 0, all finite */
 } mlmc_model;
 
@@ -70,17 +74,23 @@ typedef enum mlmc_payoff_kind {
     MLMC_EUROPEAN = 0, MLMC_ASIAN = 1, MLMC_LOOKBACK = 2, MLMC_DIGITAL = 3,
     MLMC_LINEAR_TEST = 100, MLMC_GEO_ASIAN_TEST = 101
 } mlmc_payoff_kind;
+/* What a level sample returns: the coupled difference Y = P_l - P_{l-1} of multilevel Monte
+ * Carlo (Eq. Yldef), or P_l alone -- standard Monte Carlo with Euler--Maruyama at step T / M^l
+ * (Sec. 3), the comparison of Sec. 6. */
+typedef enum mlmc_estimator { MLMC_COUPLED = 0, MLMC_SINGLE_LEVEL = 1 } mlmc_estimator;
 typedef struct mlmc_payoff {
     int32_t kind;          /* mlmc_payoff_kind */
-    int32_t reserved;      /* must be 0 */
+    int32_t estimator;     /* mlmc_estimator (the drivers require MLMC_COUPLED) */
     double K;              /* strike, finite */
     double cash;           /* digital cash amount (Sec. 6 uses 100), finite */
 } mlmc_payoff;
 
-/* Path arithmetic precision.  Moment sums are FP64 in both. */
+/* Path arithmetic precision.  Moment sums are FP64 in all three. */
 typedef enum mlmc_precision {
     MLMC_FP64 = 0,         /* FP64 normals (32-bit uniforms) and FP64 paths */
-    MLMC_FP32_PATH = 1     /* FP32 normals (23-bit uniforms) and FP32 paths */
+    MLMC_FP32_PATH = 1,    /* FP32 normals (23-bit uniforms) and FP32 paths */
+    MLMC_FP64_STREAM32 = 2 /* FP64 arithmetic on the FP32 stream's 23-bit uniforms: the same samples
+                              as MLMC_FP32_PATH, so the two differ by FP32 roundoff alone */
 } mlmc_precision;
 
 /* Random-number stream tags (the `tag` field of the Philox counter). */

@@ -56,14 +56,16 @@ bool valid_payoff_kind(int k)
 int check_problem(const mlmc_model *model, const mlmc_payoff *payoff)
 {
     if (!model || !payoff) return fail(MLMC_EINVAL, "model and payoff must not be NULL");
-    if (model->kind != MLMC_MODEL_GBM || model->reserved != 0)
-        return fail(MLMC_EINVAL, "unsupported model kind %d", model->kind);
+    if (model->kind != MLMC_MODEL_GBM) return fail(MLMC_EINVAL, "unsupported model kind %d", model->kind);
+    if (model->scheme != MLMC_EULER_MARUYAMA && model->scheme != MLMC_MILSTEIN)
+        return fail(MLMC_EINVAL, "unsupported scheme %d", model->scheme);
     if (!(model->S0 > 0) || !std::isfinite(model->S0) || !(model->sigma > 0) ||
         !std::isfinite(model->sigma) || !(model->T > 0) || !std::isfinite(model->T) ||
         !std::isfinite(model->r))
         return fail(MLMC_EINVAL, "GBM needs finite S0 > 0, sigma > 0, T > 0 and r");
-    if (!valid_payoff_kind(payoff->kind) || payoff->reserved != 0)
-        return fail(MLMC_EINVAL, "unsupported payoff kind %d", payoff->kind);
+    if (!valid_payoff_kind(payoff->kind)) return fail(MLMC_EINVAL, "unsupported payoff kind %d", payoff->kind);
+    if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_SINGLE_LEVEL)
+        return fail(MLMC_EINVAL, "unsupported estimator %d", payoff->estimator);
     if (!std::isfinite(payoff->K) || !std::isfinite(payoff->cash))
         return fail(MLMC_EINVAL, "payoff K and cash must be finite");
     return MLMC_OK;
@@ -98,17 +100,17 @@ int max_resident_blocks(const void *kernel, int threads, int *out)
 }
 
 // Launch shape for one level: explicit fields of `launch` win, zeros are filled in.
-int plan_level(int level, int M, uint64_t N, int precision, int payoff, const mlmc_launch *launch,
+int plan_level(int level, int M, uint64_t N, int precision, int payoff, int scheme, const mlmc_launch *launch,
                Plan *plan)
 {
-    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
-        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
     if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
     const long nf = ipow(M, level);
     const int unit = std::max(M, 4);  // a lane's chunk holds whole Philox blocks and coarse steps
     // a shape chosen by the autotuner fills the fields the caller left at zero
     TunedShape tuned;
-    const bool have_tuned = tuned_lookup(precision, payoff, M, level, N, &tuned);
+    const bool have_tuned = scheme == MLMC_EULER_MARUYAMA && tuned_lookup(precision, payoff, M, level, N, &tuned);
     int threads = launch && launch->threads_per_block ? launch->threads_per_block
                                                       : (have_tuned ? tuned.threads : 256);
     if (threads < 32 || threads > 1024 || threads % 32)
@@ -138,8 +140,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
     const bool split = lanes > 1;
     const bool small = nf < 4;
     const int mt = small ? -1 : (M == 4 ? 4 : 0);
-    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split)
-                                               : level_kernel_fp64(payoff, mt, split);
+    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split, scheme)
+                                               : level_kernel_fp64(payoff, mt, split, scheme);
     if (!plan->kernel) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
     int max_blocks = 0;
     int rc = max_resident_blocks(plan->kernel, threads, &max_blocks);
@@ -162,7 +164,7 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, const ml
 }
 
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
-                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes)
+                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes, int precision)
 {
     const long nf = ipow(M, level);
     p.S0 = m->S0;
@@ -187,6 +189,10 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.nf = (int)nf;
     p.lanes = lanes;
     p.payoff = pay->kind;
+    p.c2 = 0.5 * m->sigma * m->sigma * h;
+    p.scheme = m->scheme;
+    p.fine_only = pay->estimator == MLMC_SINGLE_LEVEL ? 1 : 0;
+    p.u23 = precision == MLMC_FP64_STREAM32 ? 1 : 0;
     p.partials = nullptr;
     p.out = nullptr;
     p.ticket = nullptr;
@@ -238,7 +244,7 @@ size_t mlmc_level_workspace_bytes(int level, int M, uint64_t N, int precision,
 {
     if (check_level(level, M)) return 0;
     Plan plan;
-    if (plan_level(level, M, N, precision, kEuropean, launch, &plan)) return 0;
+    if (plan_level(level, M, N, precision, kEuropean, MLMC_EULER_MARUYAMA, launch, &plan)) return 0;
     // The grid the planner picks depends on the payoff's kernel; size for the largest grid any
     // of them can get: an explicit block count, or 32 resident blocks on every SM.
     int sms = 0;
@@ -260,7 +266,7 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const ml
     if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
     if (rc) return rc;
     if (N == 0) {
         CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
@@ -272,7 +278,7 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const ml
         return fail(MLMC_EINVAL, "workspace of %zu bytes is smaller than the %zu this launch needs",
                     workspace_bytes, workspace_bytes_for_blocks(plan.blocks));
     LevelParams p;
-    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes, precision);
     p.out = d_sums;
     p.y_out = d_y;
     return launch_level(plan, p, d_workspace, st);
@@ -334,7 +340,7 @@ int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const 
                     kNoAllocMaxBlocks, kNoAllocScratchBytes);
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
     if (rc) return rc;
     if (N == 0) {
         CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
@@ -345,7 +351,7 @@ int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const 
     rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     LevelParams p;
-    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+    fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes, precision);
     p.out = d_sums;
     p.y_out = d_y;
     // The ticket keeps whatever the last call left; clear it on the stream before the launch.
@@ -365,7 +371,7 @@ int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_
     if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, launch, &plan);
+    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
     if (rc) return rc;
     double out[4] = {0.0, 0.0, 0.0, 0.0};
     if (N > 0) {
@@ -374,7 +380,7 @@ int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_
         CUDA_TRY(cudaMallocAsync(&ws, ws_bytes, st));
         cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, st);
         LevelParams p;
-        fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes);
+        fill_params(p, level, M, N, first, model, payoff, seed, tag, plan.lanes, precision);
         p.out = (double *)((char *)ws + workspace_bytes_for_blocks(plan.blocks));
         if (e == cudaSuccess) rc = launch_level(plan, p, ws, st);
         else rc = fail(MLMC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
@@ -412,8 +418,8 @@ int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int 
     if (Lmin < 1 || Lmax < Lmin || Lmax >= MLMC_MAX_LEVELS || ipow(M, Lmax) > (1L << 24))
         return fail(MLMC_EINVAL, "need 1 <= Lmin <= Lmax < %d and M^Lmax <= 2^24", MLMC_MAX_LEVELS);
     if (N0 < 2) return fail(MLMC_EINVAL, "N0 must be at least 2");
-    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
-        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
     return MLMC_OK;
 }
 
@@ -429,6 +435,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
     rc = check_estimate_args(eps, M, Lmin, Lmax, N0, precision);
     if (rc) return rc;
+    if (payoff->estimator != MLMC_COUPLED) return fail(MLMC_EINVAL, "the adaptive driver needs the coupled estimator");
     cudaStream_t st = (cudaStream_t)stream;
 
     // One workspace for every launch of this call: launches are ordered on `st`.
@@ -470,14 +477,15 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         for (int l = 0; l <= L; ++l) {
             if (!dN[l]) continue;
             Plan plan;
-            rc = plan_level(l, M, dN[l], precision, payoff->kind, nullptr, &plan);
+            rc = plan_level(l, M, dN[l], precision, payoff->kind, model->scheme, nullptr, &plan);
             if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
             if (rc) {
                 cleanup();
                 return rc;
             }
             LevelParams p;
-            fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+            fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes,
+                        precision);
             p.out = d_sums + 4 * l;
             rc = launch_level(plan, p, ws, st);
             if (rc) {

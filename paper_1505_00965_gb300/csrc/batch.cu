@@ -140,8 +140,11 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
     if (n < 1 || !problems || !results) return fail(MLMC_EINVAL, "need n >= 1 and non-NULL problems and results");
     int rc = check_estimate_args(1.0, M, Lmin, Lmax, N0, precision);
     if (rc) return rc;
+    if (precision == MLMC_FP64_STREAM32) return fail(MLMC_EINVAL, "batches run MLMC_FP64 or MLMC_FP32_PATH");
     for (int i = 0; i < n; ++i) {
         rc = check_problem(&problems[i].model, &problems[i].payoff);
+        if (!rc && (problems[i].model.scheme != MLMC_EULER_MARUYAMA || problems[i].payoff.estimator != MLMC_COUPLED))
+            rc = fail(MLMC_EINVAL, "batches run the coupled Euler--Maruyama estimator");
         if (!rc && !(problems[i].eps > 0 && std::isfinite(problems[i].eps)))
             rc = fail(MLMC_EINVAL, "eps must be positive and finite");
         if (rc) {
@@ -212,7 +215,7 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
                 const uint64_t spc = (uint64_t)std::max(1.0, std::floor(W / (double)nf));
                 LevelParams p;
                 fill_params(p, l, M, dN[l], drv[i].samples_taken(l), &problems[i].model, &problems[i].payoff,
-                            problems[i].seed, MLMC_TAG_PATHS, batch_lanes(nf, M, spc));
+                            problems[i].seed, MLMC_TAG_PATHS, batch_lanes(nf, M, spc), precision);
                 BatchRange r;
                 r.begin = (uint32_t)chunks.size();
                 for (uint64_t off = 0; off < dN[l]; off += spc) {

@@ -92,7 +92,7 @@ int launch_cv_level(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, ui
                     float *d_r, float *d_g, void *ws, int blocks, cudaStream_t st)
 {
     LevelParams p;
-    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_PATHS, 1);
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_PATHS, 1, MLMC_FP32_PATH);
     p.ticket = (unsigned *)ws;
     p.partials = (double *)((char *)ws + kTicketBytes);
     const float *params = cv->d_params[level];
@@ -105,7 +105,7 @@ int launch_cv_mean(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uin
                    float *d_g, void *ws, int blocks, cudaStream_t st)
 {
     LevelParams p;
-    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_MEAN, 1);
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_MEAN, 1, MLMC_FP32_PATH);
     p.ticket = (unsigned *)ws;
     p.partials = (double *)((char *)ws + kTicketBytes);
     const float *params = cv->d_params[level];
@@ -203,6 +203,8 @@ int mlmc_cv_create(int M, const mlmc_model *model, const mlmc_payoff *payoff, ml
 {
     int rc = check_problem(model, payoff);
     if (rc) return rc;
+    if (model->scheme != MLMC_EULER_MARUYAMA || payoff->estimator != MLMC_COUPLED)
+        return fail(MLMC_EINVAL, "the control variate runs the coupled Euler--Maruyama estimator");
     if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
     if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
     mlmc_cv *cv = new (std::nothrow) mlmc_cv();
@@ -319,7 +321,7 @@ int mlmc_cv_training_data(const mlmc_cv *cv, int level, uint64_t N, uint64_t fir
     rc = grid_for(k, N, &blocks);
     if (rc) return rc;
     LevelParams p;
-    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_TRAIN, 1);
+    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_TRAIN, 1, MLMC_FP32_PATH);
     void *args[] = {&p, &d_X, &d_Y};
     CUDA_TRY(cudaLaunchKernel(k, dim3(blocks), dim3(kCvThreads), args, 0, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -497,7 +499,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         const uint64_t nt = std::max<uint64_t>(1u << 14, (uint64_t)(1u << 22) >> std::min(2 * l, 20));
         {
             Plan plan;
-            rc = plan_level(l, M, nt, MLMC_FP32_PATH, payoff->kind, nullptr, &plan);
+            rc = plan_level(l, M, nt, MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr, &plan);
             if (rc) return cleanup(rc);
             int cvb = 0, mb = 0;
             rc = grid_for(cv_level_kernel_for(payoff->kind), nt, &cvb);
@@ -509,7 +511,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
             rc = with_workspace(sums_workspace(wb, 8), st, [&](void *ws) {
                 for (int rep = 0; rep < 2; ++rep) {  // first pass warms up, second is timed
                     LevelParams p;
-                    fill_params(p, l, M, nt, 0, model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+                    fill_params(p, l, M, nt, 0, model, payoff, seed, MLMC_TAG_PATHS, plan.lanes, MLMC_FP32_PATH);
                     p.out = d_out;
                     CUDA_TRY(cudaEventRecord(ev0, st));
                     int r2 = launch_level(plan, p, ws, st);
@@ -633,11 +635,12 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
                 launches += 2;
             } else {
                 Plan plan;
-                rc = plan_level(l, M, dN[l], MLMC_FP32_PATH, payoff->kind, nullptr, &plan);
+                rc = plan_level(l, M, dN[l], MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr, &plan);
                 if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
                 if (!rc) {
                     LevelParams p;
-                    fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes);
+                    fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes,
+                                MLMC_FP32_PATH);
                     p.out = d_sums + stride * l;
                     rc = launch_level(plan, p, ws, st);
                 }

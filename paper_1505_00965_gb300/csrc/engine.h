@@ -28,6 +28,10 @@ struct LevelParams {
     int lanes;        // lanes per sample (1 = one thread per sample)
     int small;        // 1 when M^l < 4: 4 / M^l samples share one Philox block
     int payoff;       // payoff code (the batched kernel selects its code path from it)
+    double c2;        // sigma^2 h / 2: the Milstein term's scale on the fine grid
+    int scheme;       // 0 Euler--Maruyama, 1 Milstein
+    int fine_only;    // 1: Y = P_l alone (single-level estimator)
+    int u23;          // FP64 arithmetic on the FP32 stream's 23-bit uniforms
     double *partials; // [gridDim.x][4] block partial sums (workspace)
     double *out;      // [4] level sums (device)
     unsigned *ticket; // completion counter (workspace), zero between launches
@@ -45,8 +49,8 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 
 // Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel and
 // -1 for the kernel of levels with M^l < 4.
-const void *level_kernel_fp32(int payoff, int mt, bool split);
-const void *level_kernel_fp64(int payoff, int mt, bool split);
+const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme);
+const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme);
 
 // Batched rounds: one chunk of samples of one task (a level of one problem).
 struct BatchChunk {

@@ -32,10 +32,10 @@ struct Plan {
     const void *kernel;
     int threads, lanes, blocks;
 };
-int plan_level(int level, int M, uint64_t N, int precision, int payoff, const mlmc_launch *launch,
+int plan_level(int level, int M, uint64_t N, int precision, int payoff, int scheme, const mlmc_launch *launch,
                Plan *plan);
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
-                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes);
+                 const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes, int precision);
 double level_cost(int level, int M);
 int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st);
 int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int precision);

@@ -2,9 +2,9 @@
 #include "level_kernel.cuh"
 
 namespace mlmcgb {
-const void *level_kernel_fp32(int payoff, int mt, bool split)
+const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme)
 {
-    return select_level_kernel<float>(payoff, mt, split);
+    return select_level_kernel<float>(payoff, mt, split, scheme);
 }
 const void *batch_kernel_fp32(int mt)
 {

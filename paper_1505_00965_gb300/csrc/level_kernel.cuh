@@ -89,46 +89,70 @@ __device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
     }
 }
 
-// Fine and coarse paths of one sample on a level with M^l >= 8 (one normal per fine step),
-// over the Philox calls [j0, j1) (4 fine steps per call).
-template <typename R, int MT, int PAY, bool SPLIT>
+// Fine and coarse paths of one sample on a level with M^l >= 4 (one normal per fine step), over
+// the Philox calls [j0, j1) (4 fine steps per call).  Euler--Maruyama: d = r h + sigma dW and the
+// coarse factor's d is the sum of the M fine ones.  Milstein (MIL): d = r h + sigma dW
+// + sigma^2 (dW^2 - h) / 2 = (r h - c2) + a z + c2 z^2 with a = sigma sqrt(h), c2 = sigma^2 h / 2,
+// and the coarse step the same formula on the summed increment with step M h.
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
 __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t slo, uint32_t shi,
                                                int j0, int j1, PathAcc<R, PAY, SPLIT> &fa,
                                                PathAcc<R, PAY, SPLIT> &ca)
 {
     const R a = R(p.a), rh = R(p.rh);
+    const R c2 = R(p.c2), rhm = R(p.rh - p.c2);
     R fS = fa.S, fsum = fa.sum, fhi = fa.hi, flo = fa.lo, fls = fa.lsum;
     R cS = ca.S, csum = ca.sum, chi = ca.hi, clo = ca.lo, cls = ca.lsum;
     R dc = R(0);
     int q = 0;
     const int M = MT ? MT : p.M;
+    const R rHm = R(M * (p.rh - p.c2));
+    const bool u23 = p.u23 != 0;
     for (int j = j0; j < j1; ++j) {
         const uint4 x = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
         R rho, c, s;
         R d[4];
-        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
-        R ra = rho * a;
-        d[0] = fma(ra, c, rh);
-        d[1] = fma(ra, s, rh);
-        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
-        ra = rho * a;
-        d[2] = fma(ra, c, rh);
-        d[3] = fma(ra, s, rh);
+        if constexpr (!MIL) {
+            BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
+            R ra = rho * a;
+            d[0] = fma(ra, c, rh);
+            d[1] = fma(ra, s, rh);
+            BoxMuller<R>::pair(x.z, x.w, rho, c, s, u23);
+            ra = rho * a;
+            d[2] = fma(ra, c, rh);
+            d[3] = fma(ra, s, rh);
+        } else {
+            BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
+            d[0] = rho * c;  // here d holds the normals z until the steps below
+            d[1] = rho * s;
+            BoxMuller<R>::pair(x.z, x.w, rho, c, s, u23);
+            d[2] = rho * c;
+            d[3] = rho * s;
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            em_step<R, PAY, SPLIT>(fS, fsum, fhi, flo, fls, d[k]);
-            dc += d[k];
-            if constexpr (MT != 0) {
-                if ((k + 1) % MT == 0) {
-                    em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dc);
-                    dc = R(0);
-                }
+            R dk;
+            if constexpr (MIL) {
+                dc += d[k];  // the coarse increment's sum of normals
+                dk = fma(fma(c2, d[k], a), d[k], rhm);
             } else {
-                if (++q == M) {
-                    em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dc);
-                    dc = R(0);
-                    q = 0;
-                }
+                dk = d[k];
+                dc += dk;
+            }
+            em_step<R, PAY, SPLIT>(fS, fsum, fhi, flo, fls, dk);
+            bool coarse_now;
+            if constexpr (MT != 0) {
+                coarse_now = (k + 1) % MT == 0;
+            } else {
+                coarse_now = ++q == M;
+                if (coarse_now) q = 0;
+            }
+            if (coarse_now) {
+                R dcs;
+                if constexpr (MIL) dcs = fma(fma(c2, dc, a), dc, rHm);
+                else dcs = dc;
+                em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dcs);
+                dc = R(0);
             }
         }
     }
@@ -256,7 +280,7 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
 
 // Y of sample s on a level with M^l >= 4, computed by the P lanes of one group (lane lig);
 // every lane of the group returns the same Y.
-template <typename R, int MT, int PAY, bool SPLIT>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
 __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig, int P)
 {
     const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
@@ -268,21 +292,23 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     fa.init(R(1));
     ca.init(R(1));
     if constexpr (!SPLIT) {
-        simulate_steps<R, MT, PAY, false>(p, slo, shi, 0, p.nf >> 2, fa, ca);
+        simulate_steps<R, MT, PAY, false, MIL>(p, slo, shi, 0, p.nf >> 2, fa, ca);
         const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
         const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
                                           R(p.nf) * logS0 + fa.lsum, inv_nf, p);
+        if (p.fine_only) return Pf;
         const R Pc = payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
                                           R(p.nf / p.M) * logS0 + ca.lsum, inv_nc, p);
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
-        simulate_steps<R, MT, PAY, true>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+        simulate_steps<R, MT, PAY, true, MIL>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
         const R steps_f = R(4 * calls);
         R tf, pf, hf, lf, tc, pc, hc, lc;
         join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
         join_chunks<R, PAY>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
         const R Pf = payoff_value<R, PAY>(tf, pf, hf, lf, inv_nf, p);
+        if (p.fine_only) return Pf;
         const R Pc = payoff_value<R, PAY>(tc, pc, hc, lc, inv_nc, p);
         return Pf - Pc;
     }
@@ -292,7 +318,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
 // thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
 // Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
 // sample first + i into y_out[i] when y_out is not NULL.
-template <typename R, int MT, int PAY, bool SPLIT>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
@@ -307,7 +333,7 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
         const uint64_t idx = base + g;
         const bool valid = idx < N;
         const uint64_t s = first + (valid ? idx : N - 1);
-        const R Y = sample_Y<R, MT, PAY, SPLIT>(p, s, lig, P);
+        const R Y = sample_Y<R, MT, PAY, SPLIT, MIL>(p, s, lig, P);
         if (valid && lig == 0) {
             if (y_out) y_out[idx] = (double)Y;
             add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -318,7 +344,7 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
 // Samples [first, first + N) of a level with M^l < 4.  G = 4 / M^l consecutive samples share
 // one Philox block: thread t takes blocks q = first / G + t, + T, ... and the G samples
 // q G .. q G + G - 1 that fall in the range; sample slot r takes normals r M^l .. of the block.
-template <typename R, int PAY>
+template <typename R, int PAY, bool MIL>
 __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first, uint64_t N,
                                             uint64_t t, uint64_t T, double m[4], float &b1,
                                             float &b2, float &b3, float &b4, int &nb,
@@ -330,20 +356,25 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const uint64_t q0 = first / G;
     const uint64_t nq = (end - 1) / G - q0 + 1;
     const R a = R(p.a), rh = R(p.rh), S0 = R(p.S0);
+    const R c2 = R(p.c2), rhm = R(p.rh - p.c2);
     const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
+    const bool u23 = p.u23 != 0;
     for (uint64_t u = t; u < nq; u += T) {
         const uint64_t q = q0 + u;
         const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3),
                                       p.key0, p.key1);
-        R rho, c, s, d[4];
-        BoxMuller<R>::pair(x.x, x.y, rho, c, s);
-        R ra = rho * a;
-        d[0] = fma(ra, c, rh);
-        d[1] = fma(ra, s, rh);
-        BoxMuller<R>::pair(x.z, x.w, rho, c, s);
-        ra = rho * a;
-        d[2] = fma(ra, c, rh);
-        d[3] = fma(ra, s, rh);
+        R rho, c, s, z[4], d[4];
+        BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
+        z[0] = rho * c;
+        z[1] = rho * s;
+        BoxMuller<R>::pair(x.z, x.w, rho, c, s, u23);
+        z[2] = rho * c;
+        z[3] = rho * s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (MIL) d[k] = fma(fma(c2, z[k], a), z[k], rhm);
+            else d[k] = fma(a, z[k], rh);
+        }
 #pragma unroll
         for (uint32_t r = 0; r < 4; ++r) {
             if (r >= G) break;
@@ -360,12 +391,20 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
                 const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
                 em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
                 em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
-                em_step<R, PAY, false>(cS, csum, chi, clo, cls, d0 + d1);
+                const R zc = z[2 * (r & 1)] + z[2 * (r & 1) + 1];
+                R dcs;
+                if constexpr (MIL) dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
+                else dcs = d0 + d1;
+                em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
                 const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
                 const R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls,
                                                   inv_nf, p);
-                const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
-                Y = Pf - Pc;
+                if (p.fine_only) {
+                    Y = Pf;
+                } else {
+                    const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
+                    Y = Pf - Pc;
+                }
             }
             if (y_out) y_out[sample - first] = (double)Y;
             add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -382,26 +421,26 @@ __device__ __forceinline__ void fold_batch(double m[4], float b1, float b2, floa
 }
 
 // One level, one thread (or P lanes) per sample, grid-stride over the samples.
-template <typename R, int MT, int PAY, bool SPLIT>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
 __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
 {
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
     int nb = 0;
-    regular_range<R, MT, PAY, SPLIT>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+    regular_range<R, MT, PAY, SPLIT, MIL>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                      (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
     fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
 }
 
 // Levels with M^l < 4 (level 0, and level 1 when M = 2).
-template <typename R, int PAY>
+template <typename R, int PAY, bool MIL>
 __global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
 {
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
     int nb = 0;
-    small_range<R, PAY>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+    small_range<R, PAY, MIL>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                         (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
     fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
@@ -426,9 +465,9 @@ __device__ __forceinline__ void batch_chunk(const LevelParams &p, uint64_t first
     case kGeoAsian: CALL(kGeoAsian); break;                                                     \
     default: break;                                                                             \
     }
-#define MLMC_SMALL(PAY) small_range<R, PAY>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SMALL(PAY) small_range<R, PAY, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
     if (p.small) {
         MLMC_BATCH_CASES(MLMC_SMALL)
     } else if (p.lanes > 1) {
@@ -478,44 +517,50 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelParams *__restric
 
 namespace mlmcgb {
 
-// Kernel for (payoff, M specialisation, split) at precision R; nullptr for an unknown payoff.
-template <typename R, int MT, bool SPLIT> const void *select_by_payoff(int payoff)
+// Kernel for (payoff, M specialisation, split, scheme) at precision R; nullptr for an unknown
+// payoff.
+template <typename R, int MT, bool SPLIT, bool MIL> const void *select_by_payoff(int payoff)
 {
     switch (payoff) {
-    case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, SPLIT>;
-    case kAsian: return (const void *)level_kernel<R, MT, kAsian, SPLIT>;
-    case kLookback: return (const void *)level_kernel<R, MT, kLookback, SPLIT>;
-    case kDigital: return (const void *)level_kernel<R, MT, kDigital, SPLIT>;
-    case kLinear: return (const void *)level_kernel<R, MT, kLinear, SPLIT>;
-    case kGeoAsian: return (const void *)level_kernel<R, MT, kGeoAsian, SPLIT>;
+    case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, SPLIT, MIL>;
+    case kAsian: return (const void *)level_kernel<R, MT, kAsian, SPLIT, MIL>;
+    case kLookback: return (const void *)level_kernel<R, MT, kLookback, SPLIT, MIL>;
+    case kDigital: return (const void *)level_kernel<R, MT, kDigital, SPLIT, MIL>;
+    case kLinear: return (const void *)level_kernel<R, MT, kLinear, SPLIT, MIL>;
+    case kGeoAsian: return (const void *)level_kernel<R, MT, kGeoAsian, SPLIT, MIL>;
     default: return nullptr;
     }
 }
 
-template <typename R> const void *select_small_kernel(int payoff)
+template <typename R, bool MIL> const void *select_small_kernel(int payoff)
 {
     switch (payoff) {
-    case kEuropean: return (const void *)level_small_kernel<R, kEuropean>;
-    case kAsian: return (const void *)level_small_kernel<R, kAsian>;
-    case kLookback: return (const void *)level_small_kernel<R, kLookback>;
-    case kDigital: return (const void *)level_small_kernel<R, kDigital>;
-    case kLinear: return (const void *)level_small_kernel<R, kLinear>;
-    case kGeoAsian: return (const void *)level_small_kernel<R, kGeoAsian>;
+    case kEuropean: return (const void *)level_small_kernel<R, kEuropean, MIL>;
+    case kAsian: return (const void *)level_small_kernel<R, kAsian, MIL>;
+    case kLookback: return (const void *)level_small_kernel<R, kLookback, MIL>;
+    case kDigital: return (const void *)level_small_kernel<R, kDigital, MIL>;
+    case kLinear: return (const void *)level_small_kernel<R, kLinear, MIL>;
+    case kGeoAsian: return (const void *)level_small_kernel<R, kGeoAsian, MIL>;
     default: return nullptr;
     }
 }
 
-// mt = -1 selects the kernel of levels with M^l < 4.
+template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bool split)
+{
+    if (mt < 0) return select_small_kernel<R, MIL>(payoff);
+    if (mt == 4) return split ? select_by_payoff<R, 4, true, MIL>(payoff) : select_by_payoff<R, 4, false, MIL>(payoff);
+    return split ? select_by_payoff<R, 0, true, MIL>(payoff) : select_by_payoff<R, 0, false, MIL>(payoff);
+}
+
+// mt = -1 selects the kernel of levels with M^l < 4; scheme 1 is Milstein.
+template <typename R> const void *select_level_kernel(int payoff, int mt, bool split, int scheme)
+{
+    return scheme == 1 ? select_scheme<R, true>(payoff, mt, split) : select_scheme<R, false>(payoff, mt, split);
+}
+
 template <typename R> const void *select_batch_kernel(int mt)
 {
     return mt == 4 ? (const void *)batch_kernel<R, 4> : (const void *)batch_kernel<R, 0>;
-}
-
-template <typename R> const void *select_level_kernel(int payoff, int mt, bool split)
-{
-    if (mt < 0) return select_small_kernel<R>(payoff);
-    if (mt == 4) return split ? select_by_payoff<R, 4, true>(payoff) : select_by_payoff<R, 4, false>(payoff);
-    return split ? select_by_payoff<R, 0, true>(payoff) : select_by_payoff<R, 0, false>(payoff);
 }
 
 }  // namespace mlmcgb

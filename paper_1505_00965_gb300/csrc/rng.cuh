@@ -68,7 +68,7 @@ template <typename R> struct BoxMuller;
 // the range where the hardware sine and cosine are most accurate; the sign goes into rho.
 template <> struct BoxMuller<float> {
     __device__ __forceinline__ static void pair(uint32_t xa, uint32_t xb, float &rho, float &c,
-                                                float &s)
+                                                float &s, bool = false)
     {
         const float f1 = __uint_as_float((xa & 0x007FFFFFu) | 0x3F800000u);
         const float f2 = __uint_as_float((xb & 0x007FFFFFu) | 0x3F800000u);
@@ -82,12 +82,14 @@ template <> struct BoxMuller<float> {
 };
 
 // FP64 stream: u = (x + 1) 2^-32 in (0, 1]; CUDA's double-precision log, sqrt and sincospi.
+// With u23 set, the FP32 stream's uniforms u = 1 - (x mod 2^23) 2^-23 instead (the samples of
+// the FP32 path, computed in FP64).
 template <> struct BoxMuller<double> {
     __device__ __forceinline__ static void pair(uint32_t xa, uint32_t xb, double &rho,
-                                                double &c, double &s)
+                                                double &c, double &s, bool u23 = false)
     {
-        const double u1 = ((double)xa + 1.0) * 0x1p-32;
-        const double u2 = ((double)xb + 1.0) * 0x1p-32;
+        const double u1 = u23 ? 1.0 - (double)(xa & 0x007FFFFFu) * 0x1p-23 : ((double)xa + 1.0) * 0x1p-32;
+        const double u2 = u23 ? 1.0 - (double)(xb & 0x007FFFFFu) * 0x1p-23 : ((double)xb + 1.0) * 0x1p-32;
         rho = sqrt(-2.0 * log(u1));
         sincospi(2.0 * u2, &s, &c);
     }

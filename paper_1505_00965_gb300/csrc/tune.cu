@@ -100,8 +100,8 @@ int mlmc_autotune(int M, int max_level, int precision, int payoff, void *stream,
 {
     int rc = check_level(max_level, M);
     if (rc) return rc;
-    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
-        return fail(MLMC_EINVAL, "precision must be MLMC_FP64 or MLMC_FP32_PATH");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
     mlmc_model model{MLMC_MODEL_GBM, 0, 100.0, 0.05, 0.2, 1.0};
     mlmc_payoff pay{payoff, 0, 100.0, 1.0};
     rc = check_problem(&model, &pay);
@@ -146,7 +146,7 @@ int mlmc_autotune(int M, int max_level, int precision, int payoff, void *stream,
                     for (int oversub : {1, 2}) {
                         Plan plan;
                         mlmc_launch probe{threads, lanes, 0, 0};
-                        rc = plan_level(level, M, N, precision, payoff, &probe, &plan);
+                        rc = plan_level(level, M, N, precision, payoff, MLMC_EULER_MARUYAMA, &probe, &plan);
                         if (rc) continue;
                         int resident = 0;
                         if (max_resident_blocks(plan.kernel, threads, &resident)) continue;

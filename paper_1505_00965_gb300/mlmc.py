@@ -26,8 +26,10 @@ _lib = ctypes.CDLL(LIB_PATH)
 MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ETIMEOUT, MLMC_ENOTIMPL = range(7)
 MLMC_MODEL_GBM = 0
 PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "linear": 100, "geo_asian": 101}
-MLMC_FP64, MLMC_FP32_PATH = 0, 1
-PRECISIONS = {"fp64": MLMC_FP64, "fp32": MLMC_FP32_PATH}
+MLMC_FP64, MLMC_FP32_PATH, MLMC_FP64_STREAM32 = 0, 1, 2
+PRECISIONS = {"fp64": MLMC_FP64, "fp32": MLMC_FP32_PATH, "fp64_stream32": MLMC_FP64_STREAM32}
+SCHEMES = {"em": 0, "milstein": 1}
+ESTIMATORS = {"coupled": 0, "single": 1}
 MLMC_TAG_PATHS, MLMC_TAG_CV_MEAN, MLMC_TAG_CV_TRAIN = 0, 1, 2
 MLMC_MAX_LEVELS = 16
 
@@ -39,12 +41,12 @@ class MLMCError(RuntimeError):
 
 
 class mlmc_model(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("S0", ctypes.c_double),
+    _fields_ = [("kind", ctypes.c_int32), ("scheme", ctypes.c_int32), ("S0", ctypes.c_double),
                 ("r", ctypes.c_double), ("sigma", ctypes.c_double), ("T", ctypes.c_double)]
 
 
 class mlmc_payoff(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("K", ctypes.c_double),
+    _fields_ = [("kind", ctypes.c_int32), ("estimator", ctypes.c_int32), ("K", ctypes.c_double),
                 ("cash", ctypes.c_double)]
 
 
@@ -157,12 +159,14 @@ class Problem:
     payoff: str = "european"
     K: float = 100.0
     cash: float = 1.0
+    scheme: str = "em"            # "em" (Euler--Maruyama) or "milstein"
+    estimator: str = "coupled"    # "coupled" (P_l - P_{l-1}) or "single" (P_l, standard MC)
 
     def model(self) -> mlmc_model:
-        return mlmc_model(MLMC_MODEL_GBM, 0, self.S0, self.r, self.sigma, self.T)
+        return mlmc_model(MLMC_MODEL_GBM, SCHEMES[self.scheme], self.S0, self.r, self.sigma, self.T)
 
     def payoff_struct(self) -> mlmc_payoff:
-        return mlmc_payoff(PAYOFFS[self.payoff], 0, self.K, self.cash)
+        return mlmc_payoff(PAYOFFS[self.payoff], ESTIMATORS[self.estimator], self.K, self.cash)
 
 
 def _launch(launch) -> mlmc_launch | None:
@@ -288,7 +292,7 @@ def mlmc_estimate_batch(problems, M: int = 4, Lmin: int = 2, Lmax: int = 8, N0: 
     arr = (mlmc_problem * n)()
     for i, q in enumerate(problems):
         if isinstance(q, dict):
-            prob = Problem(**{k: q[k] for k in ("S0", "r", "sigma", "T", "payoff", "K", "cash") if k in q})
+            prob = Problem(**{k: q[k] for k in ("S0", "r", "sigma", "T", "payoff", "K", "cash", "scheme") if k in q})
             eps, seed = q["eps"], q["seed"]
         else:
             prob, eps, seed = q

@@ -21,7 +21,7 @@ def run_level(mlmc, level, M, N, first, prob, seed, precision, launch=None, tag=
 
 def oracle_problem(oracle, prob):
     return oracle.Problem(S0=prob.S0, r=prob.r, sigma=prob.sigma, T=prob.T, payoff=prob.payoff, K=prob.K,
-                          Q=prob.cash)
+                          Q=prob.cash, scheme=prob.scheme)
 
 
 def moment_sums(y):

@@ -80,6 +80,27 @@ def test_invalid_arguments_rejected_on_host(kw, msg):
     assert msg in str(ei.value)
 
 
+def test_invalid_scheme_and_estimator(lib):
+    from paper_1505_00965_gb300 import mlmc
+
+    sums = (ctypes.c_double * 4)()
+    cost = ctypes.c_double()
+    p = mlmc.mlmc_payoff(0, 0, 100.0, 1.0)
+    m = mlmc.mlmc_model(0, 2, 100.0, 0.05, 0.2, 1.0)
+    assert lib.mlmc_level_sums(2, 4, ctypes.c_uint64(10), ctypes.byref(m), ctypes.byref(p), ctypes.c_uint64(1),
+                               sums, ctypes.byref(cost)) == mlmc.MLMC_EINVAL
+    m = mlmc.mlmc_model(0, 0, 100.0, 0.05, 0.2, 1.0)
+    p = mlmc.mlmc_payoff(0, 5, 100.0, 1.0)
+    assert lib.mlmc_level_sums(2, 4, ctypes.c_uint64(10), ctypes.byref(m), ctypes.byref(p), ctypes.c_uint64(1),
+                               sums, ctypes.byref(cost)) == mlmc.MLMC_EINVAL
+    with pytest.raises(mlmc.MLMCError) as ei:
+        mlmc.mlmc_estimate(1e-2, mlmc.Problem(estimator="single"), 1)
+    assert ei.value.status == mlmc.MLMC_EINVAL
+    with pytest.raises(mlmc.MLMCError) as ei:
+        mlmc.mlmc_estimate_batch([(mlmc.Problem(scheme="milstein"), 1e-2, 1)])
+    assert ei.value.status == mlmc.MLMC_EINVAL
+
+
 def test_invalid_payoff_kind_and_overflow(lib):
     from paper_1505_00965_gb300 import mlmc
 

@@ -203,3 +203,47 @@ def test_workspace_reuse_across_grid_sizes(mlmc):
     for i, (l, n, b) in enumerate(shapes):
         ref, _ = run_level(mlmc, l, 4, n, 11, p, 3, "fp32", launch={"blocks": b})
         np.testing.assert_array_equal(outs[i].cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("payoff", ["european", "asian", "lookback", "linear"])
+@pytest.mark.parametrize("M,level,N,lanes", [(4, 0, 8001, 1), (4, 1, 6001, 1), (4, 3, 2001, 1), (4, 5, 601, 1),
+                                             (4, 5, 301, 16), (2, 1, 4001, 1), (2, 4, 1001, 1), (8, 2, 1001, 1)])
+def test_milstein_matches_oracle(mlmc, M, level, N, lanes, payoff, precision):
+    """Milstein on both grids (Sec. 5): same stream, same per-sample bounds."""
+    p = mlmc.Problem(payoff=payoff, scheme="milstein", **GBM)
+    op = oracle_problem(oracle, p)
+    sums, y = run_level(mlmc, level, M, N, 7, p, 11, precision, launch={"lanes_per_path": lanes})
+    yo = oracle.level_samples(level, M, N, op, seed=11, first=7, stream=precision)
+    assert np.max(np.abs(y - yo)) <= _bound(precision, level, M, p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("level,lanes", [(0, 1), (2, 1), (4, 1), (5, 8)])
+def test_single_level_estimator_matches_oracle(mlmc, level, lanes, precision):
+    """The single-level estimator P_l (standard Monte Carlo, Sec. 3) against the oracle's
+    fine-only mode."""
+    p = mlmc.Problem(payoff="asian", estimator="single", **GBM)
+    op = oracle_problem(oracle, p)
+    N = 1201
+    sums, y = run_level(mlmc, level, 4, N, 3, p, 5, precision, launch={"lanes_per_path": lanes})
+    yo = oracle.level_samples(level, 4, N, op, seed=5, first=3, stream=precision, mode=oracle.MODE_FINE_ONLY)
+    assert np.max(np.abs(y - yo)) <= _bound(precision, level, 4, p)
+
+
+@pytest.mark.parametrize("payoff", ["asian", "digital", "lookback"])
+@pytest.mark.parametrize("level,N", [(0, 20011), (3, 3001), (6, 401)])
+def test_fp64_on_fp32_stream(mlmc, payoff, level, N):
+    """FP64 arithmetic on the FP32 stream draws the FP32 path's samples: it matches the FP64
+    oracle on that stream to the FP64 bound, and the FP32 path differs from it by FP32 roundoff
+    alone (the precision comparison at full size rests on this)."""
+    p = mlmc.Problem(payoff=payoff, **GBM)
+    op = oracle_problem(oracle, p)
+    _, y64 = run_level(mlmc, level, 4, N, 0, p, 21, "fp64_stream32", launch={"lanes_per_path": 1})
+    yo = oracle.level_samples(level, 4, N, op, seed=21, stream="fp32")
+    assert np.max(np.abs(y64 - yo)) <= _bound("fp64", level, 4, p)
+    _, y32 = run_level(mlmc, level, 4, N, 0, p, 21, "fp32", launch={"lanes_per_path": 1})
+    d = np.abs(y32 - y64)
+    if payoff == "digital":
+        d = d[d < 0.25]  # threshold flips, checked in the level parity tests
+    assert np.max(d) <= _bound("fp32", level, 4, p)
