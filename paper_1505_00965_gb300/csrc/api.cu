@@ -150,8 +150,10 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
     if (!blocks) {
         // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels
+        // (levels with M^l = 4 take two samples per thread and iteration)
         const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
-                                   : (double)std::max<uint64_t>(N, 1) * lanes;
+                                   : (nf == 4 ? std::ceil((double)std::max<uint64_t>(N, 1) / 2.0)
+                                              : (double)std::max<uint64_t>(N, 1) * lanes);
         const double need = std::ceil(items / threads);
         const int oversub = have_tuned ? std::max(1, tuned.oversub) : 1;
         blocks = (int)std::min<double>(need, (double)max_blocks * oversub);

@@ -160,6 +160,89 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
 }
 
+// NS samples' fine and coarse paths in lockstep on a level with M^l >= 4, one thread per sample
+// (no split): the samples' Philox chains and step chains are independent, so the scheduler can
+// interleave them.  Each sample's arithmetic is the same as in simulate_steps.  States start at
+// 1 (paths relative to S0).
+template <typename R, int MT, int PAY, bool MIL, int NS>
+__device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint64_t s[NS], R fS[NS],
+                                               R fsum[NS], R fhi[NS], R fls[NS], R cS[NS], R csum[NS],
+                                               R chi[NS], R cls[NS])
+{
+    const R a = R(p.a), rh = R(p.rh);
+    const R c2 = R(p.c2), rhm = R(p.rh - p.c2);
+    const int M = MT ? MT : p.M;
+    const R rHm = R(M * (p.rh - p.c2));
+    const bool u23 = p.u23 != 0;
+    R flo[NS], clo[NS], dc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        fS[i] = cS[i] = R(1);
+        fsum[i] = csum[i] = R(0);
+        fhi[i] = chi[i] = flo[i] = clo[i] = R(1);
+        fls[i] = cls[i] = R(0);
+        dc[i] = R(0);
+    }
+    int q = 0;
+    const int calls = p.nf >> 2;
+    for (int j = 0; j < calls; ++j) {
+        R d[NS][4];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)s[i], (uint32_t)(s[i] >> 32), p.ctr3),
+                                          p.key0, p.key1);
+            R rho, c, sn;
+            BoxMuller<R>::pair(x.x, x.y, rho, c, sn, u23);
+            if constexpr (MIL) {
+                d[i][0] = rho * c;
+                d[i][1] = rho * sn;
+            } else {
+                const R ra = rho * a;
+                d[i][0] = fma(ra, c, rh);
+                d[i][1] = fma(ra, sn, rh);
+            }
+            BoxMuller<R>::pair(x.z, x.w, rho, c, sn, u23);
+            if constexpr (MIL) {
+                d[i][2] = rho * c;
+                d[i][3] = rho * sn;
+            } else {
+                const R ra = rho * a;
+                d[i][2] = fma(ra, c, rh);
+                d[i][3] = fma(ra, sn, rh);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            bool coarse_now;
+            if constexpr (MT != 0) {
+                coarse_now = (k + 1) % MT == 0;
+            } else {
+                coarse_now = ++q == M;
+                if (coarse_now) q = 0;
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                R dk;
+                if constexpr (MIL) {
+                    dc[i] += d[i][k];
+                    dk = fma(fma(c2, d[i][k], a), d[i][k], rhm);
+                } else {
+                    dk = d[i][k];
+                    dc[i] += dk;
+                }
+                em_step<R, PAY, false>(fS[i], fsum[i], fhi[i], flo[i], fls[i], dk);
+                if (coarse_now) {
+                    R dcs;
+                    if constexpr (MIL) dcs = fma(fma(c2, dc[i], a), dc[i], rHm);
+                    else dcs = dc[i];
+                    em_step<R, PAY, false>(cS[i], csum[i], chi[i], clo[i], cls[i], dcs);
+                    dc[i] = R(0);
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -318,25 +401,68 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
 // thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
 // Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
 // sample first + i into y_out[i] when y_out is not NULL.
+// NS samples per thread and iteration (idx, idx + T, ...), one thread per sample.
+template <typename R, int MT, int PAY, bool MIL, int NS>
+__device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
+                                            uint64_t T, double m[4], float &b1, float &b2, float &b3,
+                                            float &b4, int &nb, double *y_out)
+{
+    const uint64_t warp_first = t & ~uint64_t(31);
+    const R S0 = R(p.S0), inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
+    const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
+    for (uint64_t base = 0; base + warp_first < N; base += NS * T) {
+        uint64_t idx[NS], s[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            idx[i] = base + t + i * T;
+            s[i] = first + (idx[i] < N ? idx[i] : N - 1);
+        }
+        R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
+        simulate_multi<R, MT, PAY, MIL, NS>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
+                                              R(p.nf) * logS0 + fls[i], inv_nf, p);
+            R Y = Pf;
+            if (!p.fine_only)
+                Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
+                                          R(p.nf / p.M) * logS0 + cls[i], inv_nc, p);
+            if (idx[i] < N) {
+                if (y_out) y_out[idx[i]] = (double)Y;
+                add_moments(Y, m, b1, b2, b3, b4, nb);
+            }
+        }
+    }
+}
+
 template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
                                               double *y_out)
 {
-    const int P = SPLIT ? p.lanes : 1;
-    const uint64_t groups = T / P;
-    const uint64_t g = t / P;
-    const uint64_t g_warp = (t & ~uint64_t(31)) / P;  // first group of this warp
-    const int lig = SPLIT ? (int)(t % P) : 0;
-    for (uint64_t base = 0; base + g_warp < N; base += groups) {
-        const uint64_t idx = base + g;
-        const bool valid = idx < N;
-        const uint64_t s = first + (valid ? idx : N - 1);
-        const R Y = sample_Y<R, MT, PAY, SPLIT, MIL>(p, s, lig, P);
-        if (valid && lig == 0) {
-            if (y_out) y_out[idx] = (double)Y;
-            add_moments(Y, m, b1, b2, b3, b4, nb);
+    if constexpr (!SPLIT) {
+        // one sample per thread and iteration; levels whose sample is a single Philox block
+        // (M^l = 4) take two, idx and idx + T, whose independent chains then interleave
+        if (p.nf == 4)
+            multi_range<R, MT, PAY, MIL, 2>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+        else
+            multi_range<R, MT, PAY, MIL, 1>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+    } else {
+        const int P = p.lanes;
+        const uint64_t groups = T / P;
+        const uint64_t g = t / P;
+        const uint64_t g_warp = (t & ~uint64_t(31)) / P;  // first group of this warp
+        const int lig = (int)(t % P);
+        for (uint64_t base = 0; base + g_warp < N; base += groups) {
+            const uint64_t idx = base + g;
+            const bool valid = idx < N;
+            const uint64_t s = first + (valid ? idx : N - 1);
+            const R Y = sample_Y<R, MT, PAY, true, MIL>(p, s, lig, P);
+            if (valid && lig == 0) {
+                if (y_out) y_out[idx] = (double)Y;
+                add_moments(Y, m, b1, b2, b3, b4, nb);
+            }
         }
     }
 }
