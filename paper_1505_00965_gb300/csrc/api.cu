@@ -17,6 +17,7 @@
 #include "engine.h"
 #include "host.h"
 #include "mlmc.h"
+#include "rng.cuh"
 
 using namespace mlmcgb;
 
@@ -126,16 +127,41 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
             return fail(MLMC_EINVAL, "lanes_per_path %d does not divide M^l = %ld into chunks of a "
                         "multiple of %d steps", lanes, nf, unit);
     } else {
-        // Enough independent samples keep every SM busy with one thread per sample; deep levels
-        // with few samples split each path over several lanes instead.
-        int sms = 0;
-        int rc = device_sms(&sms);
-        if (rc) return rc;
+        // The power of two P (chunks of whole Philox blocks and coarse steps, at least 256 steps
+        // each) with the least modelled launch time.  T resident threads run the N P lane-items
+        // in waves; a partial last wave filled to a fraction f costs min(1, 3 f) of a full one
+        // (its warps run faster on the emptier SMs).  A lane costs its M^l / P steps plus about
+        // 12 steps of chunk join, payoff and moments, and a split step about 5 % more than a
+        // whole-path one.  A larger P must win by more than 1 %.  (Fitted to launch timings
+        // of levels 3..8 at 0.25..4.5 waves.)
         lanes = 1;
-        const double want_threads = (double)sms * 2048.0;
-        while (lanes < 32 && (double)N * lanes < want_threads && nf / (2 * lanes) >= 32 &&
-               (nf / (2 * lanes)) % unit == 0)
-            lanes *= 2;
+        if (nf >= 8) {
+            const int mt1 = M == 4 ? 4 : 0;
+            const void *k1 = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, false, scheme)
+                                                         : level_kernel_fp64(payoff, mt1, false, scheme);
+            const void *kp = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, true, scheme)
+                                                         : level_kernel_fp64(payoff, mt1, true, scheme);
+            if (!k1 || !kp) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
+            int res1 = 0, resp = 0;
+            int rc = max_resident_blocks(k1, threads, &res1);
+            if (rc) return rc;
+            rc = max_resident_blocks(kp, threads, &resp);
+            if (rc) return rc;
+            double best = 0.0;
+            for (int P = 1; P <= 32; P *= 2) {
+                if (P > 1 && (nf % P != 0 || (nf / P) % unit != 0 || nf / P < 256)) break;
+                const double T = (double)(P == 1 ? res1 : resp) * threads;
+                const double w = (double)std::max<uint64_t>(N, 1) * P / T;
+                const double full = std::floor(w);
+                const double waves = full + std::min(1.0, 3.0 * (w - full));
+                const double per_step = P > 1 ? 1.05 : 1.0;
+                const double cost = waves * ((double)nf / P + 12.0) * per_step;
+                if (P == 1 || cost < 0.99 * best) {
+                    best = cost;
+                    lanes = P;
+                }
+            }
+        }
     }
     const bool split = lanes > 1;
     const bool small = nf < 4;
@@ -150,10 +176,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
     if (!blocks) {
         // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels
-        // (levels with M^l = 4 take two samples per thread and iteration)
         const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
-                                   : (nf == 4 ? std::ceil((double)std::max<uint64_t>(N, 1) / 2.0)
-                                              : (double)std::max<uint64_t>(N, 1) * lanes);
+                                   : (double)std::max<uint64_t>(N, 1) * lanes;
         const double need = std::ceil(items / threads);
         const int oversub = have_tuned ? std::max(1, tuned.oversub) : 1;
         blocks = (int)std::min<double>(need, (double)max_blocks * oversub);
@@ -185,6 +209,10 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.N = N;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        p.rkey[2 * i] = p.key0 + (uint32_t)i * kPhiloxWeylA;
+        p.rkey[2 * i + 1] = p.key1 + (uint32_t)i * kPhiloxWeylB;
+    }
     p.ctr3 = ((uint32_t)tag << 16) | (uint32_t)level;
     p.level = level;
     p.M = M;

@@ -23,6 +23,7 @@ struct LevelParams {
     uint64_t N;       // number of samples
     uint32_t key0, key1;  // Philox key (seed low, seed high)
     uint32_t ctr3;        // Philox counter word 3: (tag << 16) | level
+    uint32_t rkey[20];    // Philox round keys: key0 + i W_A, key1 + i W_B for rounds i = 0..9
     int level, M;
     int nf;           // fine steps M^l
     int lanes;        // lanes per sample (1 = one thread per sample)

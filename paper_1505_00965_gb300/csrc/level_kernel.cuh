@@ -89,12 +89,22 @@ __device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
     }
 }
 
+// Philox block of counter c under the parameters' key: from the precomputed round keys (RK, the
+// level kernels, whose parameters sit in the constant bank) or from the two key words (the
+// batched kernel, whose parameters sit in global memory).
+template <bool RK>
+__device__ __forceinline__ uint4 philox_of(const LevelParams &p, uint4 c)
+{
+    if constexpr (RK) return philox4x32_10(c, p.rkey);
+    else return philox4x32_10(c, p.key0, p.key1);
+}
+
 // Fine and coarse paths of one sample on a level with M^l >= 4 (one normal per fine step), over
 // the Philox calls [j0, j1) (4 fine steps per call).  Euler--Maruyama: d = r h + sigma dW and the
 // coarse factor's d is the sum of the M fine ones.  Milstein (MIL): d = r h + sigma dW
 // + sigma^2 (dW^2 - h) / 2 = (r h - c2) + a z + c2 z^2 with a = sigma sqrt(h), c2 = sigma^2 h / 2,
 // and the coarse step the same formula on the summed increment with step M h.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
 __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t slo, uint32_t shi,
                                                int j0, int j1, PathAcc<R, PAY, SPLIT> &fa,
                                                PathAcc<R, PAY, SPLIT> &ca)
@@ -109,7 +119,7 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     const R rHm = R(M * (p.rh - p.c2));
     const bool u23 = p.u23 != 0;
     for (int j = j0; j < j1; ++j) {
-        const uint4 x = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
+        const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, slo, shi, p.ctr3));
         R rho, c, s;
         R d[4];
         if constexpr (!MIL) {
@@ -163,8 +173,9 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
 // NS samples' fine and coarse paths in lockstep on a level with M^l >= 4, one thread per sample
 // (no split): the samples' Philox chains and step chains are independent, so the scheduler can
 // interleave them.  Each sample's arithmetic is the same as in simulate_steps.  States start at
-// 1 (paths relative to S0).
-template <typename R, int MT, int PAY, bool MIL, int NS>
+// 1 (paths relative to S0).  CALLS, when nonzero, is the number of Philox calls per path known
+// at compile time (1 on levels with M^l = 4: straight-line code).
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0>
 __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint64_t s[NS], R fS[NS],
                                                R fsum[NS], R fhi[NS], R fls[NS], R cS[NS], R csum[NS],
                                                R chi[NS], R cls[NS])
@@ -184,13 +195,12 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
         dc[i] = R(0);
     }
     int q = 0;
-    const int calls = p.nf >> 2;
+    const int calls = CALLS ? CALLS : p.nf >> 2;
     for (int j = 0; j < calls; ++j) {
         R d[NS][4];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)s[i], (uint32_t)(s[i] >> 32), p.ctr3),
-                                          p.key0, p.key1);
+            const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, (uint32_t)s[i], (uint32_t)(s[i] >> 32), p.ctr3));
             R rho, c, sn;
             BoxMuller<R>::pair(x.x, x.y, rho, c, sn, u23);
             if constexpr (MIL) {
@@ -301,19 +311,34 @@ __device__ __forceinline__ void finish_sums(double m[4], const LevelParams &p)
 // Add Y, Y^2, Y^3, Y^4 of one sample.  FP64 paths add into the FP64 sums m directly.  FP32
 // paths sum a batch of at most 32 samples in FP32 (b1..b4, nb counts the batch) and add each
 // batch into m, which keeps FP64 off the per-sample path.
-__device__ __forceinline__ void add_moments(float Y, double m[4], float &b1, float &b2, float &b3,
-                                            float &b4, int &nb)
+__device__ __forceinline__ void batch_add(float Y, float &b1, float &b2, float &b3, float &b4)
 {
     const float y2 = Y * Y;
     b1 += Y;
     b2 += y2;
     b3 = fmaf(y2, Y, b3);
     b4 = fmaf(y2, y2, b4);
-    if (++nb == 32) {
-        m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
-        b1 = b2 = b3 = b4 = 0.f;
-        nb = 0;
-    }
+}
+__device__ __forceinline__ void fold_batch_now(double m[4], float &b1, float &b2, float &b3, float &b4, int &nb)
+{
+    m[0] += b1; m[1] += b2; m[2] += b3; m[3] += b4;
+    b1 = b2 = b3 = b4 = 0.f;
+    nb = 0;
+}
+__device__ __forceinline__ void add_moments(float Y, double m[4], float &b1, float &b2, float &b3,
+                                            float &b4, int &nb)
+{
+    batch_add(Y, b1, b2, b3, b4);
+    if (++nb == 32) fold_batch_now(m, b1, b2, b3, b4, nb);
+}
+// Four samples at once (the batch never exceeds 32).
+__device__ __forceinline__ void add_moments4(const float Y[4], double m[4], float &b1, float &b2,
+                                             float &b3, float &b4, int &nb)
+{
+    if (nb > 28) fold_batch_now(m, b1, b2, b3, b4, nb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) batch_add(Y[k], b1, b2, b3, b4);
+    nb += 4;
 }
 __device__ __forceinline__ void add_moments(double Y, double m[4], float &, float &, float &,
                                             float &, int &)
@@ -323,6 +348,12 @@ __device__ __forceinline__ void add_moments(double Y, double m[4], float &, floa
     m[1] += y2;
     m[2] = fma(y2, Y, m[2]);
     m[3] = fma(y2, y2, m[3]);
+}
+__device__ __forceinline__ void add_moments4(const double Y[4], double m[4], float &b1, float &b2,
+                                             float &b3, float &b4, int &nb)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) add_moments(Y[k], m, b1, b2, b3, b4, nb);
 }
 
 // Join the chunks of one sample split over P lanes: an exclusive product scan of the chunk
@@ -363,7 +394,7 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
 
 // Y of sample s on a level with M^l >= 4, computed by the P lanes of one group (lane lig);
 // every lane of the group returns the same Y.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
 __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig, int P)
 {
     const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
@@ -375,7 +406,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     fa.init(R(1));
     ca.init(R(1));
     if constexpr (!SPLIT) {
-        simulate_steps<R, MT, PAY, false, MIL>(p, slo, shi, 0, p.nf >> 2, fa, ca);
+        simulate_steps<R, MT, PAY, false, MIL, RK>(p, slo, shi, 0, p.nf >> 2, fa, ca);
         const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
         const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
                                           R(p.nf) * logS0 + fa.lsum, inv_nf, p);
@@ -385,7 +416,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
-        simulate_steps<R, MT, PAY, true, MIL>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+        simulate_steps<R, MT, PAY, true, MIL, RK>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
         const R steps_f = R(4 * calls);
         R tf, pf, hf, lf, tc, pc, hc, lc;
         join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
@@ -397,12 +428,9 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     }
 }
 
-// Samples [first, first + N) of a level with M^l >= 4, shared by T threads of which this is
-// thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
-// Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
-// sample first + i into y_out[i] when y_out is not NULL.
-// NS samples per thread and iteration (idx, idx + T, ...), one thread per sample.
-template <typename R, int MT, int PAY, bool MIL, int NS>
+// One thread per sample, NS samples per thread and iteration (idx, idx + T, ...), over the
+// samples [first, first + N) (the arguments as for regular_range below).
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0>
 __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
                                             uint64_t T, double m[4], float &b1, float &b2, float &b3,
                                             float &b4, int &nb, double *y_out)
@@ -418,7 +446,7 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
             s[i] = first + (idx[i] < N ? idx[i] : N - 1);
         }
         R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
-        simulate_multi<R, MT, PAY, MIL, NS>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls);
+        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
@@ -435,19 +463,23 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
     }
 }
 
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
+// Samples [first, first + N) of a level with M^l >= 4, shared by T threads of which this is
+// thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
+// Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
+// sample first + i into y_out[i] when y_out is not NULL.
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
                                               double *y_out)
 {
     if constexpr (!SPLIT) {
-        // one sample per thread and iteration; levels whose sample is a single Philox block
-        // (M^l = 4) take two, idx and idx + T, whose independent chains then interleave
+        // one sample per thread and iteration; a sample of a level with M^l = 4 is a single
+        // Philox block and runs as straight-line code
         if (p.nf == 4)
-            multi_range<R, MT, PAY, MIL, 2>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK, 1>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
         else
-            multi_range<R, MT, PAY, MIL, 1>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
     } else {
         const int P = p.lanes;
         const uint64_t groups = T / P;
@@ -458,7 +490,7 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
             const uint64_t idx = base + g;
             const bool valid = idx < N;
             const uint64_t s = first + (valid ? idx : N - 1);
-            const R Y = sample_Y<R, MT, PAY, true, MIL>(p, s, lig, P);
+            const R Y = sample_Y<R, MT, PAY, true, MIL, RK>(p, s, lig, P);
             if (valid && lig == 0) {
                 if (y_out) y_out[idx] = (double)Y;
                 add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -467,74 +499,103 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
     }
 }
 
+// The four normals z of Philox block q of a level with M^l < 4 and their step increments d.
+template <typename R, bool MIL, bool RK = true>
+__device__ __forceinline__ void block_increments(const LevelParams &p, uint64_t q, R z[4], R d[4])
+{
+    const R a = R(p.a), rh = R(p.rh), c2 = R(p.c2), rhm = R(p.rh - p.c2);
+    const bool u23 = p.u23 != 0;
+    const uint4 x = philox_of<RK>(p, make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3));
+    R rho, c, s;
+    BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
+    z[0] = rho * c;
+    z[1] = rho * s;
+    BoxMuller<R>::pair(x.z, x.w, rho, c, s, u23);
+    z[2] = rho * c;
+    z[3] = rho * s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (MIL) d[k] = fma(fma(c2, z[k], a), z[k], rhm);
+        else d[k] = fma(a, z[k], rh);
+    }
+}
+
+// The samples of Philox block q (slots r = 0 .. G - 1, sample q G + r) that lie in
+// [first, end), from the block's normals z and increments d.
+template <typename R, int PAY, bool MIL>
+__device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, uint64_t first, uint64_t end,
+                                            const R z[4], const R d[4], double m[4], float &b1, float &b2,
+                                            float &b3, float &b4, int &nb, double *y_out)
+{
+    const int nf = p.nf;
+    const uint32_t G = 4u / (uint32_t)nf;
+    const R a = R(p.a), S0 = R(p.S0), c2 = R(p.c2), rhm = R(p.rh - p.c2);
+    const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
+    const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
+    if (nf == 1 && q * 4 >= first && q * 4 + 4 <= end) {
+        // four whole level-0 samples: no per-sample range checks, moments added together
+        R Y[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+            Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            if (y_out) y_out[q * 4 + r - first] = (double)Y[r];
+        }
+        add_moments4(Y, m, b1, b2, b3, b4, nb);
+        return;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < 4; ++r) {
+        if (r >= G) break;
+        const uint64_t sample = q * G + r;
+        if (sample < first || sample >= end) continue;
+        R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+        R cS = R(1), csum = R(0), chi = R(1), clo = R(1), cls = R(0);
+        R Y;
+        if (nf == 1) {
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+            Y = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+        } else {  // nf == 2, level 1 with M = 2: two fine steps, one coarse step
+            const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
+            const R zc = z[2 * (r & 1)] + z[2 * (r & 1) + 1];
+            R dcs;
+            if constexpr (MIL) dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
+            else dcs = d0 + d1;
+            em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
+            const R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls,
+                                              inv_nf, p);
+            if (p.fine_only) {
+                Y = Pf;
+            } else {
+                const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
+                Y = Pf - Pc;
+            }
+        }
+        if (y_out) y_out[sample - first] = (double)Y;
+        add_moments(Y, m, b1, b2, b3, b4, nb);
+    }
+}
+
 // Samples [first, first + N) of a level with M^l < 4.  G = 4 / M^l consecutive samples share
 // one Philox block: thread t takes blocks q = first / G + t, + T, ... and the G samples
 // q G .. q G + G - 1 that fall in the range; sample slot r takes normals r M^l .. of the block.
-template <typename R, int PAY, bool MIL>
+template <typename R, int PAY, bool MIL, bool RK = true>
 __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first, uint64_t N,
                                             uint64_t t, uint64_t T, double m[4], float &b1,
                                             float &b2, float &b3, float &b4, int &nb,
                                             double *y_out)
 {
-    const int nf = p.nf;
-    const uint32_t G = 4u / (uint32_t)nf;
+    const uint32_t G = 4u / (uint32_t)p.nf;
     const uint64_t end = first + N;
     const uint64_t q0 = first / G;
     const uint64_t nq = (end - 1) / G - q0 + 1;
-    const R a = R(p.a), rh = R(p.rh), S0 = R(p.S0);
-    const R c2 = R(p.c2), rhm = R(p.rh - p.c2);
-    const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
-    const bool u23 = p.u23 != 0;
     for (uint64_t u = t; u < nq; u += T) {
-        const uint64_t q = q0 + u;
-        const uint4 x = philox4x32_10(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3),
-                                      p.key0, p.key1);
-        R rho, c, s, z[4], d[4];
-        BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
-        z[0] = rho * c;
-        z[1] = rho * s;
-        BoxMuller<R>::pair(x.z, x.w, rho, c, s, u23);
-        z[2] = rho * c;
-        z[3] = rho * s;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if constexpr (MIL) d[k] = fma(fma(c2, z[k], a), z[k], rhm);
-            else d[k] = fma(a, z[k], rh);
-        }
-#pragma unroll
-        for (uint32_t r = 0; r < 4; ++r) {
-            if (r >= G) break;
-            const uint64_t sample = q * G + r;
-            if (sample < first || sample >= end) continue;
-            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
-            R cS = R(1), csum = R(0), chi = R(1), clo = R(1), cls = R(0);
-            R Y;
-            if (nf == 1) {
-                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-                const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
-                Y = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
-            } else {  // nf == 2, level 1 with M = 2: two fine steps, one coarse step
-                const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
-                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
-                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
-                const R zc = z[2 * (r & 1)] + z[2 * (r & 1) + 1];
-                R dcs;
-                if constexpr (MIL) dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
-                else dcs = d0 + d1;
-                em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
-                const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
-                const R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls,
-                                                  inv_nf, p);
-                if (p.fine_only) {
-                    Y = Pf;
-                } else {
-                    const R Pc = payoff_value<R, PAY>(S0 * cS, S0 * csum, S0 * chi, logS0 + cls, inv_nc, p);
-                    Y = Pf - Pc;
-                }
-            }
-            if (y_out) y_out[sample - first] = (double)Y;
-            add_moments(Y, m, b1, b2, b3, b4, nb);
-        }
+        R z[4], d[4];
+        block_increments<R, MIL, RK>(p, q0 + u, z, d);
+        small_block<R, PAY, MIL>(p, q0 + u, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
     }
 }
 
@@ -591,9 +652,9 @@ __device__ __forceinline__ void batch_chunk(const LevelParams &p, uint64_t first
     case kGeoAsian: CALL(kGeoAsian); break;                                                     \
     default: break;                                                                             \
     }
-#define MLMC_SMALL(PAY) small_range<R, PAY, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SMALL(PAY) small_range<R, PAY, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
     if (p.small) {
         MLMC_BATCH_CASES(MLMC_SMALL)
     } else if (p.lanes > 1) {

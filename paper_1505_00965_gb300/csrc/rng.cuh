@@ -32,6 +32,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same function with the key schedule precomputed: rk[2 i], rk[2 i + 1] are the two key
+// words of round i (k0 + i W_A, k1 + i W_B).  When rk lives in the kernel's parameter space the
+// round keys are constant-bank operands of the xors and the per-round key additions vanish.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long pa = (unsigned long long)kPhiloxMulA * c.x;
+        const unsigned long long pb = (unsigned long long)kPhiloxMulB * c.z;
+        const uint32_t next_x = (uint32_t)(pb >> 32) ^ c.y ^ rk[2 * round];
+        const uint32_t next_z = (uint32_t)(pa >> 32) ^ c.w ^ rk[2 * round + 1];
+        c = make_uint4(next_x, (uint32_t)pb, next_z, (uint32_t)pa);
+    }
+    return c;
+}
+
 // Hardware approximations (the MUFU unit): log2, square root, sine and cosine.
 __device__ __forceinline__ float lg2_approx(float x)
 {
