@@ -79,9 +79,11 @@ __device__ __forceinline__ float cos_approx(float x)
 template <typename R> struct BoxMuller;
 
 // FP32 stream: u = 1 - (x mod 2^23) 2^-23 in (0, 1].  The float f = 1 + (x mod 2^23) 2^-23 is
-// built by setting the exponent bits, u = 2 - f exactly.  With v = u2 - 1/2 = 3/2 - f2 (also
-// exact), cos(2 pi u2) = -cos(2 pi v) and sin(2 pi u2) = -sin(2 pi v) with 2 pi v in (-pi, pi],
-// the range where the hardware sine and cosine are most accurate; the sign goes into rho.
+// built by setting the exponent bits, u = 2 - f exactly.  With v = u2 - 1/2 = 3/2 - f2,
+// cos(2 pi u2) = -cos(2 pi v) and sin(2 pi u2) = -sin(2 pi v) with 2 pi v in (-pi, pi], the
+// range where the hardware sine and cosine are most accurate; the sign goes into rho.  The
+// angle 2 pi v = 3 pi - 2 pi f2 is one fused multiply-add (absolute error below 5e-7, the size
+// of the hardware sine's own error).
 template <> struct BoxMuller<float> {
     __device__ __forceinline__ static void pair(uint32_t xa, uint32_t xb, float &rho, float &c,
                                                 float &s, bool = false)
@@ -91,7 +93,7 @@ template <> struct BoxMuller<float> {
         const float u1 = 2.0f - f1;
         // -2 ln u1 = -2 ln(2) log2(u1)
         rho = -sqrt_approx(-1.38629436111989061883f * lg2_approx(u1));
-        const float theta = 6.28318530717958647692f * (1.5f - f2);
+        const float theta = fmaf(-6.28318530717958647692f, f2, 9.42477796076937971538f);
         s = sin_approx(theta);
         c = cos_approx(theta);
     }
