@@ -264,8 +264,83 @@ int mlmc_device_sm_count(void)
     return sms;
 }
 
+// Device buffers of the adaptive driver (workspace, level sums, pinned host copy, timing
+// events), kept between calls in a per-device pool: allocating and pinning them on every call
+// cost more than the kernels of a small estimate.  A call takes a set from the pool (or makes
+// one) and returns it when it ends; a call that met a CUDA error frees its set instead.
+struct DriverScratch {
+    int device = -1;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    double *d_sums = nullptr;
+    double *h_sums = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+static std::mutex g_pool_mutex;
+static std::vector<DriverScratch *> g_pool;
+
+static void free_scratch(DriverScratch *s)
+{
+    if (!s) return;
+    if (s->ws) cudaFree(s->ws);
+    if (s->d_sums) cudaFree(s->d_sums);
+    if (s->h_sums) cudaFreeHost(s->h_sums);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    delete s;
+}
+
+static int acquire_scratch(size_t ws_bytes, DriverScratch **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        for (size_t i = 0; i < g_pool.size(); ++i) {
+            if (g_pool[i]->device == dev && g_pool[i]->ws_bytes >= ws_bytes) {
+                *out = g_pool[i];
+                g_pool.erase(g_pool.begin() + (long)i);
+                return MLMC_OK;
+            }
+        }
+    }
+    DriverScratch *s = new DriverScratch;
+    s->device = dev;
+    s->ws_bytes = ws_bytes;
+    cudaError_t e = cudaMalloc(&s->ws, ws_bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->ws, 0, ws_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
+    if (e != cudaSuccess) {
+        free_scratch(s);
+        return fail(MLMC_ECUDA, "driver setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return MLMC_OK;
+}
+
+static void release_scratch(DriverScratch *s)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    g_pool.push_back(s);
+}
+
 int mlmc_shutdown(void)
 {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    for (size_t i = 0; i < g_pool.size();) {
+        if (g_pool[i]->device == dev) {
+            free_scratch(g_pool[i]);
+            g_pool.erase(g_pool.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
     return MLMC_OK;
 }
 
@@ -473,29 +548,21 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     rc = device_sms(&sms);
     if (rc) return rc;
     const int ws_blocks = sms * 32;
-    const size_t ws_bytes = workspace_bytes_for_blocks(ws_blocks);
-    void *ws = nullptr;
-    double *d_sums = nullptr;
-    double *h_sums = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    CUDA_TRY(cudaMalloc(&ws, ws_bytes));
-    auto cleanup = [&]() {
-        if (ws) cudaFree(ws);
-        if (d_sums) cudaFree(d_sums);
-        if (h_sums) cudaFreeHost(h_sums);
-        if (ev0) cudaEventDestroy(ev0);
-        if (ev1) cudaEventDestroy(ev1);
-    };
+    DriverScratch *sc = nullptr;
+    rc = acquire_scratch(workspace_bytes_for_blocks(ws_blocks), &sc);
+    if (rc) return rc;
+    void *ws = sc->ws;
+    double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
+    cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
+    auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
-        cleanup();
+        free_scratch(sc);
         return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     };
-    cudaError_t e = cudaMemset(ws, 0, ws_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&d_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&h_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
-    if (e != cudaSuccess) return cuda_fail(e, "driver setup");
+    // the completion ticket is zero after every finished launch; clear it in case an earlier
+    // call on this set stopped between a launch and its completion
+    cudaError_t e = cudaMemsetAsync(ws, 0, kTicketBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
     double kernel_ms = 0.0;

@@ -86,3 +86,22 @@ def test_estimates_repeat_exactly(mlmc):
     a = mlmc.mlmc_estimate(3e-3, p, 5)
     b = mlmc.mlmc_estimate(3e-3, p, 5)
     assert a.P == b.P and a.N == b.N
+
+
+def test_pooled_buffers_survive_shutdown_and_other_streams(mlmc):
+    """The driver's device buffers are pooled between calls: estimates on another stream, after
+    mlmc_shutdown released the pool, and after an interleaved estimate of another problem all
+    repeat the first result exactly."""
+    import torch
+
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    a = mlmc.mlmc_estimate(1e-2, p, 3, Lmax=5)
+    mlmc.mlmc_estimate(1e-2, mlmc.Problem(payoff="asian", **GBM), 4)
+    b = mlmc.mlmc_estimate(1e-2, p, 3, Lmax=5)
+    mlmc.mlmc_shutdown()
+    c = mlmc.mlmc_estimate(1e-2, p, 3, Lmax=5)
+    s = torch.cuda.Stream()
+    d = mlmc.mlmc_estimate(1e-2, p, 3, Lmax=5, stream=s)
+    torch.cuda.synchronize()
+    for x in (b, c, d):
+        assert x.P == a.P and x.N == a.N
