@@ -225,9 +225,11 @@ def side_workloads(mlmc, stream) -> dict:
     for l in range(4):
         i = mlmc.mlmc_cv_info(cv, l)
         levels.append({"level": l, "var_ratio": i["var_resid"] / i["var_plain"], "var_plain": i["var_plain"],
-                       "var_resid": i["var_resid"], "kappa": i["kappa"], "work_ratio": i["work_ratio"],
+                       "var_resid": i["var_resid"], "var_g": i["var_g"], "var_lattice": i["var_lattice"],
+                       "lattice_gain": i["var_g"] / i["var_lattice"] if i["var_lattice"] > 0 else None,
+                       "kappa": i["kappa"], "work_ratio": i["work_ratio"],
                        "used": bool(i["used"]), "ns_per_sample_plain": 1e9 * i["t_plain"],
-                       "ns_per_sample_cv": 1e9 * i["t_cv"], "ns_per_sample_mean": 1e9 * i["t_mean"]})
+                       "ns_per_sample_cv": 1e9 * i["t_cv"], "ns_per_lattice_point": 1e9 * i["t_mean"]})
     eps_cv = 5e-4
     a = mlmc.mlmc_estimate_cv(eps_cv, cv, 1, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
     b = mlmc.mlmc_estimate(eps_cv, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)

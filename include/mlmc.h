@@ -278,13 +278,24 @@ int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, int Lmin, in
  *   accumulation (rounded: x, W1, W2, GELU(z1)); everything else FP32;
  *   packed parameters (MLMC_CV_PARAMS floats): W1 [64][8] (row = output unit), b1 [64],
  *   W2 [64][64], b2 [64], w3 [64], b3.
- * The level estimator with the control variate is mean over N samples of (Y - g(x)) plus the
- * mean of g over kappa N independent input samples (tag MLMC_TAG_CV_MEAN: eight fresh normals
- * per sample), so it stays unbiased for any g.  A level uses it only while its measured
- * work-weighted variance (Var(Y - g) + Var(g) / kappa) (t_cv + kappa t_mean) stays below
- * Var(Y) t_plain; otherwise the plain estimator runs.  FP32 paths only.
+ * The level estimator with the control variate is mean over N samples of (Y - g(x)) plus an
+ * independent estimate of E[g]: the average of R replicate means Q_r of a randomly shifted
+ * rank-1 lattice rule (Sloan and Joe 1994; random shift after Cranley and Patterson 1976).
+ * Replicate r has the n = MLMC_CV_LATTICE_POINTS points i = 0 .. n-1 with coordinates, k = 0..7,
+ *   v_k = ((i z_k mod n) 2^16 + D_k) mod 2^32,  z_k = a^k mod n (a = MLMC_CV_LATTICE_A),
+ *   u_k = (floor(v_k / 2^9) + 1/2) 2^-23,  x_k = Phi^{-1}(u_k),
+ * where D_0..D_7 are the words of Philox blocks 0 and 1 of counter r under tag
+ * MLMC_TAG_CV_MEAN (the random shift, as 32-bit fractions).  Every point is uniform whatever
+ * the shift, so Q_r is unbiased for E[g] for any g, and replicates are independent; the lattice
+ * makes Var(Q_r) far smaller than Var(g) / n for a smooth g.  kappa is the number of lattice
+ * points per path sample (R = ceil(kappa N / n), at least 8 replicates).  A level uses the
+ * control variate only while its measured work-weighted variance
+ * (Var(Y - g) + var_lattice / kappa) (t_cv + kappa t_mean) stays below Var(Y) t_plain, with
+ * var_lattice = n Var(Q_r); otherwise the plain estimator runs.  FP32 paths only.
  */
 #define MLMC_CV_PARAMS 4801
+#define MLMC_CV_LATTICE_POINTS 65536   /* points n of one mean-sample replicate */
+#define MLMC_CV_LATTICE_A 21553        /* Korobov multiplier a of the mean-sample lattice */
 #define MLMC_CV_MAX_LEVELS 8
 typedef struct mlmc_cv mlmc_cv;   /* opaque; owns device memory */
 
@@ -304,10 +315,13 @@ typedef struct mlmc_cv_level_info {
     double var_plain;      /* Var(Y) on the held-out samples */
     double var_resid;      /* Var(Y - g) on the held-out samples */
     double var_g;          /* Var(g) on the held-out samples */
-    double kappa;          /* mean-sample ratio N' / N */
-    double t_plain, t_cv, t_mean;   /* measured seconds per sample of the three kernels */
-    double work_ratio;     /* (var_resid + var_g / kappa)(t_cv + kappa t_mean) / (var_plain t_plain) */
+    double kappa;          /* lattice points per path sample, in [1/64, 4096] */
+    double t_plain, t_cv, t_mean;   /* measured seconds per path sample (plain, control variate)
+                                       and per lattice point (mean) */
+    double work_ratio;     /* (var_resid + var_lattice / kappa)(t_cv + kappa t_mean) / (var_plain t_plain) */
     double train_loss;     /* final mean training loss (standardised targets) */
+    double var_lattice;    /* n Var(Q_r) over 128 replicates: per-point variance of the lattice mean
+                              (var_g / var_lattice is the lattice rule's gain over plain sampling) */
 } mlmc_cv_level_info;
 
 /* Create a control variate for one problem with no trained level (every level plain).
@@ -327,7 +341,8 @@ int mlmc_cv_free(mlmc_cv *cv);
 int mlmc_cv_info(const mlmc_cv *cv, int level, mlmc_cv_level_info *out);
 
 /* Read / install the packed FP32 parameters of one level (host arrays of MLMC_CV_PARAMS).
- * Installing marks the level trained and used (the statistics are left at zero). */
+ * Installing marks the level trained and used with the given kappa (lattice points per path
+ * sample, in [1/64, 4096]); the statistics are left at zero. */
 int mlmc_cv_get_params(const mlmc_cv *cv, int level, float *params);
 int mlmc_cv_set_params(mlmc_cv *cv, int level, const float *params, double kappa);
 
@@ -337,9 +352,10 @@ int mlmc_cv_set_params(mlmc_cv *cv, int level, const float *params, double kappa
 int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
                        double *d_sums8, float *d_r, float *d_g, void *stream);
 
-/* Sums of g over the independent mean sample [first, first + N) of `level`:
- * d_sums2 device, 2 doubles (sum g, sum g^2); d_g device or NULL.  Synchronises `stream`. */
-int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
+/* The lattice mean sample of `level`, replicates [first, first + R): d_sums2 device, 2 doubles
+ * (sum Q_r, sum Q_r^2, Q_r the mean of g over replicate r's n points); d_g device [R][n] (g of
+ * every point) or NULL.  Synchronises `stream`. */
+int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t R, uint64_t first, uint64_t seed,
                       double *d_sums2, float *d_g, void *stream);
 
 /* Training data of `level`: d_X device [N][8] network inputs, d_Y device [N] Y values, for

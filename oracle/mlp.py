@@ -21,7 +21,9 @@ import math
 
 import numpy as np
 
-from . import TAG_CV_MEAN, grid_brownian, normals
+from scipy.special import ndtri
+
+from . import TAG_CV_MEAN, grid_brownian, philox
 
 H = 64
 D = 8
@@ -117,7 +119,52 @@ def features(level: int, M: int, s: int, T: float, seed: int, stream: str = "fp6
     return inc / math.sqrt(T / 8.0)
 
 
-def mean_sample_features(s: int, seed: int, level: int, stream: str = "fp64") -> np.ndarray:
-    """Features of sample s of the independent sample that estimates E[g]: eight stream normals
-    (blocks 0 and 1 of counter s under the control-variate-mean tag)."""
-    return normals(seed, level, s, 8, stream=stream, tag=TAG_CV_MEAN)
+# The independent sample that estimates E[g] is a randomly shifted rank-1 lattice rule
+# (Sloan and Joe, "Lattice Methods for Multiple Integration", 1994; random shifts after
+# Cranley and Patterson, SIAM J. Numer. Anal. 13, 1976): replicate r is the point set
+# {frac(i z / n + Delta_r) : i = 0 .. n - 1} with the Korobov generating vector
+# z = (1, a, a^2, ..., a^7) mod n, mapped to N(0, I_8) coordinate by coordinate with the inverse
+# normal distribution function.  Each point of a replicate is uniform on [0, 1)^8 whatever
+# Delta_r, so the replicate's mean of g is an unbiased estimate of E[g]; replicates with
+# independent shifts are independent.  The library fixes n, a and the shift bits:
+LATTICE_N = 65536
+LATTICE_A = 21553
+
+
+def lattice_generator() -> list[int]:
+    """z_k = a^k mod n, k = 0..7."""
+    return [pow(LATTICE_A, k, LATTICE_N) for k in range(D)]
+
+
+def lattice_shift(r: int, seed: int, level: int) -> list[int]:
+    """The shift of replicate r as eight 32-bit fractions: the words of Philox blocks 0 and 1 of
+    counter r under the control-variate-mean tag."""
+    words = []
+    for j in (0, 1):
+        words += list(philox((j, r & 0xFFFFFFFF, r >> 32, (TAG_CV_MEAN << 16) | level),
+                             (seed & 0xFFFFFFFF, seed >> 32)))
+    return words
+
+
+def lattice_uniforms(r: int, i, seed: int, level: int) -> np.ndarray:
+    """Points i (array) of replicate r in (0, 1)^8.  Coordinate k in 32-bit fixed point is
+    v = (i z_k mod n) 2^16 + D_k mod 2^32 (frac(i z_k / n + D_k 2^-32) exactly), and the point
+    keeps its top 23 bits, centred: u = (floor(v / 2^9) + 1/2) 2^-23."""
+    i = np.atleast_1d(np.asarray(i, dtype=np.int64))
+    z = np.array(lattice_generator(), dtype=np.int64)
+    shift = np.array(lattice_shift(r, seed, level), dtype=np.int64)
+    v = (((i[:, None] * z[None, :]) % LATTICE_N) * 65536 + shift[None, :]) % (1 << 32)
+    return ((v >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
+
+
+def mean_sample_features(r: int, i, seed: int, level: int) -> np.ndarray:
+    """Network inputs of points i of replicate r: x_k = Phi^{-1}(u_k), shape (len(i), 8)."""
+    return ndtri(lattice_uniforms(r, i, seed, level))
+
+
+def lattice_replicate_means(theta: np.ndarray, replicates, seed: int, level: int,
+                            quantize: bool = False) -> np.ndarray:
+    """Q_r = (1/n) sum_i g(x_ri): each replicate's lattice mean of the network."""
+    i = np.arange(LATTICE_N)
+    return np.array([forward(theta, mean_sample_features(r, i, seed, level), quantize=quantize)[0].mean()
+                     for r in replicates])

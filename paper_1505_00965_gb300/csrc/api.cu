@@ -251,35 +251,16 @@ int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st)
 
 }  // namespace mlmcgb
 
-extern "C" {
+namespace mlmcgb {
 
-const char *mlmc_last_error(void) { return g_error.c_str(); }
-
-const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
-
-int mlmc_device_sm_count(void)
-{
-    int sms = 0;
-    if (device_sms(&sms)) return -1;
-    return sms;
-}
-
-// Device buffers of the adaptive driver (workspace, level sums, pinned host copy, timing
+// Device buffers of the adaptive drivers (workspace, level sums, pinned host copy, timing
 // events), kept between calls in a per-device pool: allocating and pinning them on every call
 // cost more than the kernels of a small estimate.  A call takes a set from the pool (or makes
 // one) and returns it when it ends; a call that met a CUDA error frees its set instead.
-struct DriverScratch {
-    int device = -1;
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    double *d_sums = nullptr;
-    double *h_sums = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
 static std::mutex g_pool_mutex;
 static std::vector<DriverScratch *> g_pool;
 
-static void free_scratch(DriverScratch *s)
+void free_scratch(DriverScratch *s)
 {
     if (!s) return;
     if (s->ws) cudaFree(s->ws);
@@ -290,7 +271,7 @@ static void free_scratch(DriverScratch *s)
     delete s;
 }
 
-static int acquire_scratch(size_t ws_bytes, DriverScratch **out)
+int acquire_scratch(size_t ws_bytes, DriverScratch **out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -309,8 +290,8 @@ static int acquire_scratch(size_t ws_bytes, DriverScratch **out)
     s->ws_bytes = ws_bytes;
     cudaError_t e = cudaMalloc(&s->ws, ws_bytes);
     if (e == cudaSuccess) e = cudaMemset(s->ws, 0, ws_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_sums, MLMC_MAX_LEVELS * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sums, kDriverSumsPerLevel * MLMC_MAX_LEVELS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_sums, kDriverSumsPerLevel * MLMC_MAX_LEVELS * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
     if (e != cudaSuccess) {
@@ -321,10 +302,25 @@ static int acquire_scratch(size_t ws_bytes, DriverScratch **out)
     return MLMC_OK;
 }
 
-static void release_scratch(DriverScratch *s)
+void release_scratch(DriverScratch *s)
 {
     std::lock_guard<std::mutex> lock(g_pool_mutex);
     g_pool.push_back(s);
+}
+
+}  // namespace mlmcgb
+
+extern "C" {
+
+const char *mlmc_last_error(void) { return g_error.c_str(); }
+
+const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+int mlmc_device_sm_count(void)
+{
+    int sms = 0;
+    if (device_sms(&sms)) return -1;
+    return sms;
 }
 
 int mlmc_shutdown(void)

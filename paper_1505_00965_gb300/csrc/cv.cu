@@ -30,6 +30,7 @@ struct mlmc_cv {
 namespace {
 
 constexpr int kCvThreads = 256;
+constexpr double kMinKappa = 1.0 / 64.0, kMaxKappa = 4096.0;  // mean points per path sample
 
 const void *cv_level_kernel_for(int payoff)
 {
@@ -101,17 +102,47 @@ int launch_cv_level(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, ui
     return MLMC_OK;
 }
 
-int launch_cv_mean(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums2,
-                   float *d_g, void *ws, int blocks, cudaStream_t st)
+// Replicates a launch of the lattice mean kernel can take in a workspace of ws_bytes: one FP64
+// partial per block, kChunksPerReplicate blocks per replicate.
+uint64_t mean_replicates_per_launch(size_t ws_bytes)
 {
-    LevelParams p;
-    fill_params(p, level, cv->M, N, first, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_MEAN, 1, MLMC_FP32_PATH);
-    p.ticket = (unsigned *)ws;
-    p.partials = (double *)((char *)ws + kTicketBytes);
-    const float *params = cv->d_params[level];
-    void *args[] = {&p, (void *)&params, &d_sums2, &d_g};
-    CUDA_TRY(cudaLaunchKernel((const void *)cv_mean_kernel, dim3(blocks), dim3(kCvThreads), args, 0, st));
+    return ws_bytes > kTicketBytes ? (ws_bytes - kTicketBytes) / (sizeof(double) * kChunksPerReplicate) : 0;
+}
+
+// Lattice mean sample: replicates [first, first + R) of `level`; d_sums2 = (sum Q_r, sum Q_r^2)
+// (added to its old values when `accumulate` is set); d_g [R][n] or NULL.  ws (ws_bytes, zero
+// ticket) holds the block partials; more replicates than fit run as consecutive launches.
+int launch_cv_mean(const mlmc_cv *cv, int level, uint64_t R, uint64_t first, uint64_t seed, double *d_sums2,
+                   float *d_g, void *ws, size_t ws_bytes, bool accumulate, cudaStream_t st)
+{
+    const uint64_t cap = mean_replicates_per_launch(ws_bytes);
+    if (!cap) return fail(MLMC_EINVAL, "workspace too small for one replicate");
+    for (uint64_t done = 0; done < R;) {
+        const uint64_t nr = std::min(cap, R - done);
+        LevelParams p;
+        fill_params(p, level, cv->M, nr, first + done, &cv->model, &cv->payoff, seed, MLMC_TAG_CV_MEAN, 1,
+                    MLMC_FP32_PATH);
+        p.ticket = (unsigned *)ws;
+        p.partials = (double *)((char *)ws + kTicketBytes);
+        const float *params = cv->d_params[level];
+        float *g = d_g ? d_g + done * kLatticeN : nullptr;
+        int acc = (accumulate || done > 0) ? 1 : 0;
+        void *args[] = {&p, (void *)&params, &d_sums2, &g, &acc};
+        CUDA_TRY(cudaLaunchKernel((const void *)cv_mean_kernel, dim3((unsigned)(nr * kChunksPerReplicate)),
+                                  dim3(kMeanThreads), args, 0, st));
+        done += nr;
+    }
     return MLMC_OK;
+}
+
+// Replicates of the lattice mean sample that go with dN path samples at ratio kappa (mean
+// points per path sample), at least kMinReplicates in all.
+constexpr uint64_t kMinReplicates = 8;
+uint64_t mean_replicates(double kappa, uint64_t dN, uint64_t have)
+{
+    uint64_t dR = (uint64_t)std::ceil(kappa * (double)dN / (double)kLatticeN);
+    if (have + dR < kMinReplicates) dR = kMinReplicates - have;
+    return dR;
 }
 
 // Run `body(ws)` with a zeroed stream-ordered workspace of `bytes`, then synchronise.
@@ -253,7 +284,8 @@ int mlmc_cv_set_params(mlmc_cv *cv, int level, const float *params, double kappa
     int rc = check_cv_level(cv, level);
     if (rc) return rc;
     if (!params) return fail(MLMC_EINVAL, "params must not be NULL");
-    if (!(kappa >= 1.0 && kappa <= 4096.0)) return fail(MLMC_EINVAL, "kappa must lie in [1, 4096]");
+    if (!(kappa >= kMinKappa && kappa <= kMaxKappa))
+        return fail(MLMC_EINVAL, "kappa must lie in [%g, %g]", kMinKappa, kMaxKappa);
     if (!cv->d_params[level]) CUDA_TRY(cudaMalloc(&cv->d_params[level], sizeof(float) * kNumParams));
     CUDA_TRY(cudaMemcpy(cv->d_params[level], params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
     std::memcpy(cv->h_params[level], params, sizeof(float) * kNumParams);
@@ -285,24 +317,22 @@ int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first,
     });
 }
 
-int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed, double *d_sums2,
+int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t R, uint64_t first, uint64_t seed, double *d_sums2,
                       float *d_g, void *stream)
 {
     int rc = check_trained(cv, level);
     if (rc) return rc;
     if (!d_sums2) return fail(MLMC_EINVAL, "d_sums2 must not be NULL");
-    if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
+    if (first + R < first) return fail(MLMC_EINVAL, "first + R overflows 64 bits");
     cudaStream_t st = (cudaStream_t)stream;
-    if (N == 0) {
+    if (R == 0) {
         CUDA_TRY(cudaMemsetAsync(d_sums2, 0, 2 * sizeof(double), st));
         CUDA_TRY(cudaStreamSynchronize(st));
         return MLMC_OK;
     }
-    int blocks = 0;
-    rc = grid_for((const void *)cv_mean_kernel, N, &blocks);
-    if (rc) return rc;
-    return with_workspace(sums_workspace(blocks, 2), st, [&](void *ws) {
-        return launch_cv_mean(cv, level, N, first, seed, d_sums2, d_g, ws, blocks, st);
+    const size_t bytes = kTicketBytes + std::min<uint64_t>(R, 1024) * kChunksPerReplicate * sizeof(double);
+    return with_workspace(bytes, st, [&](void *ws) {
+        return launch_cv_mean(cv, level, R, first, seed, d_sums2, d_g, ws, bytes, false, st);
     });
 }
 
@@ -496,19 +526,25 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         inf.var_g = std::max(sgg / nv - (sg / nv) * (sg / nv), 0.0);
         inf.train_loss = inf.var_resid / (sd * sd);
         // 6. measured cost per sample of the plain, control-variate and mean kernels
-        const uint64_t nt = std::max<uint64_t>(1u << 14, (uint64_t)(1u << 22) >> std::min(2 * l, 20));
+        // (sizes large enough that every timed launch runs for a millisecond or more: small
+        // launches would measure launch latency and idle SMs, not the cost per sample)
+        const uint64_t nt = std::max<uint64_t>(1u << 22, (uint64_t)(1u << 30) >> std::min(2 * l, 20));
+        const uint64_t nc = 1u << 24;
         {
             Plan plan;
             rc = plan_level(l, M, nt, MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr, &plan);
             if (rc) return cleanup(rc);
-            int cvb = 0, mb = 0;
-            rc = grid_for(cv_level_kernel_for(payoff->kind), nt, &cvb);
-            if (!rc) rc = grid_for((const void *)cv_mean_kernel, nt, &mb);
+            int cvb = 0;
+            rc = grid_for(cv_level_kernel_for(payoff->kind), nc, &cvb);
             if (rc) return cleanup(rc);
-            const int wb = std::max(std::max(plan.blocks, cvb), mb);
+            // the lattice statistics use kStatReplicates replicates (2^23 points)
+            constexpr uint64_t kStatReplicates = 128;
+            const size_t wbytes = std::max<size_t>(sums_workspace(std::max(plan.blocks, cvb), 8),
+                                                   kTicketBytes + kStatReplicates * kChunksPerReplicate * sizeof(double));
             double *d_out = nullptr;
             CV_TRY(cudaMalloc(&d_out, 16 * sizeof(double)));
-            rc = with_workspace(sums_workspace(wb, 8), st, [&](void *ws) {
+            double hq[2] = {0.0, 0.0};
+            rc = with_workspace(wbytes, st, [&](void *ws) {
                 for (int rep = 0; rep < 2; ++rep) {  // first pass warms up, second is timed
                     LevelParams p;
                     fill_params(p, l, M, nt, 0, model, payoff, seed, MLMC_TAG_PATHS, plan.lanes, MLMC_FP32_PATH);
@@ -520,29 +556,36 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
                     CUDA_TRY(cudaEventSynchronize(ev1));
                     inf.t_plain = seconds_per_sample(ev0, ev1, nt);
                     CUDA_TRY(cudaEventRecord(ev0, st));
-                    r2 = launch_cv_level(cv, l, nt, 0, seed, d_out, nullptr, nullptr, ws, cvb, st);
+                    r2 = launch_cv_level(cv, l, nc, 0, seed, d_out, nullptr, nullptr, ws, cvb, st);
                     if (r2) return r2;
                     CUDA_TRY(cudaEventRecord(ev1, st));
                     CUDA_TRY(cudaEventSynchronize(ev1));
-                    inf.t_cv = seconds_per_sample(ev0, ev1, nt);
+                    inf.t_cv = seconds_per_sample(ev0, ev1, nc);
                     CUDA_TRY(cudaEventRecord(ev0, st));
-                    r2 = launch_cv_mean(cv, l, nt, 0, seed, d_out + 8, nullptr, ws, mb, st);
+                    // replicates far from those of any estimate (which count from 0)
+                    r2 = launch_cv_mean(cv, l, kStatReplicates, 1ull << 40, seed, d_out + 8, nullptr, ws, wbytes,
+                                        false, st);
                     if (r2) return r2;
                     CUDA_TRY(cudaEventRecord(ev1, st));
                     CUDA_TRY(cudaEventSynchronize(ev1));
-                    inf.t_mean = seconds_per_sample(ev0, ev1, nt);
+                    inf.t_mean = seconds_per_sample(ev0, ev1, kStatReplicates * kLatticeN);
                 }
+                CUDA_TRY(cudaMemcpy(hq, d_out + 8, sizeof(hq), cudaMemcpyDeviceToHost));
                 return (int)MLMC_OK;
             });
             cudaFree(d_out);
             if (rc) return cleanup(rc);
+            // per-point variance of the lattice mean: n times the variance of a replicate mean
+            const double R = (double)kStatReplicates, mq = hq[0] / R;
+            inf.var_lattice = (double)kLatticeN * std::max(hq[1] - R * mq * mq, 0.0) / (R - 1.0);
         }
-        // 7. mean-sample ratio minimising (Vr + Vg / k)(t_cv + k t_mean), and the decision
+        // 7. mean points per path sample minimising (Vr + Vq / k)(t_cv + k t_mean), Vq the
+        // per-point variance of the lattice mean, and the decision
         const double vr = std::max(inf.var_resid, 1e-300);
-        double kappa = std::sqrt(inf.var_g * inf.t_cv / (vr * std::max(inf.t_mean, 1e-15)));
-        kappa = std::min(std::max(kappa, 1.0), 4096.0);
+        double kappa = std::sqrt(inf.var_lattice * inf.t_cv / (vr * std::max(inf.t_mean, 1e-15)));
+        kappa = std::min(std::max(kappa, kMinKappa), kMaxKappa);
         inf.kappa = kappa;
-        inf.work_ratio = (inf.var_resid + inf.var_g / kappa) * (inf.t_cv + kappa * inf.t_mean) /
+        inf.work_ratio = (inf.var_resid + inf.var_lattice / kappa) * (inf.t_cv + kappa * inf.t_mean) /
                          std::max(inf.var_plain * inf.t_plain, 1e-300);
         inf.used = inf.work_ratio < 1.0 ? 1 : 0;
         inf.trained = 1;
@@ -576,35 +619,29 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
     if (rc) return rc;
     const int ws_blocks = sms * 32;
     const size_t ws_bytes = sums_workspace(ws_blocks, 8);
-    void *ws = nullptr;
-    double *d_sums = nullptr, *h_sums = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    auto cleanup = [&]() {
-        if (ws) cudaFree(ws);
-        if (d_sums) cudaFree(d_sums);
-        if (h_sums) cudaFreeHost(h_sums);
-        if (ev0) cudaEventDestroy(ev0);
-        if (ev1) cudaEventDestroy(ev1);
-    };
+    const int stride = 16;  // doubles per level in the round buffer: 8 level sums + 2 mean sums
+    static_assert(stride <= kDriverSumsPerLevel, "round buffer");
+    DriverScratch *sc = nullptr;
+    rc = acquire_scratch(ws_bytes, &sc);
+    if (rc) return rc;
+    void *ws = sc->ws;
+    double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
+    cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
+    auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
-        cleanup();
+        free_scratch(sc);
         return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     };
-    const int stride = 16;  // doubles per level in the round buffer: 8 level sums + 2 mean sums
-    cudaError_t e = cudaMalloc(&ws, ws_bytes);
-    if (e == cudaSuccess) e = cudaMemset(ws, 0, ws_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&d_sums, MLMC_MAX_LEVELS * stride * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&h_sums, MLMC_MAX_LEVELS * stride * sizeof(double));
-    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
-    if (e != cudaSuccess) return cuda_fail(e, "driver setup");
+    cudaError_t e = cudaMemsetAsync(ws, 0, kTicketBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
     auto uses = [&](int l) { return l < MLMC_CV_MAX_LEVELS && cv->d_params[l] && cv->info[l].used; };
-    // control-variate levels: cumulative sums of r, r^2 (N samples) and g, g^2 (N' mean samples)
-    std::vector<double> sr(MLMC_MAX_LEVELS, 0.0), srr(MLMC_MAX_LEVELS, 0.0), sg(MLMC_MAX_LEVELS, 0.0),
-        sgg(MLMC_MAX_LEVELS, 0.0), vs0(MLMC_MAX_LEVELS, 0.0), vs1(MLMC_MAX_LEVELS, 0.0);
-    std::vector<uint64_t> nmean(MLMC_MAX_LEVELS, 0);
+    // control-variate levels: cumulative sums of r, r^2 (N path samples) and of the lattice
+    // replicate means Q, Q^2 (nrep replicates)
+    std::vector<double> sr(MLMC_MAX_LEVELS, 0.0), srr(MLMC_MAX_LEVELS, 0.0), sq(MLMC_MAX_LEVELS, 0.0),
+        sqq(MLMC_MAX_LEVELS, 0.0), vs0(MLMC_MAX_LEVELS, 0.0), vs1(MLMC_MAX_LEVELS, 0.0);
+    std::vector<uint64_t> nrep(MLMC_MAX_LEVELS, 0), drep(MLMC_MAX_LEVELS, 0);
     for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
         if (uses(l)) {
             const mlmc_cv_level_info &inf = cv->info[l];
@@ -622,17 +659,16 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
         for (int l = 0; l <= L; ++l) {
             if (!dN[l]) continue;
             if (uses(l)) {
-                const uint64_t dm = (uint64_t)std::ceil(cv->info[l].kappa * (double)dN[l]);
-                int cb = 0, mb = 0;
+                drep[l] = mean_replicates(cv->info[l].kappa, dN[l], nrep[l]);
+                int cb = 0;
                 rc = grid_for(cv_level_kernel_for(payoff->kind), dN[l], &cb);
-                if (!rc) rc = grid_for((const void *)cv_mean_kernel, dm, &mb);
                 if (!rc)
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
                                          nullptr, ws, std::min(cb, ws_blocks), st);
                 if (!rc)
-                    rc = launch_cv_mean(cv, l, dm, nmean[l], seed, d_sums + stride * l + 8, nullptr, ws,
-                                        std::min(mb, ws_blocks), st);
-                launches += 2;
+                    rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, ws, ws_bytes,
+                                        false, st);
+                launches += 1 + (drep[l] + mean_replicates_per_launch(ws_bytes) - 1) / mean_replicates_per_launch(ws_bytes);
             } else {
                 Plan plan;
                 rc = plan_level(l, M, dN[l], MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr, &plan);
@@ -663,18 +699,19 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
             if (!dN[l]) continue;
             const double *h = h_sums + stride * l;
             if (uses(l)) {
-                // level estimate mean(r) + mean'(g): its variance per path sample is
-                // Var(r) + Var(g) N / N'; hand the driver the sums of a sample with that mean
-                // and variance (as differences from the previous round's totals)
+                // level estimate mean(r) + mean of the replicate means Q: its variance per path
+                // sample is Var(r) + N Var(Q) / R; hand the driver the sums of a sample with that
+                // mean and variance (as differences from the previous round's totals)
                 sr[l] += h[0];
                 srr[l] += h[1];
-                sg[l] += h[8];
-                sgg[l] += h[9];
-                nmean[l] += (uint64_t)std::ceil(cv->info[l].kappa * (double)dN[l]);
-                const double n = (double)(drv.samples_taken(l) + dN[l]), nm = (double)nmean[l];
-                const double mr = sr[l] / n, mg = sg[l] / nm;
-                const double vr = std::max(srr[l] / n - mr * mr, 0.0), vg = std::max(sgg[l] / nm - mg * mg, 0.0);
-                const double m = mr + mg, v = vr + vg * n / nm;
+                sq[l] += h[8];
+                sqq[l] += h[9];
+                nrep[l] += drep[l];
+                const double n = (double)(drv.samples_taken(l) + dN[l]), R = (double)nrep[l];
+                const double mr = sr[l] / n, mq = sq[l] / R;
+                const double vr = std::max(srr[l] / n - mr * mr, 0.0);
+                const double vq = R > 1.0 ? std::max(sqq[l] - R * mq * mq, 0.0) / (R - 1.0) : 0.0;
+                const double m = mr + mq, v = vr + vq * n / R;
                 const double s0 = n * m, s1 = n * (v + m * m);
                 round[4 * l + 0] = s0 - vs0[l];
                 round[4 * l + 1] = s1 - vs1[l];

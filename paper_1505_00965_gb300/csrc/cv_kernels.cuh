@@ -11,6 +11,7 @@
 
 #include "engine.h"
 #include "level_kernel.cuh"
+#include "mlmc.h"
 #include "mlp.cuh"
 #include "rng.cuh"
 
@@ -221,46 +222,110 @@ __global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, cons
     finish_sums_n<8>(m, p.partials, p.ticket, out8);
 }
 
-// Independent sample that estimates E[g]: eight stream normals per sample (blocks 0 and 1 of
-// counter s under the control-variate-mean tag) are the network inputs; sums [g, g^2].
-__global__ void __launch_bounds__(256) cv_mean_kernel(const LevelParams p, const float *__restrict__ params,
-                                                      double *out2, float *g_out)
+// Independent sample that estimates E[g]: replicates of a randomly shifted rank-1 lattice rule
+// (Sloan and Joe 1994; random shift after Cranley and Patterson 1976).  Replicate r is
+// {frac(i z / n + Delta_r)}, i < n = MLMC_CV_LATTICE_POINTS, z_k = a^k mod n with the Korobov
+// multiplier a = MLMC_CV_LATTICE_A, and Delta_r the eight words of Philox blocks 0 and 1 of
+// counter r under the control-variate-mean tag, read as 32-bit fractions.  In fixed point a
+// coordinate is v = (i z_k mod n) 2^16 + D_k mod 2^32, exact; the point keeps its top 23 bits,
+// centred, u = (floor(v / 2^9) + 1/2) 2^-23 (exact in FP32), and x_k = Phi^{-1}(u_k).
+constexpr uint32_t kLatticeN = MLMC_CV_LATTICE_POINTS;
+constexpr int kMeanThreads = 256;
+constexpr uint32_t kLatticeChunk = 1024;                         // points per block
+constexpr uint32_t kChunksPerReplicate = kLatticeN / kLatticeChunk;
+static_assert(kLatticeN == 65536, "the fixed-point lattice coordinates assume n = 2^16");
+static_assert(kLatticeChunk % kMeanThreads == 0, "whole warps per chunk");
+
+__host__ __device__ constexpr uint32_t lattice_z(int k)
+{
+    uint32_t z = 1;
+    for (int j = 0; j < k; ++j) z = (z * (uint32_t)MLMC_CV_LATTICE_A) & (kLatticeN - 1);
+    return z;
+}
+
+// Blocks [q * 64, q * 64 + 64) take replicate p.first + q (p.N replicates), 1024 points each
+// (kMeanThreads threads).  Each block writes the sum of g over its points to partials[block];
+// the last block forms every replicate's mean Q = (1/n) sum of its 64 partials (fixed order)
+// and writes out2 = (sum Q, sum Q^2) over the launch's replicates, added to out2's old values
+// when `accumulate` is set.  g_out [p.N][n] (or NULL) receives g of every point.
+__global__ void __launch_bounds__(kMeanThreads) cv_mean_kernel(const LevelParams p, const float *__restrict__ params,
+                                                               double *out2, float *g_out, int accumulate)
 {
     __shared__ MlpShared net;
-    __shared__ uint32_t xw_all[8][128];
+    __shared__ uint32_t xw_all[kMeanThreads / 32][128];
+    __shared__ double sm[kMeanThreads / 32][2];
+    __shared__ bool is_last;
     load_mlp(net, params);
     __syncthreads();
     uint32_t *xw = xw_all[threadIdx.x >> 5];
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t warp_first = tid & ~uint64_t(31);
-    double m[2] = {0, 0};
-    for (uint64_t base = 0; base + warp_first < p.N; base += stride) {
-        const uint64_t idx = base + tid;
-        const bool valid = idx < p.N;
-        const uint64_t s = p.first + (valid ? idx : p.N - 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t rep = blockIdx.x / kChunksPerReplicate;
+    const uint32_t chunk = blockIdx.x % kChunksPerReplicate;
+    const uint64_t r = p.first + rep;
+    uint32_t D[8];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)r, (uint32_t)(r >> 32), p.ctr3),
+                                       p.key0, p.key1);
+        D[4 * j + 0] = xb.x;
+        D[4 * j + 1] = xb.y;
+        D[4 * j + 2] = xb.z;
+        D[4 * j + 3] = xb.w;
+    }
+    double acc = 0.0;
+#pragma unroll 1
+    for (uint32_t q = 0; q < kLatticeChunk / kMeanThreads; ++q) {
+        const uint32_t i = chunk * kLatticeChunk + q * kMeanThreads + threadIdx.x;
         float x[8];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)s, (uint32_t)(s >> 32), p.ctr3),
-                                           p.key0, p.key1);
-            float rho, c, sn;
-            BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
-            x[4 * j + 0] = rho * c;
-            x[4 * j + 1] = rho * sn;
-            BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
-            x[4 * j + 2] = rho * c;
-            x[4 * j + 3] = rho * sn;
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t v = (((i * lattice_z(k)) & (kLatticeN - 1)) << 16) + D[k];
+            x[k] = normcdfinvf(((float)(v >> 9) + 0.5f) * 0x1p-23f);
         }
         const float gv = warp_mlp(net, xw, x);
-        if (valid) {
-            const double g = gv;
-            m[0] += g;
-            m[1] = fma(g, g, m[1]);
-            if (g_out) g_out[idx] = gv;
-        }
+        acc += (double)gv;
+        if (g_out) g_out[rep * kLatticeN + i] = gv;
     }
-    finish_sums_n<2>(m, p.partials, p.ticket, out2);
+    acc = warp_sum(acc);
+    if (lane == 0) sm[warp][0] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kMeanThreads / 32; ++w) s += sm[w][0];
+        p.partials[blockIdx.x] = s;
+        __threadfence();
+        is_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const uint64_t nrep = gridDim.x / kChunksPerReplicate;
+    double sq = 0.0, sqq = 0.0;
+    for (uint64_t k = threadIdx.x; k < nrep; k += kMeanThreads) {
+        double s = 0.0;
+        for (uint32_t c = 0; c < kChunksPerReplicate; ++c) s += __ldcg(p.partials + k * kChunksPerReplicate + c);
+        const double Q = s / (double)kLatticeN;
+        sq += Q;
+        sqq = fma(Q, Q, sqq);
+    }
+    sq = warp_sum(sq);
+    sqq = warp_sum(sqq);
+    __syncthreads();
+    if (lane == 0) {
+        sm[warp][0] = sq;
+        sm[warp][1] = sqq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kMeanThreads / 32; ++w) {
+            a += sm[w][0];
+            b += sm[w][1];
+        }
+        out2[0] = (accumulate ? out2[0] : 0.0) + a;
+        out2[1] = (accumulate ? out2[1] : 0.0) + b;
+        *p.ticket = 0u;
+    }
 }
 
 // Training data: (x, Y) of samples [first, first + N) under the training tag.

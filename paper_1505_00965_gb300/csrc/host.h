@@ -47,4 +47,21 @@ struct TunedShape {
 };
 bool tuned_lookup(int precision, int payoff, int M, int level, uint64_t N, TunedShape *out);
 
+// Buffers of one adaptive-driver call, pooled per device between calls: a workspace of at least
+// ws_bytes (zero ticket), device and pinned host sums (kDriverSumsPerLevel doubles per level)
+// and two timing events.  acquire_scratch takes a set from the pool or makes one;
+// release_scratch returns it; free_scratch destroys a set that met a CUDA error.
+constexpr int kDriverSumsPerLevel = 16;
+struct DriverScratch {
+    int device = -1;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    double *d_sums = nullptr;
+    double *h_sums = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+int acquire_scratch(size_t ws_bytes, DriverScratch **out);
+void release_scratch(DriverScratch *s);
+void free_scratch(DriverScratch *s);
+
 }  // namespace mlmcgb

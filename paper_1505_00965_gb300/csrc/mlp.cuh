@@ -25,10 +25,14 @@ constexpr int kOffW3 = kOffB2 + kHidden;
 constexpr int kOffB3 = kOffW3 + kHidden;
 constexpr int kNumParams = kOffB3 + 1;  // 4801
 
-// Network in shared memory: weights as packed bfloat16 pairs, the rest FP32.
+// Network in shared memory: weights as packed bfloat16 pairs, the rest FP32.  A W2 row takes
+// kW2Stride = 36 words (32 used): the layer-2 operand loads of a warp read word 8 kt + t of rows
+// g = 0..7, which a stride of 32 would put in the same four banks; with 36 the 32 lanes hit 32
+// distinct banks.
+constexpr int kW2Stride = kHidden / 2 + 4;
 struct MlpShared {
     uint32_t W1[kHidden * kInputs / 2];   // row o: 4 words of pairs (W1[o][2t], W1[o][2t+1])
-    uint32_t W2[kHidden * kHidden / 2];   // row o: 32 words of pairs (W2[o][2j], W2[o][2j+1])
+    uint32_t W2[kHidden * kW2Stride];     // row o: 32 words of pairs (W2[o][2j], W2[o][2j+1]), then 4 unused
     float b1[kHidden], b2[kHidden], w3[kHidden];
     float b3;
 };
@@ -49,7 +53,8 @@ __device__ __forceinline__ float tanh_approx(float x)
 
 __device__ __forceinline__ float gelu(float z)
 {
-    const float u = 0.7978845608028654f * fmaf(0.044715f * z * z, z, z);
+    // sqrt(2/pi) (z + 0.044715 z^3) = z (sqrt(2/pi) + 0.044715 sqrt(2/pi) z^2)
+    const float u = z * fmaf(0.035677408136300125f, z * z, 0.7978845608028654f);
     const float hz = 0.5f * z;
     return fmaf(hz, tanh_approx(u), hz);
 }
@@ -78,7 +83,7 @@ __device__ __forceinline__ void load_mlp(MlpShared &s, const float *__restrict__
     for (int i = threadIdx.x; i < kHidden * kInputs / 2; i += blockDim.x)
         s.W1[i] = pack_bf16x2(params[kOffW1 + 2 * i], params[kOffW1 + 2 * i + 1]);
     for (int i = threadIdx.x; i < kHidden * kHidden / 2; i += blockDim.x)
-        s.W2[i] = pack_bf16x2(params[kOffW2 + 2 * i], params[kOffW2 + 2 * i + 1]);
+        s.W2[(i >> 5) * kW2Stride + (i & 31)] = pack_bf16x2(params[kOffW2 + 2 * i], params[kOffW2 + 2 * i + 1]);
     for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
         s.b1[i] = params[kOffB1 + i];
         s.b2[i] = params[kOffB2 + i];
@@ -129,7 +134,7 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
     for (int nt = 0; nt < 8; ++nt) {
         const int o = 8 * nt + 2 * t;
         float c[4] = {s.b2[o], s.b2[o + 1], s.b2[o], s.b2[o + 1]};
-        const uint32_t *w = &s.W2[(8 * nt + g) * 32];
+        const uint32_t *w = &s.W2[(8 * nt + g) * kW2Stride];
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma_bf16(c, a2[kt], w[8 * kt + t], w[8 * kt + t + 4]);
         if (acts) {

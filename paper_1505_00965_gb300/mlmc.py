@@ -89,7 +89,7 @@ class mlmc_cv_level_info(ctypes.Structure):
     _fields_ = [("trained", ctypes.c_int32), ("used", ctypes.c_int32), ("var_plain", ctypes.c_double),
                 ("var_resid", ctypes.c_double), ("var_g", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("t_plain", ctypes.c_double), ("t_cv", ctypes.c_double), ("t_mean", ctypes.c_double),
-                ("work_ratio", ctypes.c_double), ("train_loss", ctypes.c_double)]
+                ("work_ratio", ctypes.c_double), ("train_loss", ctypes.c_double), ("var_lattice", ctypes.c_double)]
 
 
 _fptr = ctypes.POINTER(ctypes.c_float)
@@ -392,9 +392,9 @@ def mlmc_cv_level_sums(cv: ControlVariate, level: int, N: int, first: int, seed:
                                    _addr(stream)))
 
 
-def mlmc_cv_mean_sums(cv: ControlVariate, level: int, N: int, first: int, seed: int, d_sums2, d_g=None,
+def mlmc_cv_mean_sums(cv: ControlVariate, level: int, R: int, first: int, seed: int, d_sums2, d_g=None,
                       stream=None) -> None:
-    _check(_lib.mlmc_cv_mean_sums(cv.handle, level, N, first, seed, _addr(d_sums2), _addr(d_g), _addr(stream)))
+    _check(_lib.mlmc_cv_mean_sums(cv.handle, level, R, first, seed, _addr(d_sums2), _addr(d_g), _addr(stream)))
 
 
 def mlmc_cv_training_data(cv: ControlVariate, level: int, N: int, first: int, seed: int, d_X, d_Y,

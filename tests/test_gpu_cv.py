@@ -142,15 +142,18 @@ def test_cv_level_and_mean_sums_match_oracle(mlmc, level):
               (Yg ** 2).sum(), np.abs(g).sum(), (g ** 2).sum()]
     for k in range(8):
         assert abs(sums[k] - own[k]) <= 1e-6 * scales[k] + 1e-9, k
-    # the independent mean sample: eight normals per sample under the mean tag
+    # the independent mean sample: replicates 3 and 4 of the shifted lattice, every point
+    R, n = 2, omlp.LATTICE_N
     d_m = torch.zeros(2, dtype=torch.float64, device="cuda")
-    d_gm = torch.zeros(N, dtype=torch.float32, device="cuda")
-    mlmc.mlmc_cv_mean_sums(cv, level, N, 7, seed, d_m, d_gm)
-    gm = d_gm.cpu().numpy().astype(np.float64)
-    Xm = np.array([omlp.mean_sample_features(7 + i, seed, level, stream="fp32") for i in range(N)])
-    gmo, _ = omlp.forward(theta.astype(np.float64), Xm, quantize=True)
-    assert np.all(np.abs(gm - gmo) <= _g_bound(theta, Xm))
-    np.testing.assert_allclose(d_m.cpu().numpy(), [gm.sum(), (gm ** 2).sum()], rtol=1e-6)
+    d_gm = torch.zeros(R * n, dtype=torch.float32, device="cuda")
+    mlmc.mlmc_cv_mean_sums(cv, level, R, 3, seed, d_m, d_gm)
+    gm = d_gm.cpu().numpy().astype(np.float64).reshape(R, n)
+    for j in range(R):
+        Xm = omlp.mean_sample_features(3 + j, np.arange(n), seed, level)
+        gmo, _ = omlp.forward(theta.astype(np.float64), Xm, quantize=True)
+        assert np.all(np.abs(gm[j] - gmo) <= _g_bound(theta, Xm)), j
+    Q = gm.mean(axis=1)
+    np.testing.assert_allclose(d_m.cpu().numpy(), [Q.sum(), (Q ** 2).sum()], rtol=1e-9)
 
 
 def test_zero_network_reduces_to_plain(mlmc):
@@ -181,6 +184,9 @@ def test_training_gains_and_estimates_stay_unbiased(mlmc):
     assert info[0]["var_resid"] < 0.05 * info[0]["var_plain"]
     assert info[1]["var_resid"] < 0.5 * info[1]["var_plain"]
     assert all(i["t_cv"] > 0 and i["t_mean"] > 0 and i["t_plain"] > 0 for i in info)
+    # the shifted lattice estimates E[g] with far less variance per point than plain sampling
+    assert info[0]["var_lattice"] < info[0]["var_g"] / 20
+    assert info[1]["var_lattice"] < info[1]["var_g"] / 20
     eps = 2e-3
     for seed in (1, 2, 3):
         a = mlmc.mlmc_estimate_cv(eps, cv, seed)

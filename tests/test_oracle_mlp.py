@@ -77,13 +77,54 @@ def test_features_are_iid_standard_normal(level):
     assert np.max(np.abs(np.cov(F.T, bias=True) - np.eye(8))) < 5 * math.sqrt(2 / n)
 
 
-def test_mean_sample_features_are_independent_normals():
-    n = 20000
-    F = np.array([mlp.mean_sample_features(s, seed=17, level=2) for s in range(n)])
-    assert np.max(np.abs(np.cov(F.T, bias=True) - np.eye(8))) < 5 * math.sqrt(2 / n)
-    # and they are not the path features of the same index
-    P = np.array([mlp.features(2, 4, s, 1.0, seed=17) for s in range(2000)])
-    assert abs(np.corrcoef(F[:2000, 0], P[:, 0])[0, 1]) < 0.1
+def _lattice_offsets(r, seed, level):
+    """K_k(i) = i z_k mod n recovered from the oracle's points: u = (floor(v / 2^9) + 1/2) 2^-23
+    with v = K 2^16 + D mod 2^32 gives floor(v / 2^9) = K 2^7 + floor(D / 2^9) mod 2^23."""
+    i = np.arange(mlp.LATTICE_N)
+    u = mlp.lattice_uniforms(r, i, seed, level)
+    top = np.rint(u * 2.0 ** 23 - 0.5).astype(np.int64)
+    D = np.array(mlp.lattice_shift(r, seed, level), dtype=np.int64)
+    K = ((top - (D >> 9)[None, :]) % (1 << 23))
+    assert np.all(K % 128 == 0)
+    return K // 128
+
+
+def test_lattice_is_the_korobov_rank1_lattice():
+    """With the random shift removed the points are i z / n for the Korobov vector
+    z = (1, a, a^2, ...) mod n: coordinate 0 is i / n, the map i -> point is additive mod n
+    (a rank-1 lattice is a group), and every coordinate runs through all n strata once."""
+    n = mlp.LATTICE_N
+    K = _lattice_offsets(5, seed=17, level=2)
+    assert np.array_equal(K[:, 0], np.arange(n))
+    assert K[1, 1] == mlp.LATTICE_A
+    for k in range(8):
+        assert np.array_equal(np.sort(K[:, k]), np.arange(n)), k
+    rng = np.random.default_rng(0)
+    a, b = rng.integers(0, n, 500), rng.integers(0, n, 500)
+    assert np.array_equal((K[a] + K[b]) % n, K[(a + b) % n])
+
+
+def test_lattice_mean_is_unbiased_with_small_variance():
+    """E[exp(c . x)] = exp(|c|^2 / 2) for x ~ N(0, I_8): the replicate means of the shifted lattice
+    scatter around it (independent shifts, unbiased) with a variance far below that of plain
+    sampling with as many points, (exp(2|c|^2) - exp(|c|^2)) / n."""
+    c = np.array([0.3, 0.25, 0.2, 0.15, 0.1, 0.08, 0.05, 0.02])
+    exact = math.exp(c @ c / 2)
+    var_f = math.exp(2 * (c @ c)) - math.exp(c @ c)
+    i = np.arange(mlp.LATTICE_N)
+    Q = np.array([np.exp(mlp.mean_sample_features(r, i, seed=3, level=1) @ c).mean() for r in range(16)])
+    se = Q.std(ddof=1) / math.sqrt(len(Q))
+    assert se > 0
+    assert abs(Q.mean() - exact) < 5 * se
+    assert Q.var(ddof=1) < var_f / mlp.LATTICE_N / 100
+
+
+def test_lattice_shifts_differ_between_replicates_levels_and_seeds():
+    s = mlp.lattice_shift(0, seed=1, level=0)
+    assert len(s) == 8 and all(0 <= w < 2 ** 32 for w in s)
+    assert s != mlp.lattice_shift(1, seed=1, level=0)
+    assert s != mlp.lattice_shift(0, seed=1, level=1)
+    assert s != mlp.lattice_shift(0, seed=2, level=0)
 
 
 def test_quantised_gradient_uses_the_rounded_forward():
