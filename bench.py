@@ -121,6 +121,13 @@ def _oracle_job(args):
     return sum(n * M ** l for l, n in enumerate(e.N)), dt
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu (level_kernel, lookback,
+# level 6, N = 10^6, one thread per sample): the kernels read no input arrays; the algorithmic
+# bytes are the block partials and the four sums (608 x 32 + 32 = 19.5 KB).
+TRAFFIC_BYTES_PER_LAUNCH = 32000
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one level_kernel launch (lookback, "
+                 "level 6, N=1e6, 608 blocks); algorithmic bytes 19.5 KB of block partials")
+
 ORACLE_SAMPLE = dict(eps=2e-2, seeds=(1, 2, 3, 4))
 ORACLE_SAMPLE_TEXT = ("oracle adaptive MLMC of the same two options and model at eps=2e-2 (not 1e-3), "
                       "seeds 1..4, FP32 stream; estimates run in parallel processes")
@@ -318,7 +325,8 @@ def gpu_arm(args) -> None:
     peak = sms * SCHEDULERS_PER_SM * WARP * max_mhz * 1e6 / 1e9          # G instructions / s
     achieved = instr / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginstr/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "level_kernel (FP32 paths, all levels of the step)",
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_basis": TRAFFIC_BASIS,
+                "kernel": "level_kernel (FP32 paths, all levels of the step)",
                 "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz (max SM clock), "
                               "one warp instruction per scheduler per clock",
                 "frac_at_run_clock": (achieved / (sms * 128 * run_mhz * 1e6 / 1e9)) if run_mhz else None,
