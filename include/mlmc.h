@@ -45,20 +45,31 @@ typedef enum mlmc_status {
     MLMC_ENOMEM = 3,      /* a device or host allocation failed */
     MLMC_ENOTCONV = 4,    /* the driver reached Lmax before the bias test passed */
     MLMC_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
-    MLMC_ENOTIMPL = 6     /* the combination of options is not implemented */
+    MLMC_ENOTIMPL = 6,    /* the combination of options is not implemented */
+    MLMC_ENONFINITE = 7   /* a level's sums are not finite: the scheme diverged (the driver stops) */
 } mlmc_status;
 
-/* Model: geometric Brownian motion dS = r S dt + sigma S dW, S(0) = S0, on [0, T]
- * (the SDE of Sec. 2, Eq. sde, with f(x) = r x and g(x) = sigma x as in Sec. 6). */
-typedef enum mlmc_model_kind { MLMC_MODEL_GBM = 0 } mlmc_model_kind;
-/* Time-stepping scheme on both grids: Euler--Maruyama (Sec. 2, Eq. em) or Milstein (Sec. 5,
- * the strongly more accurate scheme that gives beta > gamma): for GBM the Milstein step adds
- * sigma^2 X (dW^2 - dt) / 2, the coarse step using the summed increment and its own dt. */
-typedef enum mlmc_scheme { MLMC_EULER_MARUYAMA = 0, MLMC_MILSTEIN = 1 } mlmc_scheme;
+/* Models:
+ *   GBM          geometric Brownian motion dS = r S dt + sigma S dW, S(0) = S0, on [0, T]
+ *                (the SDE of Sec. 2, Eq. sde, with f(x) = r x and g(x) = sigma x as in Sec. 6).
+ *   QUINTIC_ODE  the counterexample cited in Sec. 5 (Eq. count): dX = -X^5 dt with a standard
+ *                normal X(0), on [0, T].  Only T is read (S0, r, sigma must be finite and are
+ *                ignored).  Sample s of a level draws X(0) as normal (s mod 4) of Philox block 0
+ *                of counter index floor(s / 4) (counter word as below); its fine and coarse paths
+ *                both start from that X(0).  Paired with MLMC_SECOND_MOMENT, E[X(T)^2]. */
+typedef enum mlmc_model_kind { MLMC_MODEL_GBM = 0, MLMC_MODEL_QUINTIC_ODE = 1 } mlmc_model_kind;
+/* Time-stepping scheme on both grids, with drift f and step h:
+ *   EULER_MARUYAMA  X + h f(X) + g(X) dW (Sec. 2, Eq. em); both models.
+ *   MILSTEIN        (GBM) adds sigma^2 X (dW^2 - dt) / 2, the coarse step using the summed
+ *                   increment and its own dt (Sec. 5, the strongly more accurate scheme).
+ *   TAMED_EM        (QUINTIC_ODE) X + h f(X) / (1 + h |f(X)|): the tamed method that Sec. 5
+ *                   cites as recovering multilevel convergence where explicit Euler--Maruyama
+ *                   diverges. */
+typedef enum mlmc_scheme { MLMC_EULER_MARUYAMA = 0, MLMC_MILSTEIN = 1, MLMC_TAMED_EM = 2 } mlmc_scheme;
 typedef struct mlmc_model {
     int32_t kind;          /* mlmc_model_kind */
     int32_t scheme;        /* mlmc_scheme */
-    double S0, r, sigma, T; /* S0 > 0, sigma > 0, T > 0, all finite */
+    double S0, r, sigma, T; /* GBM: S0 > 0, sigma > 0, T > 0, all finite; QUINTIC_ODE: T > 0 */
 } mlmc_model;
 
 /* Payoffs, discounted by exp(-r T) (Sec. 6):
@@ -68,10 +79,12 @@ typedef struct mlmc_model {
  *   DIGITAL   cash * 1{S_n > K}, cash / 2 when S_n == K        (Sec. 6)
  *   LINEAR_TEST     S_n, not discounted (test payoff with exact Euler--Maruyama moments)
  *   GEO_ASIAN_TEST  max(exp((1/n) sum (log S_i + log S_{i+1}) / 2) - K, 0) (closed-form test)
+ *   SECOND_MOMENT   X_n^2, not discounted (the quantity of Sec. 5, Eq. count; QUINTIC_ODE only,
+ *                   and the only payoff of that model)
  * The paper names the Asian and lookback options (Sec. 7) without defining them; the
  * definitions above are this library's reading. */
 typedef enum mlmc_payoff_kind {
-    MLMC_EUROPEAN = 0, MLMC_ASIAN = 1, MLMC_LOOKBACK = 2, MLMC_DIGITAL = 3,
+    MLMC_EUROPEAN = 0, MLMC_ASIAN = 1, MLMC_LOOKBACK = 2, MLMC_DIGITAL = 3, MLMC_SECOND_MOMENT = 4,
     MLMC_LINEAR_TEST = 100, MLMC_GEO_ASIAN_TEST = 101
 } mlmc_payoff_kind;
 /* What a level sample returns: the coupled difference Y = P_l - P_{l-1} of multilevel Monte
@@ -101,7 +114,8 @@ enum { MLMC_TAG_PATHS = 0, MLMC_TAG_CV_MEAN = 1, MLMC_TAG_CV_TRAIN = 2 };
  *   lanes_per_path     1 (one thread per sample) or a power of two up to 32: that many lanes of
  *                      one warp split the time steps of one sample into equal chunks and join
  *                      them by a product scan (GBM's step is multiplicative); requires
- *                      M^l / lanes_per_path to be a multiple of max(M, 4)
+ *                      M^l / lanes_per_path to be a multiple of max(M, 4); GBM only (QUINTIC_ODE
+ *                      paths are nonlinear and run one thread per sample)
  *   blocks             grid size; the kernel strides over the samples */
 typedef struct mlmc_launch {
     int32_t threads_per_block;
@@ -231,7 +245,8 @@ typedef struct mlmc_result {
  *   model, payoff  host, read only.  out  host, written on success and on MLMC_ENOTCONV.
  *   stream  void* cudaStream_t (NULL = default); synchronised before return.
  * Errors: MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM; MLMC_ENOTCONV when Lmax is reached first
- * (out then holds the estimate at L = Lmax).
+ * (out then holds the estimate at L = Lmax); MLMC_ENONFINITE when a round's level sums are
+ * not finite (explicit Euler--Maruyama on QUINTIC_ODE, Sec. 5), out left untouched.
  */
 int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc_model *model,
                   const mlmc_payoff *payoff, uint64_t seed, int precision, void *stream,
@@ -258,6 +273,7 @@ typedef struct mlmc_problem {
  *   `stream` has drained, and is finished on return).
  *   results host [n], written for every problem.  kernel_ms, wall_ms, launches and d2h_bytes
  *   describe the whole batch (the same values in every result).
+ * GBM problems only (other models: MLMC_ENOTIMPL).
  * Returns MLMC_OK when every problem converged, MLMC_ENOTCONV when some reached Lmax first
  * (their results carry converged = 0 and the estimate at Lmax), MLMC_EINVAL for a bad argument
  * (the message names the problem), MLMC_ECUDA or MLMC_ENOMEM for device failures.

@@ -57,9 +57,22 @@ bool valid_payoff_kind(int k)
 int check_problem(const mlmc_model *model, const mlmc_payoff *payoff)
 {
     if (!model || !payoff) return fail(MLMC_EINVAL, "model and payoff must not be NULL");
+    if (model->kind == MLMC_MODEL_QUINTIC_ODE) {
+        if (model->scheme != MLMC_EULER_MARUYAMA && model->scheme != MLMC_TAMED_EM)
+            return fail(MLMC_EINVAL, "the quintic ODE takes Euler--Maruyama or tamed Euler--Maruyama (scheme %d)",
+                        model->scheme);
+        if (!(model->T > 0) || !std::isfinite(model->T) || !std::isfinite(model->S0) ||
+            !std::isfinite(model->r) || !std::isfinite(model->sigma))
+            return fail(MLMC_EINVAL, "the quintic ODE needs a finite T > 0 (and finite unused fields)");
+        if (payoff->kind != MLMC_SECOND_MOMENT)
+            return fail(MLMC_EINVAL, "the quintic ODE takes the second-moment payoff (kind %d)", payoff->kind);
+        if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_SINGLE_LEVEL)
+            return fail(MLMC_EINVAL, "unsupported estimator %d", payoff->estimator);
+        return MLMC_OK;
+    }
     if (model->kind != MLMC_MODEL_GBM) return fail(MLMC_EINVAL, "unsupported model kind %d", model->kind);
     if (model->scheme != MLMC_EULER_MARUYAMA && model->scheme != MLMC_MILSTEIN)
-        return fail(MLMC_EINVAL, "unsupported scheme %d", model->scheme);
+        return fail(MLMC_EINVAL, "GBM takes Euler--Maruyama or Milstein (scheme %d)", model->scheme);
     if (!(model->S0 > 0) || !std::isfinite(model->S0) || !(model->sigma > 0) ||
         !std::isfinite(model->sigma) || !(model->T > 0) || !std::isfinite(model->T) ||
         !std::isfinite(model->r))
@@ -189,6 +202,45 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     return MLMC_OK;
 }
 
+// Launch shape of the QUINTIC_ODE kernel: one thread per Philox block of four samples, no
+// lanes split; explicit fields of `launch` (threads, blocks) win.
+static int plan_ode(int level, int M, uint64_t N, int precision, int scheme, const mlmc_launch *launch, Plan *plan)
+{
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
+        return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
+    if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
+    if (launch && launch->lanes_per_path > 1)
+        return fail(MLMC_EINVAL, "the quintic ODE runs one thread per sample (lanes_per_path %d)",
+                    launch->lanes_per_path);
+    (void)level;
+    (void)M;
+    const int threads = launch && launch->threads_per_block ? launch->threads_per_block : 256;
+    if (threads < 32 || threads > 256 || threads % 32)
+        return fail(MLMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256] for the quintic ODE");
+    plan->kernel = ode_level_kernel(precision, scheme);
+    if (!plan->kernel) return fail(MLMC_EINVAL, "no quintic ODE kernel for scheme %d", scheme);
+    int max_blocks = 0;
+    int rc = max_resident_blocks(plan->kernel, threads, &max_blocks);
+    if (rc) return rc;
+    int blocks = launch && launch->blocks ? launch->blocks : 0;
+    if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
+    if (!blocks) {
+        const double items = std::ceil((double)std::max<uint64_t>(N, 1) / 4.0) + 1.0;
+        blocks = (int)std::min<double>(std::ceil(items / threads), (double)max_blocks);
+    }
+    plan->threads = threads;
+    plan->lanes = 1;
+    plan->blocks = std::max(blocks, 1);
+    return MLMC_OK;
+}
+
+int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *model, const mlmc_payoff *payoff,
+                 const mlmc_launch *launch, Plan *plan)
+{
+    if (model->kind == MLMC_MODEL_QUINTIC_ODE) return plan_ode(level, M, N, precision, model->scheme, launch, plan);
+    return plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, plan);
+}
+
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
                  const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes, int precision)
 {
@@ -203,6 +255,7 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.sqrt_h = std::sqrt(h);
     p.sqrt_t8 = std::sqrt(m->T / 8.0);
     p.rh = m->r * h;
+    p.h = h;
     p.inv_nf = 1.0 / (double)nf;
     p.inv_nc = level > 0 ? (double)M / (double)nf : 0.0;
     p.first = first;
@@ -367,7 +420,7 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first, const ml
     if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
+    rc = plan_problem(level, M, N, precision, model, payoff, launch, &plan);
     if (rc) return rc;
     if (N == 0) {
         CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
@@ -441,7 +494,7 @@ int mlmc_level_sums_noalloc(int level, int M, uint64_t N, uint64_t first, const 
                     kNoAllocMaxBlocks, kNoAllocScratchBytes);
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
+    rc = plan_problem(level, M, N, precision, model, payoff, launch, &plan);
     if (rc) return rc;
     if (N == 0) {
         CUDA_TRY(cudaMemsetAsync(d_sums, 0, 4 * sizeof(double), st));
@@ -472,7 +525,7 @@ int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_
     if (first + N < first) return fail(MLMC_EINVAL, "first + N overflows 64 bits");
     cudaStream_t st = (cudaStream_t)stream;
     Plan plan;
-    rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, &plan);
+    rc = plan_problem(level, M, N, precision, model, payoff, launch, &plan);
     if (rc) return rc;
     double out[4] = {0.0, 0.0, 0.0, 0.0};
     if (N > 0) {
@@ -570,7 +623,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         for (int l = 0; l <= L; ++l) {
             if (!dN[l]) continue;
             Plan plan;
-            rc = plan_level(l, M, dN[l], precision, payoff->kind, model->scheme, nullptr, &plan);
+            rc = plan_problem(l, M, dN[l], precision, model, payoff, nullptr, &plan);
             if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
             if (rc) {
                 cleanup();
@@ -594,6 +647,15 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         if (e != cudaSuccess) return cuda_fail(e, "level round");
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) kernel_ms += ms;
+        for (int l = 0; l <= L; ++l) {
+            if (!dN[l]) continue;
+            for (int k = 0; k < 4; ++k) {
+                if (!std::isfinite(h_sums[4 * l + k])) {
+                    cleanup();
+                    return fail(MLMC_ENONFINITE, "level %d sums are not finite (the scheme diverged)", l);
+                }
+            }
+        }
         drv.absorb(h_sums);
     }
     cleanup();

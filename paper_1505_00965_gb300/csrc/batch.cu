@@ -143,6 +143,8 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
     if (precision == MLMC_FP64_STREAM32) return fail(MLMC_EINVAL, "batches run MLMC_FP64 or MLMC_FP32_PATH");
     for (int i = 0; i < n; ++i) {
         rc = check_problem(&problems[i].model, &problems[i].payoff);
+        if (!rc && problems[i].model.kind != MLMC_MODEL_GBM)
+            rc = fail(MLMC_ENOTIMPL, "batches run GBM problems");
         if (!rc && (problems[i].model.scheme != MLMC_EULER_MARUYAMA || problems[i].payoff.estimator != MLMC_COUPLED))
             rc = fail(MLMC_EINVAL, "batches run the coupled Euler--Maruyama estimator");
         if (!rc && !(problems[i].eps > 0 && std::isfinite(problems[i].eps)))

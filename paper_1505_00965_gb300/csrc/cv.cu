@@ -234,6 +234,7 @@ int mlmc_cv_create(int M, const mlmc_model *model, const mlmc_payoff *payoff, ml
 {
     int rc = check_problem(model, payoff);
     if (rc) return rc;
+    if (model->kind != MLMC_MODEL_GBM) return fail(MLMC_ENOTIMPL, "the control variate is built for GBM");
     if (model->scheme != MLMC_EULER_MARUYAMA || payoff->estimator != MLMC_COUPLED)
         return fail(MLMC_EINVAL, "the control variate runs the coupled Euler--Maruyama estimator");
     if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
@@ -607,6 +608,7 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
     const auto t_start = std::chrono::steady_clock::now();
     int rc = check_problem(model, payoff);
     if (rc) return rc;
+    if (model->kind != MLMC_MODEL_GBM) return fail(MLMC_ENOTIMPL, "the control variate is built for GBM");
     if (!out || !cv) return fail(MLMC_EINVAL, "out and cv must not be NULL");
     rc = check_estimate_args(eps, M, Lmin, Lmax, N0, MLMC_FP32_PATH);
     if (rc) return rc;

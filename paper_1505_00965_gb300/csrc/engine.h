@@ -19,6 +19,7 @@ struct LevelParams {
     double inv_nc;    // 1 / M^(l-1)
     double sqrt_h;    // sqrt(h): Brownian increment scale of one fine step
     double sqrt_t8;   // sqrt(T / 8): scale of the control variate's grid increments
+    double h;         // fine step T / M^l
     uint64_t first;   // first sample index
     uint64_t N;       // number of samples
     uint32_t key0, key1;  // Philox key (seed low, seed high)
@@ -51,6 +52,8 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 // Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel and
 // -1 for the kernel of levels with M^l < 4.
 const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme);
+// Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
+const void *ode_level_kernel(int precision, int scheme);
 const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme);
 
 // Batched rounds: one chunk of samples of one task (a level of one problem).

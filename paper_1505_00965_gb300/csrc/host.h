@@ -34,6 +34,9 @@ struct Plan {
 };
 int plan_level(int level, int M, uint64_t N, int precision, int payoff, int scheme, const mlmc_launch *launch,
                Plan *plan);
+// plan_level for GBM, the one-thread-per-sample plan of the QUINTIC_ODE kernel otherwise.
+int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *model, const mlmc_payoff *payoff,
+                 const mlmc_launch *launch, Plan *plan);
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
                  const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes, int precision);
 double level_cost(int level, int M);

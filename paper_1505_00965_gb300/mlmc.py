@@ -23,12 +23,14 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ETIMEOUT, MLMC_ENOTIMPL = range(7)
-MLMC_MODEL_GBM = 0
-PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "linear": 100, "geo_asian": 101}
+MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ETIMEOUT, MLMC_ENOTIMPL, MLMC_ENONFINITE = range(8)
+MLMC_MODEL_GBM, MLMC_MODEL_QUINTIC_ODE = 0, 1
+MODELS = {"gbm": MLMC_MODEL_GBM, "quintic": MLMC_MODEL_QUINTIC_ODE}
+PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "second_moment": 4, "linear": 100,
+           "geo_asian": 101}
 MLMC_FP64, MLMC_FP32_PATH, MLMC_FP64_STREAM32 = 0, 1, 2
 PRECISIONS = {"fp64": MLMC_FP64, "fp32": MLMC_FP32_PATH, "fp64_stream32": MLMC_FP64_STREAM32}
-SCHEMES = {"em": 0, "milstein": 1}
+SCHEMES = {"em": 0, "milstein": 1, "tamed": 2}
 ESTIMATORS = {"coupled": 0, "single": 1}
 MLMC_TAG_PATHS, MLMC_TAG_CV_MEAN, MLMC_TAG_CV_TRAIN = 0, 1, 2
 MLMC_MAX_LEVELS = 16
@@ -150,7 +152,9 @@ def _addr(x) -> int | None:
 
 @dataclass(frozen=True)
 class Problem:
-    """GBM dS = r S dt + sigma S dW and a discounted payoff (the C structs in Python form)."""
+    """A model and a payoff (the C structs in Python form): GBM dS = r S dt + sigma S dW with a
+    discounted payoff, or (kind="quintic") the random ODE dX = -X^5 dt with X(0) ~ N(0, 1) and the
+    second moment X(T)^2 (scheme "em" or "tamed")."""
 
     S0: float = 100.0
     r: float = 0.05
@@ -161,9 +165,10 @@ class Problem:
     cash: float = 1.0
     scheme: str = "em"            # "em" (Euler--Maruyama) or "milstein"
     estimator: str = "coupled"    # "coupled" (P_l - P_{l-1}) or "single" (P_l, standard MC)
+    kind: str = "gbm"             # "gbm" or "quintic"
 
     def model(self) -> mlmc_model:
-        return mlmc_model(MLMC_MODEL_GBM, SCHEMES[self.scheme], self.S0, self.r, self.sigma, self.T)
+        return mlmc_model(MODELS[self.kind], SCHEMES[self.scheme], self.S0, self.r, self.sigma, self.T)
 
     def payoff_struct(self) -> mlmc_payoff:
         return mlmc_payoff(PAYOFFS[self.payoff], ESTIMATORS[self.estimator], self.K, self.cash)

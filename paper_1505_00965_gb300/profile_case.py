@@ -2,6 +2,8 @@
 
     python -m paper_1505_00965_gb300.profile_case --level 6 --N 1000000 --payoff asian \\
         --precision fp32 --reps 3
+    python -m paper_1505_00965_gb300.profile_case --kind quintic --scheme tamed --payoff second_moment \\
+        --level 6 --N 1000000
 
 Prints the CUDA-event time per launch and the coupled path-steps per second.
 """
@@ -18,6 +20,8 @@ def main(argv=None) -> None:
     ap.add_argument("--M", type=int, default=4)
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--payoff", default="asian", choices=sorted(mlmc.PAYOFFS))
+    ap.add_argument("--kind", default="gbm", choices=sorted(mlmc.MODELS))
+    ap.add_argument("--scheme", default="em", choices=sorted(mlmc.SCHEMES))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--lanes", type=int, default=0, help="lanes per path (0 = automatic)")
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = automatic)")
@@ -27,7 +31,7 @@ def main(argv=None) -> None:
 
     import torch
 
-    prob = mlmc.Problem(payoff=args.payoff)
+    prob = mlmc.Problem(payoff=args.payoff, kind=args.kind, scheme=args.scheme)
     launch = {"lanes_per_path": args.lanes, "threads_per_block": args.threads}
     ws_bytes = mlmc.mlmc_level_workspace_bytes(args.level, args.M, args.N, args.precision, launch)
     ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
@@ -49,7 +53,8 @@ def main(argv=None) -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.reps, 1)
     steps = args.N * args.M ** args.level
-    print(f"level={args.level} M={args.M} N={args.N} payoff={args.payoff} precision={args.precision}: "
+    print(f"level={args.level} M={args.M} N={args.N} model={args.kind} scheme={args.scheme} payoff={args.payoff} "
+          f"precision={args.precision}: "
           f"{ms:.4f} ms/launch, {steps / ms / 1e6:.4g} G coupled steps/s, sums={d_sums.tolist()}")
 
 

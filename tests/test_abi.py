@@ -148,3 +148,22 @@ def test_product_does_not_reference_the_oracle():
         if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text and "mlmc_oracle" not in text, path
+
+
+@pytest.mark.parametrize("kw,launch,msg", [
+    (dict(kind="quintic", scheme="milstein", payoff="second_moment"), None, "tamed"),
+    (dict(kind="quintic", scheme="tamed", payoff="european"), None, "second-moment"),
+    (dict(kind="quintic", scheme="tamed", payoff="second_moment", T=0.0), None, "T > 0"),
+    (dict(kind="gbm", scheme="tamed"), None, "Milstein"),
+    (dict(payoff="second_moment"), None, "payoff kind"),
+    (dict(kind="quintic", scheme="em", payoff="second_moment"), {"lanes_per_path": 4}, "one thread per sample"),
+])
+def test_quintic_model_arguments_rejected_on_host(kw, launch, msg):
+    """The QUINTIC_ODE model (Sec. 5, Eq. count) pairs with EM or tamed EM and the second moment;
+    GBM takes neither; its paths are never split over lanes."""
+    from paper_1505_00965_gb300 import mlmc
+
+    with pytest.raises(mlmc.MLMCError) as ei:
+        mlmc.mlmc_level_sums_ex(2, 4, 100, 0, mlmc.Problem(**kw), 1, launch=launch)
+    assert ei.value.status == mlmc.MLMC_EINVAL
+    assert msg in str(ei.value)
