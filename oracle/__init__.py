@@ -37,7 +37,7 @@ _lib = None
 PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "linear": 100, "geo_asian": 101}
 STREAMS = {"fp64": 0, "fp32": 1}
 SCHEMES = {"em": 0, "milstein": 1}
-MODE_COUPLED, MODE_FINE_ONLY = 0, 1
+MODE_COUPLED, MODE_FINE_ONLY, MODE_ANTITHETIC = 0, 1, 2
 TAG_PATHS, TAG_CV_MEAN, TAG_CV_TRAIN = 0, 1, 2
 
 

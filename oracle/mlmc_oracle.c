@@ -41,6 +41,10 @@
  *   - Arithmetic Asian: trapezoid average (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 on each path's own
  *     grid.  Lookback: fixed strike, max over the grid points S_0..S_n.  Both discounted.
  *   - Cost of one level-l sample: C_0 = 1, C_l = M^l + M^{l-1} Euler--Maruyama steps.
+ *   - Antithetic mode (Sec. 7, the antithetic multilevel estimator of Giles and Szpruch): a
+ *     second fine path takes the M fine increments of every coarse step in reverse order (for
+ *     M = 2, swapped); the coarse path is unchanged and Y = (P_f + P_f^a) / 2 - P_c.  Cost
+ *     C_l = 2 M^l + M^{l-1}.  On level 0 it is the plain estimator.
  *   - Milstein scheme (Sec. 5, the strongly more accurate scheme that gives beta > gamma): for
  *     g(x) = sigma x the step adds (1/2) g g' (dW^2 - dt) = (1/2) sigma^2 X (dW^2 - dt); the coarse
  *     step uses the coarse increment (the sum of the fine ones) and its own step size.
@@ -55,7 +59,7 @@
 enum { PAY_EUROPEAN = 0, PAY_ASIAN = 1, PAY_LOOKBACK = 2, PAY_DIGITAL = 3,
        PAY_LINEAR = 100, PAY_GEO_ASIAN = 101 };
 enum { STREAM_FP64 = 0, STREAM_FP32 = 1 };
-enum { MODE_COUPLED = 0, MODE_FINE_ONLY = 1 };
+enum { MODE_COUPLED = 0, MODE_FINE_ONLY = 1, MODE_ANTITHETIC = 2 };
 
 /* ---------------------------------------------------------------- random stream ---------- */
 
@@ -293,11 +297,23 @@ int oracle_level_samples(int level, int M, uint64_t N, uint64_t first, int tag, 
     double *dW = (double *)malloc(sizeof(double) * (size_t)nf);
     double *fine = (double *)malloc(sizeof(double) * (size_t)(nf + 1));
     double *coarse = (double *)malloc(sizeof(double) * (size_t)(nf / M + 1));
-    int coupled = (level > 0 && mode == MODE_COUPLED);
+    int coupled = (level > 0 && (mode == MODE_COUPLED || mode == MODE_ANTITHETIC));
+    int anti = (level > 0 && mode == MODE_ANTITHETIC);
+    double *dWa = anti ? (double *)malloc(sizeof(double) * (size_t)nf) : NULL;
+    double *fine_a = anti ? (double *)malloc(sizeof(double) * (size_t)(nf + 1)) : NULL;
     for (uint64_t i = 0; i < N; ++i) {
         oracle_sample_paths(level, M, first + i, tag, p, seed, stream, dW, fine,
                             coupled ? coarse : NULL);
         double Pf = oracle_payoff(p->payoff, p->K, p->Q, p->r, p->T, fine, (int)nf);
+        if (anti) {
+            /* the antithetic fine path: each coarse step's M increments in reverse order */
+            for (long c = 0; c < nf / M; ++c)
+                for (int q = 0; q < M; ++q)
+                    dWa[c * M + q] = dW[c * M + (M - 1 - q)];
+            scheme_path(p, (int)nf, p->T / (double)nf, dWa, fine_a);
+            double Pfa = oracle_payoff(p->payoff, p->K, p->Q, p->r, p->T, fine_a, (int)nf);
+            Pf = 0.5 * (Pf + Pfa);
+        }
         double Pc = coupled ? oracle_payoff(p->payoff, p->K, p->Q, p->r, p->T, coarse,
                                             (int)(nf / M))
                             : 0.0;
@@ -306,6 +322,8 @@ int oracle_level_samples(int level, int M, uint64_t N, uint64_t first, int tag, 
     free(dW);
     free(fine);
     free(coarse);
+    free(dWa);
+    free(fine_a);
     return 0;
 }
 
@@ -355,6 +373,8 @@ int oracle_level_sums(int level, int M, uint64_t N, uint64_t first, int tag, int
     double Cl = level == 0 ? 1.0 : (double)(ipow(M, level) + ipow(M, level - 1));
     if (mode == MODE_FINE_ONLY)
         Cl = (double)ipow(M, level);
+    if (mode == MODE_ANTITHETIC && level > 0)
+        Cl = (double)(2 * ipow(M, level) + ipow(M, level - 1));
     *cost = (double)N * Cl;
     return 0;
 }
