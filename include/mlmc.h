@@ -88,12 +88,19 @@ typedef enum mlmc_payoff_kind {
     MLMC_LINEAR_TEST = 100, MLMC_GEO_ASIAN_TEST = 101
 } mlmc_payoff_kind;
 /* What a level sample returns: the coupled difference Y = P_l - P_{l-1} of multilevel Monte
- * Carlo (Eq. Yldef), or P_l alone -- standard Monte Carlo with Euler--Maruyama at step T / M^l
- * (Sec. 3), the comparison of Sec. 6. */
-typedef enum mlmc_estimator { MLMC_COUPLED = 0, MLMC_SINGLE_LEVEL = 1 } mlmc_estimator;
+ * Carlo (Eq. Yldef); P_l alone -- standard Monte Carlo with Euler--Maruyama at step T / M^l
+ * (Sec. 3), the comparison of Sec. 6; or the antithetic difference (Sec. 7: antithetic
+ * variables inside multilevel Monte Carlo, after Giles and Szpruch)
+ * Y = (P_l + P_l^a) / 2 - P_{l-1}, where the antithetic fine path P_l^a takes the same fine
+ * increments with the M increments of every coarse step in reverse order (M = 2: swapped), so
+ * it has the fine path's law and E[Y] is unchanged.  GBM with M = 2 or 4, one thread per
+ * sample; cost 2 M^l + M^(l-1) steps.  Under GBM the step factors commute, so payoffs of S(T)
+ * alone are unchanged; the trapezoid average and the maximum gain. */
+typedef enum mlmc_estimator { MLMC_COUPLED = 0, MLMC_SINGLE_LEVEL = 1, MLMC_ANTITHETIC = 2 } mlmc_estimator;
 typedef struct mlmc_payoff {
     int32_t kind;          /* mlmc_payoff_kind */
-    int32_t estimator;     /* mlmc_estimator (the drivers require MLMC_COUPLED) */
+    int32_t estimator;     /* mlmc_estimator (mlmc_estimate: COUPLED or ANTITHETIC; batch and
+                              control variate: COUPLED) */
     double K;              /* strike, finite */
     double cash;           /* digital cash amount (Sec. 6 uses 100), finite */
 } mlmc_payoff;

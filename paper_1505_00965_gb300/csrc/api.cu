@@ -78,7 +78,8 @@ int check_problem(const mlmc_model *model, const mlmc_payoff *payoff)
         !std::isfinite(model->r))
         return fail(MLMC_EINVAL, "GBM needs finite S0 > 0, sigma > 0, T > 0 and r");
     if (!valid_payoff_kind(payoff->kind)) return fail(MLMC_EINVAL, "unsupported payoff kind %d", payoff->kind);
-    if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_SINGLE_LEVEL)
+    if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_SINGLE_LEVEL &&
+        payoff->estimator != MLMC_ANTITHETIC)
         return fail(MLMC_EINVAL, "unsupported estimator %d", payoff->estimator);
     if (!std::isfinite(payoff->K) || !std::isfinite(payoff->cash))
         return fail(MLMC_EINVAL, "payoff K and cash must be finite");
@@ -238,7 +239,34 @@ int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *
                  const mlmc_launch *launch, Plan *plan)
 {
     if (model->kind == MLMC_MODEL_QUINTIC_ODE) return plan_ode(level, M, N, precision, model->scheme, launch, plan);
-    return plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, plan);
+    if (payoff->estimator != MLMC_ANTITHETIC)
+        return plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, plan);
+    // antithetic: one thread per sample; the kernel of levels with M^l < 4 reads the flag
+    if (M != 2 && M != 4) return fail(MLMC_ENOTIMPL, "the antithetic estimator is built for M = 2 and 4 (M = %d)", M);
+    if (launch && launch->lanes_per_path > 1)
+        return fail(MLMC_EINVAL, "the antithetic estimator runs one thread per sample (lanes_per_path %d)",
+                    launch->lanes_per_path);
+    mlmc_launch one = launch ? *launch : mlmc_launch{0, 0, 0, 0};
+    one.lanes_per_path = 1;
+    int rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, &one, plan);
+    if (rc || ipow(M, level) < 4) return rc;
+    const int mt = M == 4 ? 4 : 0;
+    plan->kernel = precision == MLMC_FP32_PATH ? level_anti_kernel_fp32(payoff->kind, mt, model->scheme)
+                                               : level_anti_kernel_fp64(payoff->kind, mt, model->scheme);
+    if (!plan->kernel) return fail(MLMC_EINVAL, "no antithetic kernel for payoff %d", payoff->kind);
+    int resident = 0;
+    rc = max_resident_blocks(plan->kernel, plan->threads, &resident);
+    if (rc) return rc;
+    if (!(launch && launch->blocks)) plan->blocks = std::max(1, std::min(plan->blocks, resident));
+    return MLMC_OK;
+}
+
+double problem_cost(int level, int M, const mlmc_payoff *payoff)
+{
+    if (level > 0 && payoff->estimator == MLMC_ANTITHETIC)
+        return (double)(2 * ipow(M, level) + ipow(M, level - 1));
+    if (payoff->estimator == MLMC_SINGLE_LEVEL) return (double)ipow(M, level);
+    return level_cost(level, M);
 }
 
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
@@ -276,6 +304,7 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.scheme = m->scheme;
     p.fine_only = pay->estimator == MLMC_SINGLE_LEVEL ? 1 : 0;
     p.u23 = precision == MLMC_FP64_STREAM32 ? 1 : 0;
+    p.antithetic = pay->estimator == MLMC_ANTITHETIC ? 1 : 0;
     p.partials = nullptr;
     p.out = nullptr;
     p.ticket = nullptr;
@@ -548,7 +577,7 @@ int mlmc_level_sums_ex(int level, int M, uint64_t N, uint64_t first, const mlmc_
         if (rc) return rc;
     }
     std::memcpy(sums, out, sizeof(out));
-    *cost = (double)N * level_cost(level, M);
+    *cost = (double)N * problem_cost(level, M, payoff);
     return MLMC_OK;
 }
 
@@ -589,7 +618,8 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (!out) return fail(MLMC_EINVAL, "out must not be NULL");
     rc = check_estimate_args(eps, M, Lmin, Lmax, N0, precision);
     if (rc) return rc;
-    if (payoff->estimator != MLMC_COUPLED) return fail(MLMC_EINVAL, "the adaptive driver needs the coupled estimator");
+    if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_ANTITHETIC)
+        return fail(MLMC_EINVAL, "the adaptive driver needs the coupled or antithetic estimator");
     cudaStream_t st = (cudaStream_t)stream;
 
     // One workspace for every launch of this call: launches are ordered on `st`.
@@ -614,6 +644,8 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
+    if (payoff->estimator == MLMC_ANTITHETIC)  // two fine paths per sample: 2 M^l + M^(l-1) steps
+        for (int l = 1; l < MLMC_MAX_LEVELS; ++l) drv.set_cost_scale(l, (2.0 * M + 1.0) / (M + 1.0));
     double kernel_ms = 0.0;
     uint64_t launches = 0, d2h_bytes = 0;
     while (drv.active()) {

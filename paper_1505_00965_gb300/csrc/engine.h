@@ -34,6 +34,7 @@ struct LevelParams {
     int scheme;       // 0 Euler--Maruyama, 1 Milstein
     int fine_only;    // 1: Y = P_l alone (single-level estimator)
     int u23;          // FP64 arithmetic on the FP32 stream's 23-bit uniforms
+    int antithetic;   // antithetic estimator (read by the kernel of levels with M^l < 4)
     double *partials; // [gridDim.x][4] block partial sums (workspace)
     double *out;      // [4] level sums (device)
     unsigned *ticket; // completion counter (workspace), zero between launches
@@ -52,6 +53,9 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 // Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel and
 // -1 for the kernel of levels with M^l < 4.
 const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme);
+// Antithetic level kernels (level_anti_fp32.cu, level_anti_fp64.cu): mt = 4 (M = 4) or 0 (M = 2).
+const void *level_anti_kernel_fp32(int payoff, int mt, int scheme);
+const void *level_anti_kernel_fp64(int payoff, int mt, int scheme);
 // Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
 const void *ode_level_kernel(int precision, int scheme);
 const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme);

@@ -40,6 +40,8 @@ int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
                  const mlmc_model *m, const mlmc_payoff *pay, uint64_t seed, int tag, int lanes, int precision);
 double level_cost(int level, int M);
+// Euler--Maruyama steps of one sample of the payoff's estimator (level_cost for the coupled one).
+double problem_cost(int level, int M, const mlmc_payoff *payoff);
 int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st);
 int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int precision);
 

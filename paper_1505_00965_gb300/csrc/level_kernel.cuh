@@ -174,18 +174,22 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
 // (no split): the samples' Philox chains and step chains are independent, so the scheduler can
 // interleave them.  Each sample's arithmetic is the same as in simulate_steps.  States start at
 // 1 (paths relative to S0).  CALLS, when nonzero, is the number of Philox calls per path known
-// at compile time (1 on levels with M^l = 4: straight-line code).
-template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0>
+// at compile time (1 on levels with M^l = 4: straight-line code).  ANTI adds the antithetic fine
+// path (aS, asum, ahi, als): the same increments with each coarse step's M in reverse order
+// (M = 4: a Philox block is one coarse step, read backwards; M = 2: its two pairs swapped).
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false>
 __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint64_t s[NS], R fS[NS],
                                                R fsum[NS], R fhi[NS], R fls[NS], R cS[NS], R csum[NS],
-                                               R chi[NS], R cls[NS])
+                                               R chi[NS], R cls[NS], R aS[NS], R asum[NS], R ahi[NS],
+                                               R als[NS])
 {
+    static_assert(!ANTI || MT == 4 || MT == 0, "antithetic paths for M = 4 (MT = 4) and M = 2 (MT = 0)");
     const R a = R(p.a), rh = R(p.rh);
     const R c2 = R(p.c2), rhm = R(p.rh - p.c2);
     const int M = MT ? MT : p.M;
     const R rHm = R(M * (p.rh - p.c2));
     const bool u23 = p.u23 != 0;
-    R flo[NS], clo[NS], dc[NS];
+    R flo[NS], clo[NS], alo[NS], dc[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         fS[i] = cS[i] = R(1);
@@ -193,6 +197,10 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
         fhi[i] = chi[i] = flo[i] = clo[i] = R(1);
         fls[i] = cls[i] = R(0);
         dc[i] = R(0);
+        if constexpr (ANTI) {
+            aS[i] = ahi[i] = alo[i] = R(1);
+            asum[i] = als[i] = R(0);
+        }
     }
     int q = 0;
     const int calls = CALLS ? CALLS : p.nf >> 2;
@@ -241,6 +249,13 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
                     dc[i] += dk;
                 }
                 em_step<R, PAY, false>(fS[i], fsum[i], fhi[i], flo[i], fls[i], dk);
+                if constexpr (ANTI) {
+                    const int ka = MT == 4 ? 3 - k : (k ^ 1);
+                    R da;
+                    if constexpr (MIL) da = fma(fma(c2, d[i][ka], a), d[i][ka], rhm);
+                    else da = d[i][ka];
+                    em_step<R, PAY, false>(aS[i], asum[i], ahi[i], alo[i], als[i], da);
+                }
                 if (coarse_now) {
                     R dcs;
                     if constexpr (MIL) dcs = fma(fma(c2, dc[i], a), dc[i], rHm);
@@ -430,7 +445,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
 
 // One thread per sample, NS samples per thread and iteration (idx, idx + T, ...), over the
 // samples [first, first + N) (the arguments as for regular_range below).
-template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0>
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false>
 __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
                                             uint64_t T, double m[4], float &b1, float &b2, float &b3,
                                             float &b4, int &nb, double *y_out)
@@ -446,11 +461,16 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
             s[i] = first + (idx[i] < N ? idx[i] : N - 1);
         }
         R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
-        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls);
+        R aS[NS], asum[NS], ahi[NS], als[NS];
+        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls, aS, asum,
+                                                             ahi, als);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-            const R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
-                                              R(p.nf) * logS0 + fls[i], inv_nf, p);
+            R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
+                                        R(p.nf) * logS0 + fls[i], inv_nf, p);
+            if constexpr (ANTI)
+                Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
+                                                         R(p.nf) * logS0 + als[i], inv_nf, p));
             R Y = Pf;
             if (!p.fine_only)
                 Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
@@ -467,7 +487,7 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
 // thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
 // Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
 // sample first + i into y_out[i] when y_out is not NULL.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool ANTI = false>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
@@ -477,10 +497,11 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
         // one sample per thread and iteration; a sample of a level with M^l = 4 is a single
         // Philox block and runs as straight-line code
         if (p.nf == 4)
-            multi_range<R, MT, PAY, MIL, 1, RK, 1>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
         else
-            multi_range<R, MT, PAY, MIL, 1, RK>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK, 0, ANTI>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
     } else {
+        static_assert(!ANTI, "antithetic paths run one thread per sample");
         const int P = p.lanes;
         const uint64_t groups = T / P;
         const uint64_t g = t / P;
@@ -565,8 +586,15 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
             if constexpr (MIL) dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
             else dcs = d0 + d1;
             em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
-            const R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls,
-                                              inv_nf, p);
+            R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls, inv_nf, p);
+            if (p.antithetic) {
+                // the antithetic fine path: the coarse step's two increments swapped
+                R aS = R(1), asum = R(0), ahi = R(1), alo = R(1), als = R(0);
+                em_step<R, PAY, false>(aS, asum, ahi, alo, als, d1);
+                em_step<R, PAY, false>(aS, asum, ahi, alo, als, d0);
+                Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS, S0 * asum, S0 * ahi, R(2) * logS0 + als,
+                                                         inv_nf, p));
+            }
             if (p.fine_only) {
                 Y = Pf;
             } else {
@@ -607,14 +635,15 @@ __device__ __forceinline__ void fold_batch(double m[4], float b1, float b2, floa
     }
 }
 
-// One level, one thread (or P lanes) per sample, grid-stride over the samples.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL>
+// One level, one thread (or P lanes) per sample, grid-stride over the samples; ANTI: the
+// antithetic estimator Y = (P_f + P_f^a) / 2 - P_c (one thread per sample).
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool ANTI = false>
 __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
 {
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
     int nb = 0;
-    regular_range<R, MT, PAY, SPLIT, MIL>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+    regular_range<R, MT, PAY, SPLIT, MIL, true, ANTI>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                      (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
     fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
@@ -743,6 +772,26 @@ template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bo
 template <typename R> const void *select_level_kernel(int payoff, int mt, bool split, int scheme)
 {
     return scheme == 1 ? select_scheme<R, true>(payoff, mt, split) : select_scheme<R, false>(payoff, mt, split);
+}
+
+// Antithetic kernels: mt = 4 (M = 4) or 0 (M = 2), one thread per sample; nullptr otherwise.
+template <typename R, int MT, bool MIL> const void *select_anti_by_payoff(int payoff)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, false, MIL, true>;
+    case kAsian: return (const void *)level_kernel<R, MT, kAsian, false, MIL, true>;
+    case kLookback: return (const void *)level_kernel<R, MT, kLookback, false, MIL, true>;
+    case kDigital: return (const void *)level_kernel<R, MT, kDigital, false, MIL, true>;
+    case kLinear: return (const void *)level_kernel<R, MT, kLinear, false, MIL, true>;
+    case kGeoAsian: return (const void *)level_kernel<R, MT, kGeoAsian, false, MIL, true>;
+    default: return nullptr;
+    }
+}
+template <typename R> const void *select_anti_kernel(int payoff, int mt, int scheme)
+{
+    if (mt == 4) return scheme == 1 ? select_anti_by_payoff<R, 4, true>(payoff) : select_anti_by_payoff<R, 4, false>(payoff);
+    if (mt == 0) return scheme == 1 ? select_anti_by_payoff<R, 0, true>(payoff) : select_anti_by_payoff<R, 0, false>(payoff);
+    return nullptr;
 }
 
 template <typename R> const void *select_batch_kernel(int mt)

@@ -31,7 +31,7 @@ PAYOFFS = {"european": 0, "asian": 1, "lookback": 2, "digital": 3, "second_momen
 MLMC_FP64, MLMC_FP32_PATH, MLMC_FP64_STREAM32 = 0, 1, 2
 PRECISIONS = {"fp64": MLMC_FP64, "fp32": MLMC_FP32_PATH, "fp64_stream32": MLMC_FP64_STREAM32}
 SCHEMES = {"em": 0, "milstein": 1, "tamed": 2}
-ESTIMATORS = {"coupled": 0, "single": 1}
+ESTIMATORS = {"coupled": 0, "single": 1, "antithetic": 2}
 MLMC_TAG_PATHS, MLMC_TAG_CV_MEAN, MLMC_TAG_CV_TRAIN = 0, 1, 2
 MLMC_MAX_LEVELS = 16
 

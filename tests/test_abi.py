@@ -157,6 +157,7 @@ def test_product_does_not_reference_the_oracle():
     (dict(kind="gbm", scheme="tamed"), None, "Milstein"),
     (dict(payoff="second_moment"), None, "payoff kind"),
     (dict(kind="quintic", scheme="em", payoff="second_moment"), {"lanes_per_path": 4}, "one thread per sample"),
+    (dict(kind="quintic", scheme="tamed", payoff="second_moment", estimator="antithetic"), None, "estimator"),
 ])
 def test_quintic_model_arguments_rejected_on_host(kw, launch, msg):
     """The QUINTIC_ODE model (Sec. 5, Eq. count) pairs with EM or tamed EM and the second moment;
