@@ -224,6 +224,15 @@ def side_workloads(mlmc, stream) -> dict:
                         "converged": sum(r.converged for r in res), "problems": len(res),
                         "workload": "K~U[80,120], sigma~U[0.1,0.5], T~U[0.25,2], r=0.05, payoff uniform over "
                                     "European/Asian/lookback/digital, eps log-uniform in [1e-3,1e-2], seeds 1..512"}
+    # the antithetic estimator (Sec. 7) on the benchmark's options and eps, Euler--Maruyama
+    anti = {}
+    for p in PAYOFFS:
+        prob = mlmc.Problem(payoff=p, cash=1.0, estimator="antithetic", **GBM)
+        mlmc.mlmc_estimate(EPS, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
+        times = [mlmc.mlmc_estimate(EPS, prob, s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream).wall_ms
+                 for s in range(1, 9)]
+        anti[p] = statistics.median(times)
+    out["antithetic_time_to_eps_ms"] = anti
     prob = mlmc.Problem(payoff="asian", cash=1.0, **GBM)
     t = time.perf_counter()
     cv = mlmc.mlmc_cv_train(M, prob, seed=2024, levels=4, epochs=20, n_train=1_000_000, stream=stream)
