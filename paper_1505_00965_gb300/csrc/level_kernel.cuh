@@ -118,11 +118,21 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     const int M = MT ? MT : p.M;
     const R rHm = R(M * (p.rh - p.c2));
     const bool u23 = p.u23 != 0;
+    const R a_s = R(p.a) * R(kSqrt2Ln2);  // FP32: sigma sqrt(h) sqrt(2 ln 2), for box_muller_lg2
     for (int j = j0; j < j1; ++j) {
         const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, slo, shi, p.ctr3));
         R rho, c, s;
         R d[4];
-        if constexpr (!MIL) {
+        if constexpr (!MIL && sizeof(R) == 4) {
+            box_muller_lg2(x.x, x.y, rho, c, s);
+            R ra = rho * a_s;
+            d[0] = fma(ra, c, rh);
+            d[1] = fma(ra, s, rh);
+            box_muller_lg2(x.z, x.w, rho, c, s);
+            ra = rho * a_s;
+            d[2] = fma(ra, c, rh);
+            d[3] = fma(ra, s, rh);
+        } else if constexpr (!MIL) {
             BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
             R ra = rho * a;
             d[0] = fma(ra, c, rh);
@@ -189,6 +199,7 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
     const int M = MT ? MT : p.M;
     const R rHm = R(M * (p.rh - p.c2));
     const bool u23 = p.u23 != 0;
+    const R a_s = R(p.a) * R(kSqrt2Ln2);  // FP32: sigma sqrt(h) sqrt(2 ln 2), for box_muller_lg2
     R flo[NS], clo[NS], alo[NS], dc[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -210,23 +221,34 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
         for (int i = 0; i < NS; ++i) {
             const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, (uint32_t)s[i], (uint32_t)(s[i] >> 32), p.ctr3));
             R rho, c, sn;
-            BoxMuller<R>::pair(x.x, x.y, rho, c, sn, u23);
-            if constexpr (MIL) {
-                d[i][0] = rho * c;
-                d[i][1] = rho * sn;
-            } else {
-                const R ra = rho * a;
+            if constexpr (!MIL && sizeof(R) == 4) {
+                box_muller_lg2(x.x, x.y, rho, c, sn);
+                R ra = rho * a_s;
                 d[i][0] = fma(ra, c, rh);
                 d[i][1] = fma(ra, sn, rh);
-            }
-            BoxMuller<R>::pair(x.z, x.w, rho, c, sn, u23);
-            if constexpr (MIL) {
-                d[i][2] = rho * c;
-                d[i][3] = rho * sn;
-            } else {
-                const R ra = rho * a;
+                box_muller_lg2(x.z, x.w, rho, c, sn);
+                ra = rho * a_s;
                 d[i][2] = fma(ra, c, rh);
                 d[i][3] = fma(ra, sn, rh);
+            } else {
+                BoxMuller<R>::pair(x.x, x.y, rho, c, sn, u23);
+                if constexpr (MIL) {
+                    d[i][0] = rho * c;
+                    d[i][1] = rho * sn;
+                } else {
+                    const R ra = rho * a;
+                    d[i][0] = fma(ra, c, rh);
+                    d[i][1] = fma(ra, sn, rh);
+                }
+                BoxMuller<R>::pair(x.z, x.w, rho, c, sn, u23);
+                if constexpr (MIL) {
+                    d[i][2] = rho * c;
+                    d[i][3] = rho * sn;
+                } else {
+                    const R ra = rho * a;
+                    d[i][2] = fma(ra, c, rh);
+                    d[i][3] = fma(ra, sn, rh);
+                }
             }
         }
 #pragma unroll
@@ -528,6 +550,19 @@ __device__ __forceinline__ void block_increments(const LevelParams &p, uint64_t 
     const bool u23 = p.u23 != 0;
     const uint4 x = philox_of<RK>(p, make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3));
     R rho, c, s;
+    if constexpr (!MIL && sizeof(R) == 4) {
+        // FP32 Euler--Maruyama needs the increments only (z is left unset)
+        const R a_s = a * R(kSqrt2Ln2);
+        box_muller_lg2(x.x, x.y, rho, c, s);
+        R ra = rho * a_s;
+        d[0] = fma(ra, c, rh);
+        d[1] = fma(ra, s, rh);
+        box_muller_lg2(x.z, x.w, rho, c, s);
+        ra = rho * a_s;
+        d[2] = fma(ra, c, rh);
+        d[3] = fma(ra, s, rh);
+        return;
+    }
     BoxMuller<R>::pair(x.x, x.y, rho, c, s, u23);
     z[0] = rho * c;
     z[1] = rho * s;
@@ -581,10 +616,13 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
             const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
             em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
             em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d1);
-            const R zc = z[2 * (r & 1)] + z[2 * (r & 1) + 1];
             R dcs;
-            if constexpr (MIL) dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
-            else dcs = d0 + d1;
+            if constexpr (MIL) {
+                const R zc = z[2 * (r & 1)] + z[2 * (r & 1) + 1];
+                dcs = fma(fma(c2, zc, a), zc, R(2) * rhm);
+            } else {
+                dcs = d0 + d1;
+            }
             em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
             R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls, inv_nf, p);
             if (p.antithetic) {
@@ -620,10 +658,39 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const uint64_t end = first + N;
     const uint64_t q0 = first / G;
     const uint64_t nq = (end - 1) / G - q0 + 1;
-    for (uint64_t u = t; u < nq; u += T) {
+    if (p.nf != 1) {
+        for (uint64_t u = t; u < nq; u += T) {
+            R z[4], d[4];
+            block_increments<R, MIL, RK>(p, q0 + u, z, d);
+            small_block<R, PAY, MIL>(p, q0 + u, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
+        }
+        return;
+    }
+    // level 0: the blocks [qa, qb) hold four samples of the range each and run without range
+    // checks; the first and last block of the range, when only partly inside, follow
+    const uint64_t qa = (first + 3) / 4, qb = end / 4;
+    const R S0 = R(p.S0), inv_nf = R(p.inv_nf);
+    const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
+    for (uint64_t q = qa + t; q < qb; q += T) {
+        R z[4], d[4], Y[4];
+        block_increments<R, MIL, RK>(p, q, z, d);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+            Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            if (y_out) y_out[q * 4 + r - first] = (double)Y[r];
+        }
+        add_moments4(Y, m, b1, b2, b3, b4, nb);
+    }
+    const uint64_t qlast = (end - 1) / 4;
+    const bool first_partial = q0 < qa || q0 >= qb;
+    const bool last_partial = qlast != q0 && qlast >= qb;
+    if ((t == 0 && first_partial) || (t == 1 && last_partial)) {
+        const uint64_t q = t == 0 ? q0 : qlast;
         R z[4], d[4];
-        block_increments<R, MIL, RK>(p, q0 + u, z, d);
-        small_block<R, PAY, MIL>(p, q0 + u, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
+        block_increments<R, MIL, RK>(p, q, z, d);
+        small_block<R, PAY, MIL>(p, q, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
     }
 }
 

@@ -99,6 +99,19 @@ template <> struct BoxMuller<float> {
     }
 };
 
+// The FP32 pair with rho / sqrt(2 ln 2) in place of rho: rho_s = -sqrt(-log2 u1), one multiply
+// fewer.  Callers that multiply rho by a scale anyway use rho_s times (scale sqrt(2 ln 2)).
+__device__ __forceinline__ void box_muller_lg2(uint32_t xa, uint32_t xb, float &rho_s, float &c, float &s)
+{
+    const float f1 = __uint_as_float((xa & 0x007FFFFFu) | 0x3F800000u);
+    const float f2 = __uint_as_float((xb & 0x007FFFFFu) | 0x3F800000u);
+    rho_s = -sqrt_approx(-lg2_approx(2.0f - f1));
+    const float theta = fmaf(-6.28318530717958647692f, f2, 9.42477796076937971538f);
+    s = sin_approx(theta);
+    c = cos_approx(theta);
+}
+constexpr float kSqrt2Ln2 = 1.17741002251547469101f;  // sqrt(2 ln 2)
+
 // FP64 stream: u = (x + 1) 2^-32 in (0, 1]; CUDA's double-precision log, sqrt and sincospi.
 // With u23 set, the FP32 stream's uniforms u = 1 - (x mod 2^23) 2^-23 instead (the samples of
 // the FP32 path, computed in FP64).
