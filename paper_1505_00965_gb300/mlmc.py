@@ -78,6 +78,7 @@ _dptr = ctypes.POINTER(ctypes.c_double)
 _pm, _pp, _pl = ctypes.POINTER(mlmc_model), ctypes.POINTER(mlmc_payoff), ctypes.POINTER(mlmc_launch)
 
 MLMC_CV_PARAMS = 4801
+MLMC_CV_LATTICE_POINTS = 65536
 MLMC_CV_MAX_LEVELS = 8
 
 

@@ -27,9 +27,30 @@ def main(argv=None) -> None:
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = automatic)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--cv-mean", type=int, default=0, metavar="R",
+                    help="time the control variate's lattice mean sample over R replicates instead "
+                         "(a seeded random network on level 0)")
     args = ap.parse_args(argv)
 
     import torch
+
+    if args.cv_mean:
+        import time
+
+        import numpy as np
+
+        cv = mlmc.mlmc_cv_create(4, mlmc.Problem(payoff="asian"))
+        theta = (np.random.default_rng(1).standard_normal(mlmc.MLMC_CV_PARAMS) * 0.2).astype(np.float32)
+        mlmc.mlmc_cv_set_params(cv, 0, theta)
+        d = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for rep in range(args.warmup + args.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mlmc.mlmc_cv_mean_sums(cv, 0, args.cv_mean, 0, 1, d)
+            dt = time.perf_counter() - t0
+        print(f"cv mean sample: {args.cv_mean} replicates, {dt * 1e3:.3f} ms per call (host clock), "
+              f"{dt / (args.cv_mean * mlmc.MLMC_CV_LATTICE_POINTS) * 1e9:.4f} ns per lattice point")
+        return
 
     prob = mlmc.Problem(payoff=args.payoff, kind=args.kind, scheme=args.scheme)
     launch = {"lanes_per_path": args.lanes, "threads_per_block": args.threads}
