@@ -340,6 +340,18 @@ def gpu_arm(args) -> None:
                               "one warp instruction per scheduler per clock",
                 "frac_at_run_clock": (achieved / (sms * 128 * run_mhz * 1e6 / 1e9)) if run_mhz else None,
                 "kernel_path_steps_per_s": steps / (kern_ms / 1e3)}
+    # SFU: two hardware approximations per normal (log2 and sqrt per pair, sine and cosine per
+    # pair), one normal per fine step, against the MUFU throughput the build's own probe measures
+    try:
+        from paper_1505_00965_gb300 import peaks as peak_probe
+
+        probe = peak_probe.measure()
+        mufu = 2.0 * steps / (kern_ms / 1e3)
+        roofline["sfu"] = {"achieved": mufu, "peak": probe["mufu_per_s"], "unit": "MUFU ops/s",
+                           "frac": mufu / probe["mufu_per_s"],
+                           "peak_basis": f"probe_peaks.cu: {probe['mufu_per_sm_per_clk']:.1f} MUFU ops per SM per clock"}
+    except Exception as exc:  # the probe is a report; the benchmark line stands without it
+        roofline["sfu"] = {"unavailable": str(exc)[:200]}
 
     # plain FP64 GPU MLMC on the same GPU, same eps (outside the timed region; Asian, first seed)
     fp64 = mlmc.mlmc_estimate(EPS, problems["asian"], seeds[0], M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64",
