@@ -128,8 +128,8 @@ int launch_cv_mean(const mlmc_cv *cv, int level, uint64_t R, uint64_t first, uin
         float *g = d_g ? d_g + done * kLatticeN : nullptr;
         int acc = (accumulate || done > 0) ? 1 : 0;
         void *args[] = {&p, (void *)&params, &d_sums2, &g, &acc};
-        CUDA_TRY(cudaLaunchKernel((const void *)cv_mean_kernel, dim3((unsigned)(nr * kChunksPerReplicate)),
-                                  dim3(kMeanThreads), args, 0, st));
+        CUDA_TRY(cudaLaunchKernel((const void *)cv_mean_tc_kernel, dim3((unsigned)(nr * kChunksPerReplicate)),
+                                  dim3(kMeanTcThreads), args, 0, st));
         done += nr;
     }
     return MLMC_OK;

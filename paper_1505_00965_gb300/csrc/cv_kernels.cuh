@@ -13,6 +13,7 @@
 #include "level_kernel.cuh"
 #include "mlmc.h"
 #include "mlp.cuh"
+#include "tc_mlp.cuh"
 #include "rng.cuh"
 
 namespace mlmcgb {
@@ -230,11 +231,10 @@ __global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, cons
 // coordinate is v = (i z_k mod n) 2^16 + D_k mod 2^32, exact; the point keeps its top 23 bits,
 // centred, u = (floor(v / 2^9) + 1/2) 2^-23 (exact in FP32), and x_k = Phi^{-1}(u_k).
 constexpr uint32_t kLatticeN = MLMC_CV_LATTICE_POINTS;
-constexpr int kMeanThreads = 256;
 constexpr uint32_t kLatticeChunk = 1024;                         // points per block
 constexpr uint32_t kChunksPerReplicate = kLatticeN / kLatticeChunk;
 static_assert(kLatticeN == 65536, "the fixed-point lattice coordinates assume n = 2^16");
-static_assert(kLatticeChunk % kMeanThreads == 0, "whole warps per chunk");
+static_assert(kLatticeChunk % kTcRows == 0, "whole tiles per chunk");
 
 __host__ __device__ constexpr uint32_t lattice_z(int k)
 {
@@ -243,21 +243,22 @@ __host__ __device__ constexpr uint32_t lattice_z(int k)
     return z;
 }
 
-// Blocks [q * 64, q * 64 + 64) take replicate p.first + q (p.N replicates), 1024 points each
-// (kMeanThreads threads).  Each block writes the sum of g over its points to partials[block];
-// the last block forms every replicate's mean Q = (1/n) sum of its 64 partials (fixed order)
-// and writes out2 = (sum Q, sum Q^2) over the launch's replicates, added to out2's old values
-// when `accumulate` is set.  g_out [p.N][n] (or NULL) receives g of every point.
-__global__ void __launch_bounds__(kMeanThreads) cv_mean_kernel(const LevelParams p, const float *__restrict__ params,
-                                                               double *out2, float *g_out, int accumulate)
+// Blocks [q * 64, q * 64 + 64) take replicate p.first + q (p.N replicates), 1024 points each:
+// 128 threads, one point per thread and tile, 8 tiles, the network on the tcgen05 tensor cores
+// (tc_mlp.cuh).  Each block writes the sum of g over its points to partials[block]; the last
+// block forms every replicate's mean Q = (1/n) sum of its 64 partials (fixed order) and writes
+// out2 = (sum Q, sum Q^2) over the launch's replicates, added to out2's old values when
+// `accumulate` is set.  g_out [p.N][n] (or NULL) receives g of every point.  A tile whose
+// tensor-core wait ran out makes the sums NaN (the driver then stops on non-finite sums).
+constexpr int kMeanTcThreads = kTcRows;
+__global__ void __launch_bounds__(kMeanTcThreads) cv_mean_tc_kernel(const LevelParams p,
+                                                                    const float *__restrict__ params,
+                                                                    double *out2, float *g_out, int accumulate)
 {
-    __shared__ MlpShared net;
-    __shared__ uint32_t xw_all[kMeanThreads / 32][128];
-    __shared__ double sm[kMeanThreads / 32][2];
+    __shared__ TcShared s;
+    __shared__ double sm[kMeanTcThreads / 32][2];
     __shared__ bool is_last;
-    load_mlp(net, params);
-    __syncthreads();
-    uint32_t *xw = xw_all[threadIdx.x >> 5];
+    const uint32_t tmem = tc_setup(s, params);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t rep = blockIdx.x / kChunksPerReplicate;
     const uint32_t chunk = blockIdx.x % kChunksPerReplicate;
@@ -273,26 +274,30 @@ __global__ void __launch_bounds__(kMeanThreads) cv_mean_kernel(const LevelParams
         D[4 * j + 3] = xb.w;
     }
     double acc = 0.0;
+    uint32_t phase = 0;
+    bool ok = true;
 #pragma unroll 1
-    for (uint32_t q = 0; q < kLatticeChunk / kMeanThreads; ++q) {
-        const uint32_t i = chunk * kLatticeChunk + q * kMeanThreads + threadIdx.x;
+    for (uint32_t tile = 0; tile < kLatticeChunk / kMeanTcThreads; ++tile) {
+        const uint32_t i = chunk * kLatticeChunk + tile * kMeanTcThreads + threadIdx.x;
         float x[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const uint32_t v = (((i * lattice_z(k)) & (kLatticeN - 1)) << 16) + D[k];
             x[k] = normcdfinvf(((float)(v >> 9) + 0.5f) * 0x1p-23f);
         }
-        const float gv = warp_mlp(net, xw, x);
+        const float gv = tc_mlp_tile(s, tmem, x, phase, ok);
         acc += (double)gv;
         if (g_out) g_out[rep * kLatticeN + i] = gv;
     }
+    tc_teardown(s, tmem);
+    if (!ok) acc = __longlong_as_double(0x7FF8000000000000LL);  // NaN: reported as non-finite sums
     acc = warp_sum(acc);
     if (lane == 0) sm[warp][0] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kMeanThreads / 32; ++w) s += sm[w][0];
-        p.partials[blockIdx.x] = s;
+        double sum = 0.0;
+        for (int w = 0; w < kMeanTcThreads / 32; ++w) sum += sm[w][0];
+        p.partials[blockIdx.x] = sum;
         __threadfence();
         is_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
     }
@@ -301,10 +306,10 @@ __global__ void __launch_bounds__(kMeanThreads) cv_mean_kernel(const LevelParams
     __threadfence();
     const uint64_t nrep = gridDim.x / kChunksPerReplicate;
     double sq = 0.0, sqq = 0.0;
-    for (uint64_t k = threadIdx.x; k < nrep; k += kMeanThreads) {
-        double s = 0.0;
-        for (uint32_t c = 0; c < kChunksPerReplicate; ++c) s += __ldcg(p.partials + k * kChunksPerReplicate + c);
-        const double Q = s / (double)kLatticeN;
+    for (uint64_t k = threadIdx.x; k < nrep; k += kMeanTcThreads) {
+        double sum = 0.0;
+        for (uint32_t c = 0; c < kChunksPerReplicate; ++c) sum += __ldcg(p.partials + k * kChunksPerReplicate + c);
+        const double Q = sum / (double)kLatticeN;
         sq += Q;
         sqq = fma(Q, Q, sqq);
     }
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kMeanThreads) cv_mean_kernel(const LevelParams
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < kMeanThreads / 32; ++w) {
+        for (int w = 0; w < kMeanTcThreads / 32; ++w) {
             a += sm[w][0];
             b += sm[w][1];
         }
