@@ -92,3 +92,27 @@ def test_antithetic_rejections(mlmc):
     with pytest.raises(mlmc.MLMCError) as ei:
         mlmc.mlmc_estimate_batch([(p, 1e-2, 1)])
     assert ei.value.status == mlmc.MLMC_EINVAL
+
+
+@pytest.mark.parametrize("level,N", [(1, 8001), (4, 1001)])
+def test_antithetic_fp64_on_fp32_stream(mlmc, level, N):
+    """FP64 arithmetic on the FP32 stream: the antithetic samples of the FP32 path, to the FP64
+    bound against the oracle on that stream."""
+    p = mlmc.Problem(payoff="asian", estimator="antithetic", **GBM)
+    op = oracle_problem(oracle, p)
+    _, y = run_level(mlmc, level, 4, N, 0, p, 21, "fp64_stream32")
+    yo = oracle.level_samples(level, 4, N, op, seed=21, stream="fp32", mode=oracle.MODE_ANTITHETIC)
+    assert np.max(np.abs(y - yo)) <= _bound("fp64", level, 4)
+
+
+def test_antithetic_empty_and_ragged_ranges(mlmc):
+    """No samples give zero sums; ranges that start and end inside a Philox block (level 0 packs
+    four samples per block; M = 2 level 1 packs two) match the oracle sample for sample."""
+    p = mlmc.Problem(payoff="lookback", estimator="antithetic", **GBM)
+    sums, _ = run_level(mlmc, 3, 4, 0, 0, p, 1, "fp32")
+    assert np.all(sums == 0)
+    op = oracle_problem(oracle, p)
+    for M, level, first, N in [(4, 0, 5, 3), (4, 0, 6, 9), (2, 1, 3, 4), (2, 1, 1, 1), (4, 2, 7, 1)]:
+        _, y = run_level(mlmc, level, M, N, first, p, 3, "fp64")
+        yo = oracle.level_samples(level, M, N, op, seed=3, first=first, stream="fp64", mode=oracle.MODE_ANTITHETIC)
+        assert np.max(np.abs(y - yo)) <= _bound("fp64", level, M), (M, level, first, N)

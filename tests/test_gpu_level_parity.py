@@ -247,3 +247,17 @@ def test_fp64_on_fp32_stream(mlmc, payoff, level, N):
     if payoff == "digital":
         d = d[d < 0.25]  # threshold flips, checked in the level parity tests
     assert np.max(d) <= _bound("fp32", level, 4, p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_level0_ranges_inside_one_philox_block(mlmc, precision):
+    """Level 0 packs four samples per Philox block and runs the blocks wholly inside the range
+    without range checks: ranges that start and end inside a block, or lie within one, match the
+    oracle sample for sample."""
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    op = oracle_problem(oracle, p)
+    for first, N in [(5, 3), (6, 9), (1, 1), (3, 2), (7, 12), (4, 4), (2 ** 35 + 2, 7)]:
+        sums, y = run_level(mlmc, 0, 4, N, first, p, 13, precision)
+        yo = oracle.level_samples(0, 4, N, op, seed=13, first=first, stream=precision)
+        assert np.max(np.abs(y - yo)) <= _bound(precision, 0, 4, p), (first, N)
+        np.testing.assert_allclose(sums[0], y.sum(), rtol=1e-6)

@@ -118,3 +118,31 @@ def test_quintic_rejected_where_not_built(mlmc):
     with pytest.raises(mlmc.MLMCError) as ei:
         mlmc.mlmc_cv_create(4, p)
     assert ei.value.status == mlmc.MLMC_ENOTIMPL
+
+
+@pytest.mark.parametrize("level,N,first", [(0, 3, 5), (0, 9, 6), (2, 1, 7), (4, 33, 2 ** 40 + 3)])
+def test_tamed_ragged_ranges_and_fp64_on_fp32_stream(mlmc, level, N, first):
+    """Ranges that start and end inside a Philox block of four samples, and FP64 arithmetic on
+    the FP32 stream (the FP32 path's samples to the FP64 bound)."""
+    seed = 9
+    p = _problem(mlmc, "tamed")
+    for precision, stream in (("fp64", "fp64"), ("fp64_stream32", "fp32")):
+        _, y = run_level(mlmc, level, 4, N, first, p, seed, precision)
+        yo = ode.level_samples(level, 4, N, T, seed, "tamed", first=first, stream=stream)
+        x0 = ode.initial_values(level, first, N, seed, stream=stream)
+        tol = 8.0 * (1.0 + x0 ** 2) * (EZ["fp64"] + 4 * U["fp64"] * math.sqrt(4 ** level + 1))
+        assert np.all(np.abs(y - yo) <= tol), precision
+
+
+def test_quintic_empty_range_and_noalloc(mlmc):
+    """No samples give zero sums; the allocation-free entry point runs the quintic kernel too."""
+    import torch
+
+    p = _problem(mlmc, "tamed")
+    sums, _ = run_level(mlmc, 2, 4, 0, 0, p, 1, "fp32")
+    assert np.all(sums == 0)
+    d = torch.zeros(4, dtype=torch.float64, device="cuda")
+    mlmc.mlmc_level_sums_noalloc(3, 4, 5000, 0, p, 1, d)
+    torch.cuda.synchronize()
+    ref, _ = run_level(mlmc, 3, 4, 5000, 0, p, 1, "fp32")
+    np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-5)
