@@ -78,21 +78,41 @@ def test_features_are_iid_standard_normal(level):
 
 
 def _lattice_offsets(r, seed, level):
-    """K_k(i) = i z_k mod n recovered from the oracle's points: u = (floor(v / 2^9) + 1/2) 2^-23
-    with v = K 2^16 + D mod 2^32 gives floor(v / 2^9) = K 2^7 + floor(D / 2^9) mod 2^23."""
+    """K_k(i) = i z_k mod n recovered from the oracle's 32-bit points v = K 2^16 + D mod 2^32."""
     i = np.arange(mlp.LATTICE_N)
-    u = mlp.lattice_uniforms(r, i, seed, level)
-    top = np.rint(u * 2.0 ** 23 - 0.5).astype(np.int64)
+    v = mlp.lattice_points32(r, i, seed, level)
     D = np.array(mlp.lattice_shift(r, seed, level), dtype=np.int64)
-    K = ((top - (D >> 9)[None, :]) % (1 << 23))
-    assert np.all(K % 128 == 0)
-    return K // 128
+    K = (v - D[None, :]) % (1 << 32)
+    assert np.all(K % 65536 == 0)
+    return K // 65536
+
+
+def test_tent_transform_is_two_to_one_onto_even_fractions():
+    """The tent transform of the 32-bit fractions: u -> 1 - |2u - 1| up to one unit, image the
+    even fractions, each hit twice (so uniform input gives uniform top-23-bit cells), and the
+    uniforms used are the centred cells of the transformed points."""
+    rng = np.random.default_rng(4)
+    v = rng.integers(0, 2 ** 32, 200_000, dtype=np.int64)
+    w = mlp.tent32(v)
+    assert np.all(w % 2 == 0) and np.all((w >= 0) & (w <= 2 ** 32 - 2))
+    u = v / 2.0 ** 32
+    assert np.max(np.abs(w / 2.0 ** 32 - (1 - np.abs(2 * u - 1)))) <= 2.0 ** -31
+    edges = np.array([0, 1, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 2, 2 ** 32 - 1], dtype=np.int64)
+    assert mlp.tent32(edges).tolist() == [0, 2, 2 ** 32 - 2, 2 ** 32 - 2, 2, 0]
+    # exhaustive on a 12-bit analogue of the map: two to one onto the even values
+    small = np.arange(4096)
+    img = np.where(small < 2048, 2 * small, 2 * (4095 - small))
+    assert np.array_equal(np.bincount(img, minlength=4096)[::2], np.full(2048, 2))
+    uu = mlp.lattice_uniforms(3, np.arange(50), seed=1, level=0)
+    ww = mlp.tent32(mlp.lattice_points32(3, np.arange(50), seed=1, level=0))
+    assert np.array_equal(uu, ((ww >> 9) + 0.5) * 2.0 ** -23)
 
 
 def test_lattice_is_the_korobov_rank1_lattice():
-    """With the random shift removed the points are i z / n for the Korobov vector
-    z = (1, a, a^2, ...) mod n: coordinate 0 is i / n, the map i -> point is additive mod n
-    (a rank-1 lattice is a group), and every coordinate runs through all n strata once."""
+    """Before the tent transform and with the random shift removed the points are i z / n for the
+    Korobov vector z = (1, a, a^2, ...) mod n: coordinate 0 is i / n, the map i -> point is
+    additive mod n (a rank-1 lattice is a group), and every coordinate runs through all n strata
+    once."""
     n = mlp.LATTICE_N
     K = _lattice_offsets(5, seed=17, level=2)
     assert np.array_equal(K[:, 0], np.arange(n))
