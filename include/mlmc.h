@@ -306,7 +306,9 @@ int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, int Lmin, in
  * rank-1 lattice rule (Sloan and Joe 1994; random shift after Cranley and Patterson 1976).
  * Replicate r has the n = MLMC_CV_LATTICE_POINTS points i = 0 .. n-1 with coordinates, k = 0..7,
  *   v_k = ((i z_k mod n) 2^16 + D_k) mod 2^32,  z_k = a^k mod n (a = MLMC_CV_LATTICE_A),
- *   u_k = (floor(v_k / 2^9) + 1/2) 2^-23,  x_k = Phi^{-1}(u_k),
+ *   w_k = 2 v_k if v_k < 2^31, else 2 (2^32 - 1 - v_k)  (the baker's, or tent, transform
+ *         u -> 1 - |2u - 1|, which keeps points uniform and suits non-periodic integrands),
+ *   u_k = (floor(w_k / 2^9) + 1/2) 2^-23,  x_k = Phi^{-1}(u_k),
  * where D_0..D_7 are the words of Philox blocks 0 and 1 of counter r under tag
  * MLMC_TAG_CV_MEAN (the random shift, as 32-bit fractions).  Every point is uniform whatever
  * the shift, so Q_r is unbiased for E[g] for any g, and replicates are independent; the lattice

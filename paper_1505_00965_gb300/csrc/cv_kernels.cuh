@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, cons
 // multiplier a = MLMC_CV_LATTICE_A, and Delta_r the eight words of Philox blocks 0 and 1 of
 // counter r under the control-variate-mean tag, read as 32-bit fractions.  In fixed point a
 // coordinate is v = (i z_k mod n) 2^16 + D_k mod 2^32, exact; the point keeps its top 23 bits,
-// centred, u = (floor(v / 2^9) + 1/2) 2^-23 (exact in FP32), and x_k = Phi^{-1}(u_k).
+// the baker's (tent) transform w = 2 v below one half, 2 (2^32 - 1 - v) above (Hickernell 2002;
+// two to one onto the even fractions, so still uniform), keeps its top 23 bits, centred,
+// u = (floor(w / 2^9) + 1/2) 2^-23 (exact in FP32), and x_k = Phi^{-1}(u_k).
 constexpr uint32_t kLatticeN = MLMC_CV_LATTICE_POINTS;
 constexpr uint32_t kLatticeChunk = 1024;                         // points per block
 constexpr uint32_t kChunksPerReplicate = kLatticeN / kLatticeChunk;
@@ -283,7 +285,8 @@ __global__ void __launch_bounds__(kMeanTcThreads) cv_mean_tc_kernel(const LevelP
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const uint32_t v = (((i * lattice_z(k)) & (kLatticeN - 1)) << 16) + D[k];
-            x[k] = normcdfinvf(((float)(v >> 9) + 0.5f) * 0x1p-23f);
+            const uint32_t w = v < 0x80000000u ? v << 1 : (~v) << 1;  // tent: 2v, or 2 (2^32 - 1 - v)
+            x[k] = normcdfinvf(((float)(w >> 9) + 0.5f) * 0x1p-23f);
         }
         const float gv = tc_mlp_tile(s, tmem, x, phase, ok);
         acc += (double)gv;
