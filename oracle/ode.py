@@ -32,14 +32,15 @@ SCHEMES = ("em", "tamed")
 
 
 def initial_values(level: int, first: int, N: int, seed: int, stream: str = "fp64", tag: int = TAG_PATHS):
-    """X(0) of samples [first, first + N)."""
-    s = np.arange(first, first + N, dtype=np.int64)
+    """X(0) of samples [first, first + N) (any 64-bit sample indices)."""
     out = np.empty(N, dtype=np.float64)
     q0, q1 = first // 4, (first + N - 1) // 4
     for q in range(q0, q1 + 1):
         z = normals(seed, level, q, 4, stream=stream, tag=tag)
-        sel = (s // 4) == q
-        out[sel] = z[s[sel] % 4]
+        # samples 4q .. 4q + 3 that lie in the range, as offsets i = s - first
+        lo, hi = max(4 * q, first), min(4 * q + 4, first + N)
+        for s in range(lo, hi):
+            out[s - first] = z[s - 4 * q]
     return out
 
 

@@ -25,6 +25,9 @@ namespace {
 
 thread_local std::string g_error;
 
+// Least cost of a launch with fewer items than one wave, in waves (see plan_level)
+constexpr double kLoneWaveCost = 0.25;
+
 }  // namespace
 
 namespace mlmcgb {
@@ -147,14 +150,17 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
         // (its warps run faster on the emptier SMs).  A lane costs its M^l / P steps plus about
         // 12 steps of chunk join, payoff and moments, and a split step about 5 % more than a
         // whole-path one.  A larger P must win by more than 1 %.  (Fitted to launch timings
-        // of levels 3..8 at 0.25..4.5 waves.)
+        // of levels 3..8 at 0.25..4.5 waves.)  Fewer items than one wave still cost at least a
+        // quarter of a wave: a warp alone on its scheduler takes about 64 cycles per step,
+        // against about 266 for each warp of a full SM (measured on levels 6..12 at 1 to 2^15
+        // samples), so short launches go to the most lanes.
         lanes = 1;
         if (nf >= 8) {
             const int mt1 = M == 4 ? 4 : 0;
-            const void *k1 = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, false, scheme)
-                                                         : level_kernel_fp64(payoff, mt1, false, scheme);
-            const void *kp = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, true, scheme)
-                                                         : level_kernel_fp64(payoff, mt1, true, scheme);
+            const void *k1 = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, false, scheme, false)
+                                                         : level_kernel_fp64(payoff, mt1, false, scheme, false);
+            const void *kp = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt1, true, scheme, false)
+                                                         : level_kernel_fp64(payoff, mt1, true, scheme, false);
             if (!k1 || !kp) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
             int res1 = 0, resp = 0;
             int rc = max_resident_blocks(k1, threads, &res1);
@@ -167,7 +173,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
                 const double T = (double)(P == 1 ? res1 : resp) * threads;
                 const double w = (double)std::max<uint64_t>(N, 1) * P / T;
                 const double full = std::floor(w);
-                const double waves = full + std::min(1.0, 3.0 * (w - full));
+                const double waves = w < 1.0 ? std::max(std::min(1.0, 3.0 * w), kLoneWaveCost)
+                                             : full + std::min(1.0, 3.0 * (w - full));
                 const double per_step = P > 1 ? 1.05 : 1.0;
                 const double cost = waves * ((double)nf / P + 12.0) * per_step;
                 if (P == 1 || cost < 0.99 * best) {
@@ -180,8 +187,9 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     const bool split = lanes > 1;
     const bool small = nf < 4;
     const int mt = small ? -1 : (M == 4 ? 4 : 0);
-    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split, scheme)
-                                               : level_kernel_fp64(payoff, mt, split, scheme);
+    const bool long_lanes = nf / lanes > kLongLaneSteps;
+    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split, scheme, long_lanes)
+                                               : level_kernel_fp64(payoff, mt, split, scheme, long_lanes);
     if (!plan->kernel) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
     int max_blocks = 0;
     int rc = max_resident_blocks(plan->kernel, threads, &max_blocks);
@@ -251,8 +259,9 @@ int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *
     int rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, &one, plan);
     if (rc || ipow(M, level) < 4) return rc;
     const int mt = M == 4 ? 4 : 0;
-    plan->kernel = precision == MLMC_FP32_PATH ? level_anti_kernel_fp32(payoff->kind, mt, model->scheme)
-                                               : level_anti_kernel_fp64(payoff->kind, mt, model->scheme);
+    const bool long_lanes = ipow(M, level) > kLongLaneSteps;
+    plan->kernel = precision == MLMC_FP32_PATH ? level_anti_kernel_fp32(payoff->kind, mt, model->scheme, long_lanes)
+                                               : level_anti_kernel_fp64(payoff->kind, mt, model->scheme, long_lanes);
     if (!plan->kernel) return fail(MLMC_EINVAL, "no antithetic kernel for payoff %d", payoff->kind);
     int resident = 0;
     rc = max_resident_blocks(plan->kernel, plan->threads, &resident);

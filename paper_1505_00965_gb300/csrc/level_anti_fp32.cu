@@ -3,8 +3,8 @@
 #include "level_kernel.cuh"
 
 namespace mlmcgb {
-const void *level_anti_kernel_fp32(int payoff, int mt, int scheme)
+const void *level_anti_kernel_fp32(int payoff, int mt, int scheme, bool long_lanes)
 {
-    return select_anti_kernel<float>(payoff, mt, scheme);
+    return select_anti_kernel<float>(payoff, mt, scheme, long_lanes);
 }
 }  // namespace mlmcgb

@@ -2,9 +2,9 @@
 #include "level_kernel.cuh"
 
 namespace mlmcgb {
-const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme)
+const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes)
 {
-    return select_level_kernel<double>(payoff, mt, split, scheme);
+    return select_level_kernel<double>(payoff, mt, split, scheme, long_lanes);
 }
 const void *batch_kernel_fp64(int mt)
 {

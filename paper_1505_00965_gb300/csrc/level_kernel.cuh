@@ -22,6 +22,17 @@
 
 namespace mlmcgb {
 
+// Philox calls (4 fine steps each) per partial of the Asian running sums: a path's sum of its
+// values adds in two levels, a partial over each group of 4 kSumGroup = 256 steps folded into the
+// total at the group's end.  One accumulator over all M^l values of order one loses, in FP32, a
+// relative 1e-5 of the average at 2^16 steps and 1e-3 to 1e-2 at 2^20 to 2^22 steps (each add
+// rounds to the total's ulp); two levels keep it near 1e-6 up to 2^24 steps.  The kernels for
+// lanes of more than kLongLaneSteps steps (template flag LONG, FP32 arithmetic-Asian kernels
+// only) sum in two levels; shorter lanes, FP64 paths (whose adds round 2^29 times finer) and the
+// other payoffs keep the single step loop, whose code the grouped one slows by 2-3 %.
+constexpr int kSumGroup = 64;
+template <typename R, int PAY> constexpr bool kBlockedSum = PAY == kAsian && sizeof(R) == 4;
+
 // Running state of one path over the steps a lane simulates.  The step loops below keep these
 // values in local scalars and store the struct once at the end: an FP64 build that updated the
 // struct's members through a reference inside the loop lost the updates (every step restarted
@@ -104,7 +115,7 @@ __device__ __forceinline__ uint4 philox_of(const LevelParams &p, uint4 c)
 // coarse factor's d is the sum of the M fine ones.  Milstein (MIL): d = r h + sigma dW
 // + sigma^2 (dW^2 - h) / 2 = (r h - c2) + a z + c2 z^2 with a = sigma sqrt(h), c2 = sigma^2 h / 2,
 // and the coarse step the same formula on the summed increment with step M h.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false>
 __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t slo, uint32_t shi,
                                                int j0, int j1, PathAcc<R, PAY, SPLIT> &fa,
                                                PathAcc<R, PAY, SPLIT> &ca)
@@ -119,7 +130,8 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     const R rHm = R(M * (p.rh - p.c2));
     const bool u23 = p.u23 != 0;
     const R a_s = R(p.a) * R(kSqrt2Ln2);  // FP32: sigma sqrt(h) sqrt(2 ln 2), for box_muller_lg2
-    for (int j = j0; j < j1; ++j) {
+    // one Philox call: four fine steps and the coarse steps they complete
+    auto call = [&](int j) {
         const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, slo, shi, p.ctr3));
         R rho, c, s;
         R d[4];
@@ -175,6 +187,20 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
                 dc = R(0);
             }
         }
+    };
+    if constexpr (!(LONG && kBlockedSum<R, PAY>)) {
+        for (int j = j0; j < j1; ++j) call(j);
+    } else {
+        R fsum_t = R(0), csum_t = R(0);  // totals of the finished groups
+        for (int g = j0; g < j1; g += kSumGroup) {
+            const int ge = min(g + kSumGroup, j1);
+            for (int j = g; j < ge; ++j) call(j);
+            fsum_t += fsum;
+            csum_t += csum;
+            fsum = csum = R(0);
+        }
+        fsum = fsum_t;
+        csum = csum_t;
     }
     fa.S = fS; fa.sum = fsum; fa.hi = fhi; fa.lo = flo; fa.lsum = fls;
     ca.S = cS; ca.sum = csum; ca.hi = chi; ca.lo = clo; ca.lsum = cls;
@@ -187,7 +213,8 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
 // at compile time (1 on levels with M^l = 4: straight-line code).  ANTI adds the antithetic fine
 // path (aS, asum, ahi, als): the same increments with each coarse step's M in reverse order
 // (M = 4: a Philox block is one coarse step, read backwards; M = 2: its two pairs swapped).
-template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false>
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false,
+          bool LONG = false>
 __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint64_t s[NS], R fS[NS],
                                                R fsum[NS], R fhi[NS], R fls[NS], R cS[NS], R csum[NS],
                                                R chi[NS], R cls[NS], R aS[NS], R asum[NS], R ahi[NS],
@@ -215,7 +242,8 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
     }
     int q = 0;
     const int calls = CALLS ? CALLS : p.nf >> 2;
-    for (int j = 0; j < calls; ++j) {
+    // one Philox call per sample: four fine steps and the coarse steps they complete
+    auto call = [&](int j) {
         R d[NS][4];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -286,6 +314,33 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
                     dc[i] = R(0);
                 }
             }
+        }
+    };
+    if constexpr (!(LONG && kBlockedSum<R, PAY>)) {
+        for (int j = 0; j < calls; ++j) call(j);
+    } else {
+        R fsum_t[NS], csum_t[NS], asum_t[NS];  // totals of the finished groups
+#pragma unroll
+        for (int i = 0; i < NS; ++i) fsum_t[i] = csum_t[i] = asum_t[i] = R(0);
+        for (int g = 0; g < calls; g += kSumGroup) {
+            const int ge = min(g + kSumGroup, calls);
+            for (int j = g; j < ge; ++j) call(j);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                fsum_t[i] += fsum[i];
+                csum_t[i] += csum[i];
+                fsum[i] = csum[i] = R(0);
+                if constexpr (ANTI) {
+                    asum_t[i] += asum[i];
+                    asum[i] = R(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            fsum[i] = fsum_t[i];
+            csum[i] = csum_t[i];
+            if constexpr (ANTI) asum[i] = asum_t[i];
         }
     }
 }
@@ -431,7 +486,7 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
 
 // Y of sample s on a level with M^l >= 4, computed by the P lanes of one group (lane lig);
 // every lane of the group returns the same Y.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false>
 __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig, int P)
 {
     const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
@@ -443,7 +498,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     fa.init(R(1));
     ca.init(R(1));
     if constexpr (!SPLIT) {
-        simulate_steps<R, MT, PAY, false, MIL, RK>(p, slo, shi, 0, p.nf >> 2, fa, ca);
+        simulate_steps<R, MT, PAY, false, MIL, RK, LONG>(p, slo, shi, 0, p.nf >> 2, fa, ca);
         const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
         const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
                                           R(p.nf) * logS0 + fa.lsum, inv_nf, p);
@@ -453,7 +508,7 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
-        simulate_steps<R, MT, PAY, true, MIL, RK>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+        simulate_steps<R, MT, PAY, true, MIL, RK, LONG>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
         const R steps_f = R(4 * calls);
         R tf, pf, hf, lf, tc, pc, hc, lc;
         join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
@@ -467,7 +522,8 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
 
 // One thread per sample, NS samples per thread and iteration (idx, idx + T, ...), over the
 // samples [first, first + N) (the arguments as for regular_range below).
-template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false>
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false,
+          bool LONG = false>
 __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
                                             uint64_t T, double m[4], float &b1, float &b2, float &b3,
                                             float &b4, int &nb, double *y_out)
@@ -484,7 +540,7 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
         }
         R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
         R aS[NS], asum[NS], ahi[NS], als[NS];
-        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls, aS, asum,
+        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls, aS, asum,
                                                              ahi, als);
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -509,7 +565,8 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
 // thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
 // Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
 // sample first + i into y_out[i] when y_out is not NULL.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool ANTI = false>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool ANTI = false,
+          bool LONG = false>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
@@ -519,9 +576,9 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
         // one sample per thread and iteration; a sample of a level with M^l = 4 is a single
         // Philox block and runs as straight-line code
         if (p.nf == 4)
-            multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
         else
-            multi_range<R, MT, PAY, MIL, 1, RK, 0, ANTI>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            multi_range<R, MT, PAY, MIL, 1, RK, 0, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
     } else {
         static_assert(!ANTI, "antithetic paths run one thread per sample");
         const int P = p.lanes;
@@ -533,7 +590,7 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
             const uint64_t idx = base + g;
             const bool valid = idx < N;
             const uint64_t s = first + (valid ? idx : N - 1);
-            const R Y = sample_Y<R, MT, PAY, true, MIL, RK>(p, s, lig, P);
+            const R Y = sample_Y<R, MT, PAY, true, MIL, RK, LONG>(p, s, lig, P);
             if (valid && lig == 0) {
                 if (y_out) y_out[idx] = (double)Y;
                 add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -667,8 +724,9 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
         return;
     }
     // level 0: the blocks [qa, qb) hold four samples of the range each and run without range
-    // checks; the first and last block of the range, when only partly inside, follow
-    const uint64_t qa = (first + 3) / 4, qb = end / 4;
+    // checks; the first and last block of the range, when only partly inside, follow (qa rounds
+    // first / 4 up without forming first + 3, which wraps for ranges at the top of 64 bits)
+    const uint64_t qa = first / 4 + ((first & 3) != 0), qb = end / 4;
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf);
     const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
     for (uint64_t q = qa + t; q < qb; q += T) {
@@ -703,14 +761,15 @@ __device__ __forceinline__ void fold_batch(double m[4], float b1, float b2, floa
 }
 
 // One level, one thread (or P lanes) per sample, grid-stride over the samples; ANTI: the
-// antithetic estimator Y = (P_f + P_f^a) / 2 - P_c (one thread per sample).
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool ANTI = false>
+// antithetic estimator Y = (P_f + P_f^a) / 2 - P_c (one thread per sample); LONG: lanes of more
+// than kLongLaneSteps steps (two-level Asian sums).
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool ANTI = false, bool LONG = false>
 __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
 {
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
     int nb = 0;
-    regular_range<R, MT, PAY, SPLIT, MIL, true, ANTI>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+    regular_range<R, MT, PAY, SPLIT, MIL, true, ANTI, LONG>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                      (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
     fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
@@ -800,13 +859,23 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelParams *__restric
 
 namespace mlmcgb {
 
-// Kernel for (payoff, M specialisation, split, scheme) at precision R; nullptr for an unknown
-// payoff.
-template <typename R, int MT, bool SPLIT, bool MIL> const void *select_by_payoff(int payoff)
+// The arithmetic-Asian kernel for lanes of `long_lanes` (more than kLongLaneSteps steps) or not;
+// the two are the same kernel where the sums keep one level (FP64 paths).
+template <typename R, int MT, bool SPLIT, bool MIL, bool ANTI> const void *asian_kernel(bool long_lanes)
+{
+    if constexpr (kBlockedSum<R, kAsian>) {
+        if (long_lanes) return (const void *)level_kernel<R, MT, kAsian, SPLIT, MIL, ANTI, true>;
+    }
+    return (const void *)level_kernel<R, MT, kAsian, SPLIT, MIL, ANTI>;
+}
+
+// Kernel for (payoff, M specialisation, split, scheme, lane length) at precision R; nullptr for
+// an unknown payoff.
+template <typename R, int MT, bool SPLIT, bool MIL> const void *select_by_payoff(int payoff, bool long_lanes)
 {
     switch (payoff) {
     case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, SPLIT, MIL>;
-    case kAsian: return (const void *)level_kernel<R, MT, kAsian, SPLIT, MIL>;
+    case kAsian: return asian_kernel<R, MT, SPLIT, MIL, false>(long_lanes);
     case kLookback: return (const void *)level_kernel<R, MT, kLookback, SPLIT, MIL>;
     case kDigital: return (const void *)level_kernel<R, MT, kDigital, SPLIT, MIL>;
     case kLinear: return (const void *)level_kernel<R, MT, kLinear, SPLIT, MIL>;
@@ -828,25 +897,29 @@ template <typename R, bool MIL> const void *select_small_kernel(int payoff)
     }
 }
 
-template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bool split)
+template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bool split, bool long_lanes)
 {
     if (mt < 0) return select_small_kernel<R, MIL>(payoff);
-    if (mt == 4) return split ? select_by_payoff<R, 4, true, MIL>(payoff) : select_by_payoff<R, 4, false, MIL>(payoff);
-    return split ? select_by_payoff<R, 0, true, MIL>(payoff) : select_by_payoff<R, 0, false, MIL>(payoff);
+    if (mt == 4)
+        return split ? select_by_payoff<R, 4, true, MIL>(payoff, long_lanes)
+                     : select_by_payoff<R, 4, false, MIL>(payoff, long_lanes);
+    return split ? select_by_payoff<R, 0, true, MIL>(payoff, long_lanes)
+                 : select_by_payoff<R, 0, false, MIL>(payoff, long_lanes);
 }
 
 // mt = -1 selects the kernel of levels with M^l < 4; scheme 1 is Milstein.
-template <typename R> const void *select_level_kernel(int payoff, int mt, bool split, int scheme)
+template <typename R> const void *select_level_kernel(int payoff, int mt, bool split, int scheme, bool long_lanes)
 {
-    return scheme == 1 ? select_scheme<R, true>(payoff, mt, split) : select_scheme<R, false>(payoff, mt, split);
+    return scheme == 1 ? select_scheme<R, true>(payoff, mt, split, long_lanes)
+                       : select_scheme<R, false>(payoff, mt, split, long_lanes);
 }
 
 // Antithetic kernels: mt = 4 (M = 4) or 0 (M = 2), one thread per sample; nullptr otherwise.
-template <typename R, int MT, bool MIL> const void *select_anti_by_payoff(int payoff)
+template <typename R, int MT, bool MIL> const void *select_anti_by_payoff(int payoff, bool long_lanes)
 {
     switch (payoff) {
     case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, false, MIL, true>;
-    case kAsian: return (const void *)level_kernel<R, MT, kAsian, false, MIL, true>;
+    case kAsian: return asian_kernel<R, MT, false, MIL, true>(long_lanes);
     case kLookback: return (const void *)level_kernel<R, MT, kLookback, false, MIL, true>;
     case kDigital: return (const void *)level_kernel<R, MT, kDigital, false, MIL, true>;
     case kLinear: return (const void *)level_kernel<R, MT, kLinear, false, MIL, true>;
@@ -854,10 +927,14 @@ template <typename R, int MT, bool MIL> const void *select_anti_by_payoff(int pa
     default: return nullptr;
     }
 }
-template <typename R> const void *select_anti_kernel(int payoff, int mt, int scheme)
+template <typename R> const void *select_anti_kernel(int payoff, int mt, int scheme, bool long_lanes)
 {
-    if (mt == 4) return scheme == 1 ? select_anti_by_payoff<R, 4, true>(payoff) : select_anti_by_payoff<R, 4, false>(payoff);
-    if (mt == 0) return scheme == 1 ? select_anti_by_payoff<R, 0, true>(payoff) : select_anti_by_payoff<R, 0, false>(payoff);
+    if (mt == 4)
+        return scheme == 1 ? select_anti_by_payoff<R, 4, true>(payoff, long_lanes)
+                           : select_anti_by_payoff<R, 4, false>(payoff, long_lanes);
+    if (mt == 0)
+        return scheme == 1 ? select_anti_by_payoff<R, 0, true>(payoff, long_lanes)
+                           : select_anti_by_payoff<R, 0, false>(payoff, long_lanes);
     return nullptr;
 }
 

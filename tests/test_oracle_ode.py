@@ -87,3 +87,15 @@ def test_tamed_multilevel_rates_and_telescoping():
     assert abs(sum(means) - Pf.mean()) < 4 * se
     # and both sit within the first-order bias of the exact value
     assert abs(Pf.mean() - ode.exact_second_moment(T)) < 4 * Pf.std() / math.sqrt(len(Pf)) + 4e-3
+
+
+def test_initial_values_at_top_of_64_bit_sample_indices():
+    """Sample indices up to 2^64 - 2: X(0) of sample s is normal (s mod 4) of Philox block
+    floor(s / 4), including blocks the range covers only in part."""
+    from oracle import normals
+
+    first, N = 2 ** 64 - 7, 6
+    x0 = ode.initial_values(3, first, N, 11, stream="fp32")
+    blocks = {q: normals(11, 3, q, 4, stream="fp32") for q in (first // 4, (first + N - 1) // 4)}
+    want = [blocks[s // 4][s % 4] for s in range(first, first + N)]
+    np.testing.assert_array_equal(x0, want)
