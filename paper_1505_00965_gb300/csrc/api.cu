@@ -359,6 +359,14 @@ void free_scratch(DriverScratch *s)
     if (s->h_sums) cudaFreeHost(s->h_sums);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->fork) cudaEventDestroy(s->fork);
+    for (int k = 0; k < kDriverStreams - 1; ++k) {
+        if (s->aux[k]) {
+            cudaStreamSynchronize(s->aux[k]);
+            cudaStreamDestroy(s->aux[k]);
+        }
+        if (s->join[k]) cudaEventDestroy(s->join[k]);
+    }
     delete s;
 }
 
@@ -385,6 +393,11 @@ int acquire_scratch(size_t ws_bytes, DriverScratch **out)
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_sums, kDriverSumsPerLevel * MLMC_MAX_LEVELS * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    for (int k = 0; k < kDriverStreams - 1 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&s->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         free_scratch(s);
         return fail(MLMC_ECUDA, "driver setup failed: %s", cudaGetErrorString(e));
@@ -631,25 +644,38 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         return fail(MLMC_EINVAL, "the adaptive driver needs the coupled or antithetic estimator");
     cudaStream_t st = (cudaStream_t)stream;
 
-    // One workspace for every launch of this call: launches are ordered on `st`.
+    // A round's level launches go round-robin over `st` and the set's own streams, deepest level
+    // first: the blocks of the next launch fill the SMs that one launch's last partial wave
+    // leaves idle, and a round of a few small launches runs them side by side.  Stream k owns
+    // workspace slot k (launches on one stream are ordered); the streams fork from `st` after
+    // the round's first event and join it before the sums are copied back, so `st` orders the
+    // whole call as before.  Each launch reduces its own sums in a fixed order, so the results
+    // do not depend on how the launches overlap.
     int sms = 0;
     rc = device_sms(&sms);
     if (rc) return rc;
     const int ws_blocks = sms * 32;
+    const size_t ws_slot = (workspace_bytes_for_blocks(ws_blocks) + 255) / 256 * 256;
     DriverScratch *sc = nullptr;
-    rc = acquire_scratch(workspace_bytes_for_blocks(ws_blocks), &sc);
+    rc = acquire_scratch(ws_slot * kDriverStreams, &sc);
     if (rc) return rc;
-    void *ws = sc->ws;
     double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
     cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
+    cudaStream_t streams[kDriverStreams];
+    void *slots[kDriverStreams];
+    for (int k = 0; k < kDriverStreams; ++k) {
+        streams[k] = k ? sc->aux[k - 1] : st;
+        slots[k] = (char *)sc->ws + ws_slot * k;
+    }
     auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         free_scratch(sc);
         return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     };
-    // the completion ticket is zero after every finished launch; clear it in case an earlier
+    // the completion tickets are zero after every finished launch; clear them in case an earlier
     // call on this set stopped between a launch and its completion
-    cudaError_t e = cudaMemsetAsync(ws, 0, kTicketBytes, st);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kDriverStreams && e == cudaSuccess; ++k) e = cudaMemsetAsync(slots[k], 0, kTicketBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
@@ -661,25 +687,37 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         const std::vector<uint64_t> dN = drv.next_samples();
         const int L = drv.finest_level();
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        for (int l = 0; l <= L; ++l) {
+        if ((e = cudaEventRecord(sc->fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (int k = 1; k < kDriverStreams; ++k)
+            if ((e = cudaStreamWaitEvent(streams[k], sc->fork, 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
+        int issued = 0;
+        for (int l = L; l >= 0; --l) {
             if (!dN[l]) continue;
             Plan plan;
             rc = plan_problem(l, M, dN[l], precision, model, payoff, nullptr, &plan);
             if (!rc && plan.blocks > ws_blocks) plan.blocks = ws_blocks;
             if (rc) {
-                cleanup();
+                free_scratch(sc);  // waits for the launches already queued on the set's streams
                 return rc;
             }
             LevelParams p;
             fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes,
                         precision);
             p.out = d_sums + 4 * l;
-            rc = launch_level(plan, p, ws, st);
+            const int k = issued++ % kDriverStreams;
+            rc = launch_level(plan, p, slots[k], streams[k]);
             if (rc) {
-                cleanup();
+                free_scratch(sc);  // waits for the launches already queued on the set's streams
                 return rc;
             }
             ++launches;
+        }
+        for (int k = 1; k < kDriverStreams; ++k) {
+            if ((e = cudaEventRecord(sc->join[k - 1], streams[k])) != cudaSuccess)
+                return cuda_fail(e, "cudaEventRecord");
+            if ((e = cudaStreamWaitEvent(st, sc->join[k - 1], 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
         }
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -53,10 +53,13 @@ struct TunedShape {
 bool tuned_lookup(int precision, int payoff, int M, int level, uint64_t N, TunedShape *out);
 
 // Buffers of one adaptive-driver call, pooled per device between calls: a workspace of at least
-// ws_bytes (zero ticket), device and pinned host sums (kDriverSumsPerLevel doubles per level)
-// and two timing events.  acquire_scratch takes a set from the pool or makes one;
-// release_scratch returns it; free_scratch destroys a set that met a CUDA error.
+// ws_bytes (zero tickets), device and pinned host sums (kDriverSumsPerLevel doubles per level),
+// two timing events, and kDriverStreams - 1 streams with their fork and join events, over which
+// (with the caller's stream) a round spreads its level launches.  acquire_scratch takes a set
+// from the pool or makes one; release_scratch returns it; free_scratch destroys a set that met
+// a CUDA error.
 constexpr int kDriverSumsPerLevel = 16;
+constexpr int kDriverStreams = 4;
 struct DriverScratch {
     int device = -1;
     void *ws = nullptr;
@@ -64,6 +67,8 @@ struct DriverScratch {
     double *d_sums = nullptr;
     double *h_sums = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t aux[kDriverStreams - 1] = {};
+    cudaEvent_t fork = nullptr, join[kDriverStreams - 1] = {};
 };
 int acquire_scratch(size_t ws_bytes, DriverScratch **out);
 void release_scratch(DriverScratch *s);

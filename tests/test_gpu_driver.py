@@ -105,3 +105,30 @@ def test_pooled_buffers_survive_shutdown_and_other_streams(mlmc):
     torch.cuda.synchronize()
     for x in (b, c, d):
         assert x.P == a.P and x.N == a.N
+
+
+def test_concurrent_estimates_on_two_streams(mlmc):
+    """A round's launches spread over the caller's stream and the pooled set's own streams; two
+    estimates running at once from two host threads on two streams (each with its own pooled
+    set) give exactly their sequential results."""
+    import threading
+
+    import torch
+
+    probs = [(mlmc.Problem(payoff="lookback", **GBM), 5), (mlmc.Problem(payoff="asian", **GBM), 6)]
+    ref = [mlmc.mlmc_estimate(3e-3, p, s, Lmax=6) for p, s in probs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out = [None, None]
+
+    def run(i):
+        p, s = probs[i]
+        out[i] = mlmc.mlmc_estimate(3e-3, p, s, Lmax=6, stream=streams[i])
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    for r, o in zip(ref, out):
+        assert o is not None and o.P == r.P and o.N == r.N and o.sums == r.sums
