@@ -623,18 +623,27 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
     const size_t ws_bytes = sums_workspace(ws_blocks, 8);
     const int stride = 16;  // doubles per level in the round buffer: 8 level sums + 2 mean sums
     static_assert(stride <= kDriverSumsPerLevel, "round buffer");
+    // a round's levels spread over `st` and the set's own streams as in mlmc_estimate; a level's
+    // path kernel and lattice-mean kernel share one stream and its workspace slot
+    const size_t ws_slot = (ws_bytes + 255) / 256 * 256;
     DriverScratch *sc = nullptr;
-    rc = acquire_scratch(ws_bytes, &sc);
+    rc = acquire_scratch(ws_slot * kDriverStreams, &sc);
     if (rc) return rc;
-    void *ws = sc->ws;
     double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
     cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
+    cudaStream_t streams[kDriverStreams];
+    void *slots[kDriverStreams];
+    for (int k = 0; k < kDriverStreams; ++k) {
+        streams[k] = k ? sc->aux[k - 1] : st;
+        slots[k] = (char *)sc->ws + ws_slot * k;
+    }
     auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         free_scratch(sc);
         return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     };
-    cudaError_t e = cudaMemsetAsync(ws, 0, kTicketBytes, st);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kDriverStreams && e == cudaSuccess; ++k) e = cudaMemsetAsync(slots[k], 0, kTicketBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
@@ -658,18 +667,26 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
         const std::vector<uint64_t> dN = drv.next_samples();
         const int L = drv.finest_level();
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        for (int l = 0; l <= L; ++l) {
+        if ((e = cudaEventRecord(sc->fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        for (int k = 1; k < kDriverStreams; ++k)
+            if ((e = cudaStreamWaitEvent(streams[k], sc->fork, 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
+        int issued = 0;
+        for (int l = L; l >= 0; --l) {
             if (!dN[l]) continue;
+            const int k = issued++ % kDriverStreams;
+            void *ws = slots[k];
+            const cudaStream_t sk = streams[k];
             if (uses(l)) {
                 drep[l] = mean_replicates(cv->info[l].kappa, dN[l], nrep[l]);
                 int cb = 0;
                 rc = grid_for(cv_level_kernel_for(payoff->kind), dN[l], &cb);
                 if (!rc)
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
-                                         nullptr, ws, std::min(cb, ws_blocks), st);
+                                         nullptr, ws, std::min(cb, ws_blocks), sk);
                 if (!rc)
                     rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, ws, ws_bytes,
-                                        false, st);
+                                        false, sk);
                 launches += 1 + (drep[l] + mean_replicates_per_launch(ws_bytes) - 1) / mean_replicates_per_launch(ws_bytes);
             } else {
                 Plan plan;
@@ -680,14 +697,20 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
                     fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes,
                                 MLMC_FP32_PATH);
                     p.out = d_sums + stride * l;
-                    rc = launch_level(plan, p, ws, st);
+                    rc = launch_level(plan, p, ws, sk);
                 }
                 launches += 1;
             }
             if (rc) {
-                cleanup();
+                free_scratch(sc);  // waits for the launches already queued on the set's streams
                 return rc;
             }
+        }
+        for (int k = 1; k < kDriverStreams; ++k) {
+            if ((e = cudaEventRecord(sc->join[k - 1], streams[k])) != cudaSuccess)
+                return cuda_fail(e, "cudaEventRecord");
+            if ((e = cudaStreamWaitEvent(st, sc->join[k - 1], 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
         }
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * stride * sizeof(double), cudaMemcpyDeviceToHost, st);
