@@ -16,6 +16,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "engine.h"
 #include "rng.cuh"
@@ -729,18 +730,23 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const uint64_t qa = first / 4 + ((first & 3) != 0), qb = end / 4;
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf);
     const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
-    for (uint64_t q = qa + t; q < qb; q += T) {
-        R z[4], d[4], Y[4];
-        block_increments<R, MIL, RK>(p, q, z, d);
+    // two copies of the loop, with and without per-sample output, keep the output test out of it
+    auto whole_blocks = [&](auto with_output) {
+        for (uint64_t q = qa + t; q < qb; q += T) {
+            R z[4], d[4], Y[4];
+            block_increments<R, MIL, RK>(p, q, z, d);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
-            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-            Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
-            if (y_out) y_out[q * 4 + r - first] = (double)Y[r];
+            for (int r = 0; r < 4; ++r) {
+                R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+                if constexpr (decltype(with_output)::value) y_out[q * 4 + r - first] = (double)Y[r];
+            }
+            add_moments4(Y, m, b1, b2, b3, b4, nb);
         }
-        add_moments4(Y, m, b1, b2, b3, b4, nb);
-    }
+    };
+    if (y_out) whole_blocks(std::true_type{});
+    else whole_blocks(std::false_type{});
     const uint64_t qlast = (end - 1) / 4;
     const bool first_partial = q0 < qa || q0 >= qb;
     const bool last_partial = qlast != q0 && qlast >= qb;
