@@ -575,10 +575,14 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
 {
     if constexpr (!SPLIT) {
         // one sample per thread and iteration; a sample of a level with M^l = 4 is a single
-        // Philox block and runs as straight-line code
-        if (p.nf == 4)
-            multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
-        else
+        // Philox block and runs as straight-line code, in two copies (with and without
+        // per-sample output) so that the output test leaves its loop
+        if (p.nf == 4) {
+            if (y_out)
+                multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
+            else
+                multi_range<R, MT, PAY, MIL, 1, RK, 1, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, nullptr);
+        } else
             multi_range<R, MT, PAY, MIL, 1, RK, 0, ANTI, LONG>(p, first, N, t, T, m, b1, b2, b3, b4, nb, y_out);
     } else {
         static_assert(!ANTI, "antithetic paths run one thread per sample");
