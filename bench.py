@@ -335,7 +335,8 @@ def gpu_arm(args) -> None:
     achieved = instr / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginstr/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_basis": TRAFFIC_BASIS,
-                "kernel": "level_kernel (FP32 paths, all levels of the step)",
+                "kernel": "level_kernel (FP32 paths, all levels of the step; time = the driver's events around each "
+                          "round on the engine stream, which bracket its four streams' launches)",
                 "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz (max SM clock), "
                               "one warp instruction per scheduler per clock",
                 "frac_at_run_clock": (achieved / (sms * 128 * run_mhz * 1e6 / 1e9)) if run_mhz else None,
