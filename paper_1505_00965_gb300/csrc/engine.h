@@ -56,6 +56,9 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 // running sum in two levels (partials of 256 steps).
 constexpr long kLongLaneSteps = 4096;
 const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme, bool long_lanes);
+// Milstein kernels (level_fp32_mil.cu, level_fp64_mil.cu), selected by the two above.
+const void *level_kernel_fp32_milstein(int payoff, int mt, bool split, bool long_lanes);
+const void *level_kernel_fp64_milstein(int payoff, int mt, bool split, bool long_lanes);
 // Antithetic level kernels (level_anti_fp32.cu, level_anti_fp64.cu): mt = 4 (M = 4) or 0 (M = 2).
 const void *level_anti_kernel_fp32(int payoff, int mt, int scheme, bool long_lanes);
 const void *level_anti_kernel_fp64(int payoff, int mt, int scheme, bool long_lanes);

@@ -1,10 +1,14 @@
 // level_fp32.cu -- FP32-path level kernels (FP32 normals and paths, FP64 moment sums).
 #include "level_kernel.cuh"
+#include "mlmc.h"
 
 namespace mlmcgb {
+// Euler--Maruyama kernels here; the Milstein ones in level_fp32_mil.cu (a translation unit of
+// their own, compiled in parallel).
 const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme, bool long_lanes)
 {
-    return select_level_kernel<float>(payoff, mt, split, scheme, long_lanes);
+    if (scheme == MLMC_MILSTEIN) return level_kernel_fp32_milstein(payoff, mt, split, long_lanes);
+    return select_scheme<float, false>(payoff, mt, split, long_lanes);
 }
 const void *batch_kernel_fp32(int mt)
 {

@@ -907,6 +907,7 @@ template <typename R, bool MIL> const void *select_small_kernel(int payoff)
     }
 }
 
+// mt = -1 selects the kernel of levels with M^l < 4; MIL the Milstein kernels.
 template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bool split, bool long_lanes)
 {
     if (mt < 0) return select_small_kernel<R, MIL>(payoff);
@@ -917,12 +918,6 @@ template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bo
                  : select_by_payoff<R, 0, false, MIL>(payoff, long_lanes);
 }
 
-// mt = -1 selects the kernel of levels with M^l < 4; scheme 1 is Milstein.
-template <typename R> const void *select_level_kernel(int payoff, int mt, bool split, int scheme, bool long_lanes)
-{
-    return scheme == 1 ? select_scheme<R, true>(payoff, mt, split, long_lanes)
-                       : select_scheme<R, false>(payoff, mt, split, long_lanes);
-}
 
 // Antithetic kernels: mt = 4 (M = 4) or 0 (M = 2), one thread per sample; nullptr otherwise.
 template <typename R, int MT, bool MIL> const void *select_anti_by_payoff(int payoff, bool long_lanes)
