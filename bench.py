@@ -133,8 +133,9 @@ ORACLE_SAMPLE_TEXT = ("oracle adaptive MLMC of the same two options and model at
                       "seeds 1..4, FP32 stream; estimates run in parallel processes")
 
 
-def run_oracle_sample(pool_size: int) -> tuple[float, float, int]:
-    """(path-steps, wall seconds, processes) of the bounded oracle sample."""
+def run_oracle_sample(pool_size: int) -> tuple[float, float, int, float]:
+    """(path-steps, wall seconds, processes, summed per-process seconds) of the bounded oracle
+    sample."""
     import multiprocessing as mp
 
     jobs = [(p, s, ORACLE_SAMPLE["eps"]) for p in PAYOFFS for s in ORACLE_SAMPLE["seeds"]]
@@ -144,13 +145,35 @@ def run_oracle_sample(pool_size: int) -> tuple[float, float, int]:
     with ctx.Pool(procs) as pool:
         res = pool.map(_oracle_job, jobs)
     wall = time.perf_counter() - t
-    return float(sum(r[0] for r in res)), wall, procs
+    return float(sum(r[0] for r in res)), wall, procs, float(sum(r[1] for r in res))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def cpu_baseline(pool_size: int) -> dict:
-    steps, wall, procs = run_oracle_sample(pool_size)
+    steps, wall, procs, busy = run_oracle_sample(pool_size)
     return {"value": steps / wall, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT,
-            "wall_s": round(wall, 3)}
+            "wall_s": round(wall, 3), "single_thread_value": steps / busy, "cpu_model": cpu_model(),
+            "host_cpus": os.cpu_count()}
 
 
 def reference_arm(args) -> None:
@@ -163,18 +186,20 @@ def reference_arm(args) -> None:
     pool = os.cpu_count() or 1
     for _ in range(args.warmup):
         run_oracle_sample(pool)
-    tot_steps, tot_wall, procs = 0.0, 0.0, 1
+    tot_steps, tot_wall, tot_busy, procs = 0.0, 0.0, 0.0, 1
     for _ in range(args.steps):
-        s, w, procs = run_oracle_sample(pool)
+        s, w, procs, b = run_oracle_sample(pool)
         tot_steps += s
         tot_wall += w
+        tot_busy += b
     value = tot_steps / tot_wall
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "reference_sample": ORACLE_SAMPLE_TEXT},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                             "sample": ORACLE_SAMPLE_TEXT},
+                             "sample": ORACLE_SAMPLE_TEXT, "single_thread_value": tot_steps / tot_busy,
+                             "cpu_model": cpu_model(), "host_cpus": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
