@@ -32,6 +32,8 @@ namespace mlmcgb {
 // only) sum in two levels; shorter lanes, FP64 paths (whose adds round 2^29 times finer) and the
 // other payoffs keep the single step loop, whose code the grouped one slows by 2-3 %.
 constexpr int kSumGroup = 64;
+// Samples per span of the one-thread-per-sample loop, walked with 32-bit offsets.
+constexpr uint64_t kSpan32 = uint64_t(1) << 31;
 template <typename R, int PAY> constexpr bool kBlockedSum = PAY == kAsian && sizeof(R) == 4;
 
 // Running state of one path over the steps a lane simulates.  The step loops below keep these
@@ -529,36 +531,46 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
                                             uint64_t T, double m[4], float &b1, float &b2, float &b3,
                                             float &b4, int &nb, double *y_out)
 {
-    const uint64_t warp_first = t & ~uint64_t(31);
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
     const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
-    for (uint64_t base = 0; base + warp_first < N; base += NS * T) {
-        uint64_t idx[NS], s[NS];
+    // The range in spans of at most 2^31 samples, each walked with 32-bit offsets (threads leave
+    // the loop independently: nothing in it synchronises the warp).  With 64-bit offsets and a
+    // warp-uniform exit the loop control took about 25 of the 126 instructions of a sample on
+    // levels with M^l = 4.
+    const uint32_t t32 = (uint32_t)t, T32 = (uint32_t)T;
+    for (uint64_t c0 = 0; c0 < N;) {
+        const uint32_t n = (uint32_t)(N - c0 < kSpan32 ? N - c0 : kSpan32);  // c0 + n <= N: no wrap
+        for (uint32_t i0 = t32; i0 < n; i0 += NS * T32) {
+            uint64_t s[NS];
+            bool valid[NS];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            idx[i] = base + t + i * T;
-            s[i] = first + (idx[i] < N ? idx[i] : N - 1);
-        }
-        R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
-        R aS[NS], asum[NS], ahi[NS], als[NS];
-        simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls, aS, asum,
-                                                             ahi, als);
+            for (int i = 0; i < NS; ++i) {
+                const uint32_t j = i0 + (uint32_t)i * T32;
+                valid[i] = i == 0 || j < n;
+                s[i] = first + c0 + (valid[i] ? j : i0);
+            }
+            R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
+            R aS[NS], asum[NS], ahi[NS], als[NS];
+            simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls,
+                                                                       aS, asum, ahi, als);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
-                                        R(p.nf) * logS0 + fls[i], inv_nf, p);
-            if constexpr (ANTI)
-                Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
-                                                         R(p.nf) * logS0 + als[i], inv_nf, p));
-            R Y = Pf;
-            if (!p.fine_only)
-                Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
-                                          R(p.nf / p.M) * logS0 + cls[i], inv_nc, p);
-            if (idx[i] < N) {
-                if (y_out) y_out[idx[i]] = (double)Y;
-                add_moments(Y, m, b1, b2, b3, b4, nb);
+            for (int i = 0; i < NS; ++i) {
+                R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
+                                            R(p.nf) * logS0 + fls[i], inv_nf, p);
+                if constexpr (ANTI)
+                    Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
+                                                             R(p.nf) * logS0 + als[i], inv_nf, p));
+                R Y = Pf;
+                if (!p.fine_only)
+                    Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
+                                              R(p.nf / p.M) * logS0 + cls[i], inv_nc, p);
+                if (valid[i]) {
+                    if (y_out) y_out[c0 + i0 + (uint32_t)i * T32] = (double)Y;
+                    add_moments(Y, m, b1, b2, b3, b4, nb);
+                }
             }
         }
+        c0 += n;
     }
 }
 
