@@ -243,12 +243,40 @@ static int plan_ode(int level, int M, uint64_t N, int precision, int scheme, con
     return MLMC_OK;
 }
 
+// Whether every fine and coarse step factor 1 + d of a GBM path on this level is positive for any
+// normal the stream can produce.  The uniforms are at least 2^-32 (FP64 stream) or 2^-23 (FP32),
+// so |z| <= sqrt(-2 ln 2^-32) < 6.7; the bound used is 7.  Euler--Maruyama: the fine factor is at
+// least 1 + r h - sigma sqrt(h) 7, the coarse one (M fine increments summed) at least
+// 1 + r M h - sigma M sqrt(h) 7.  Milstein: the factor is a quadratic in w = sigma sqrt(h) z whose
+// least value over all w is 1/2 + r h - sigma^2 h / 2, and the same with M h for the coarse step.
+bool positive_step_factors(const mlmc_model *m, int level, int M)
+{
+    constexpr double kNormalBound = 7.0, kMargin = 1e-2;
+    const double h = m->T / (double)ipow(M, level), H = M * h;
+    if (m->scheme == MLMC_MILSTEIN)
+        return 0.5 + m->r * h - 0.5 * m->sigma * m->sigma * h > kMargin &&
+               0.5 + m->r * H - 0.5 * m->sigma * m->sigma * H > kMargin;
+    return 1.0 + m->r * h - m->sigma * std::sqrt(h) * kNormalBound > kMargin &&
+           1.0 + m->r * H - m->sigma * M * std::sqrt(h) * kNormalBound > kMargin;
+}
+
 int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *model, const mlmc_payoff *payoff,
                  const mlmc_launch *launch, Plan *plan)
 {
     if (model->kind == MLMC_MODEL_QUINTIC_ODE) return plan_ode(level, M, N, precision, model->scheme, launch, plan);
-    if (payoff->estimator != MLMC_ANTITHETIC)
-        return plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, plan);
+    if (payoff->estimator != MLMC_ANTITHETIC) {
+        const int rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, launch, plan);
+        if (rc) return rc;
+        // split lookback paths whose chunks all start above zero keep no running minimum
+        if (plan->lanes > 1 && payoff->kind == kLookback && positive_step_factors(model, level, M)) {
+            const int mt = M == 4 ? 4 : 0;
+            const void *k = precision == MLMC_FP32_PATH
+                                ? level_kernel_fp32(payoff->kind, mt, true, model->scheme, false, true)
+                                : level_kernel_fp64(payoff->kind, mt, true, model->scheme, false, true);
+            if (k) plan->kernel = k;
+        }
+        return MLMC_OK;
+    }
     // antithetic: one thread per sample; the kernel of levels with M^l < 4 reads the flag
     if (M != 2 && M != 4) return fail(MLMC_ENOTIMPL, "the antithetic estimator is built for M = 2 and 4 (M = %d)", M);
     if (launch && launch->lanes_per_path > 1)

@@ -53,18 +53,20 @@ inline size_t workspace_bytes_for_blocks(int blocks)
 // Kernel selection.  `mt` is 4 for the M = 4 specialisation, 0 for the generic-M kernel and
 // -1 for the kernel of levels with M^l < 4.  `long_lanes`: a lane runs more than kLongLaneSteps
 // fine steps of its path (M^l / lanes), for which the FP32 arithmetic-Asian kernels add the
-// running sum in two levels (partials of 256 steps).
+// running sum in two levels (partials of 256 steps).  `positive`: every fine and coarse step
+// factor 1 + d is positive for any normal the stream can produce, so the split lookback kernels
+// keep no running minimum (no chunk of a path starts below zero).
 constexpr long kLongLaneSteps = 4096;
-const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme, bool long_lanes);
+const void *level_kernel_fp32(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive = false);
 // Milstein kernels (level_fp32_mil.cu, level_fp64_mil.cu), selected by the two above.
-const void *level_kernel_fp32_milstein(int payoff, int mt, bool split, bool long_lanes);
-const void *level_kernel_fp64_milstein(int payoff, int mt, bool split, bool long_lanes);
+const void *level_kernel_fp32_milstein(int payoff, int mt, bool split, bool long_lanes, bool positive);
+const void *level_kernel_fp64_milstein(int payoff, int mt, bool split, bool long_lanes, bool positive);
 // Antithetic level kernels (level_anti_fp32.cu, level_anti_fp64.cu): mt = 4 (M = 4) or 0 (M = 2).
 const void *level_anti_kernel_fp32(int payoff, int mt, int scheme, bool long_lanes);
 const void *level_anti_kernel_fp64(int payoff, int mt, int scheme, bool long_lanes);
 // Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
 const void *ode_level_kernel(int precision, int scheme);
-const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes);
+const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive = false);
 
 // Batched rounds: one chunk of samples of one task (a level of one problem).
 struct BatchChunk {

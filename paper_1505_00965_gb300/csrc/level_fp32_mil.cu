@@ -3,8 +3,8 @@
 #include "level_kernel.cuh"
 
 namespace mlmcgb {
-const void *level_kernel_fp32_milstein(int payoff, int mt, bool split, bool long_lanes)
+const void *level_kernel_fp32_milstein(int payoff, int mt, bool split, bool long_lanes, bool positive)
 {
-    return select_scheme<float, true>(payoff, mt, split, long_lanes);
+    return select_scheme<float, true>(payoff, mt, split, long_lanes, positive);
 }
 }  // namespace mlmcgb

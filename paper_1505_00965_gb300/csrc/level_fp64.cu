@@ -5,10 +5,10 @@
 namespace mlmcgb {
 // Euler--Maruyama kernels here; the Milstein ones in level_fp64_mil.cu (a translation unit of
 // their own, compiled in parallel).
-const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes)
+const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive)
 {
-    if (scheme == MLMC_MILSTEIN) return level_kernel_fp64_milstein(payoff, mt, split, long_lanes);
-    return select_scheme<double, false>(payoff, mt, split, long_lanes);
+    if (scheme == MLMC_MILSTEIN) return level_kernel_fp64_milstein(payoff, mt, split, long_lanes, positive);
+    return select_scheme<double, false>(payoff, mt, split, long_lanes, positive);
 }
 const void *batch_kernel_fp64(int mt)
 {

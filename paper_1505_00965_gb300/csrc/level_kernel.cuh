@@ -118,7 +118,7 @@ __device__ __forceinline__ uint4 philox_of(const LevelParams &p, uint4 c)
 // coarse factor's d is the sum of the M fine ones.  Milstein (MIL): d = r h + sigma dW
 // + sigma^2 (dW^2 - h) / 2 = (r h - c2) + a z + c2 z^2 with a = sigma sqrt(h), c2 = sigma^2 h / 2,
 // and the coarse step the same formula on the summed increment with step M h.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false, bool POS = false>
 __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t slo, uint32_t shi,
                                                int j0, int j1, PathAcc<R, PAY, SPLIT> &fa,
                                                PathAcc<R, PAY, SPLIT> &ca)
@@ -174,7 +174,7 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
                 dk = d[k];
                 dc += dk;
             }
-            em_step<R, PAY, SPLIT>(fS, fsum, fhi, flo, fls, dk);
+            em_step<R, PAY, SPLIT && !POS>(fS, fsum, fhi, flo, fls, dk);
             bool coarse_now;
             if constexpr (MT != 0) {
                 coarse_now = (k + 1) % MT == 0;
@@ -186,7 +186,7 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
                 R dcs;
                 if constexpr (MIL) dcs = fma(fma(c2, dc, a), dc, rHm);
                 else dcs = dc;
-                em_step<R, PAY, SPLIT>(cS, csum, chi, clo, cls, dcs);
+                em_step<R, PAY, SPLIT && !POS>(cS, csum, chi, clo, cls, dcs);
                 dc = R(0);
             }
         }
@@ -454,7 +454,7 @@ __device__ __forceinline__ void add_moments4(const double Y[4], double m[4], flo
 // Join the chunks of one sample split over P lanes: an exclusive product scan of the chunk
 // factors gives each chunk's starting value relative to S0; the path totals are then sums and
 // maxima over the lanes.  Every lane of the group receives the totals.
-template <typename R, int PAY>
+template <typename R, int PAY, bool POS = false>
 __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int lig, int P, R S0,
                                             R steps, R &total, R &post, R &hi, R &lpost)
 {
@@ -471,7 +471,7 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
     total = S0 * __shfl_sync(0xffffffffu, incl, P - 1, P);
     const R start = S0 * excl;
     R ps = start * A.sum;
-    R ph = start >= R(0) ? start * A.hi : start * A.lo;
+    R ph = (POS || start >= R(0)) ? start * A.hi : start * A.lo;  // POS: every start is positive
     R pl = R(0);
     if constexpr (PAY == kGeoAsian) pl = steps * PathAcc<R, PAY, true>::log_r(start) + A.lsum;
 #pragma unroll
@@ -489,7 +489,7 @@ __device__ __forceinline__ void join_chunks(const PathAcc<R, PAY, true> &A, int 
 
 // Y of sample s on a level with M^l >= 4, computed by the P lanes of one group (lane lig);
 // every lane of the group returns the same Y.
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false>
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool LONG = false, bool POS = false>
 __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig, int P)
 {
     const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
@@ -511,11 +511,11 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
-        simulate_steps<R, MT, PAY, true, MIL, RK, LONG>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
+        simulate_steps<R, MT, PAY, true, MIL, RK, LONG, POS>(p, slo, shi, lig * calls, (lig + 1) * calls, fa, ca);
         const R steps_f = R(4 * calls);
         R tf, pf, hf, lf, tc, pc, hc, lc;
-        join_chunks<R, PAY>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
-        join_chunks<R, PAY>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
+        join_chunks<R, PAY, POS>(fa, lig, P, S0, steps_f, tf, pf, hf, lf);
+        join_chunks<R, PAY, POS>(ca, lig, P, S0, steps_f / R(p.M), tc, pc, hc, lc);
         const R Pf = payoff_value<R, PAY>(tf, pf, hf, lf, inv_nf, p);
         if (p.fine_only) return Pf;
         const R Pc = payoff_value<R, PAY>(tc, pc, hc, lc, inv_nc, p);
@@ -579,7 +579,7 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
 // Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
 // sample first + i into y_out[i] when y_out is not NULL.
 template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool ANTI = false,
-          bool LONG = false>
+          bool LONG = false, bool POS = false>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
                                               uint64_t t, uint64_t T, double m[4], float &b1,
                                               float &b2, float &b3, float &b4, int &nb,
@@ -607,7 +607,7 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
             const uint64_t idx = base + g;
             const bool valid = idx < N;
             const uint64_t s = first + (valid ? idx : N - 1);
-            const R Y = sample_Y<R, MT, PAY, true, MIL, RK, LONG>(p, s, lig, P);
+            const R Y = sample_Y<R, MT, PAY, true, MIL, RK, LONG, POS>(p, s, lig, P);
             if (valid && lig == 0) {
                 if (y_out) y_out[idx] = (double)Y;
                 add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -784,14 +784,16 @@ __device__ __forceinline__ void fold_batch(double m[4], float b1, float b2, floa
 
 // One level, one thread (or P lanes) per sample, grid-stride over the samples; ANTI: the
 // antithetic estimator Y = (P_f + P_f^a) / 2 - P_c (one thread per sample); LONG: lanes of more
-// than kLongLaneSteps steps (two-level Asian sums).
-template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool ANTI = false, bool LONG = false>
+// than kLongLaneSteps steps (two-level Asian sums); POS: split paths whose step factors 1 + d are
+// all positive (the host checks the bound of the normals), so that no chunk starts below zero
+// and the lookback lanes keep no running minimum.
+template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool ANTI = false, bool LONG = false, bool POS = false>
 __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
 {
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;  // FP32-path batch sums
     int nb = 0;
-    regular_range<R, MT, PAY, SPLIT, MIL, true, ANTI, LONG>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+    regular_range<R, MT, PAY, SPLIT, MIL, true, ANTI, LONG, POS>(p, p.first, p.N, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                      (uint64_t)gridDim.x * blockDim.x, m, b1, b2, b3, b4, nb, p.y_out);
     fold_batch<R>(m, b1, b2, b3, b4);
     finish_sums(m, p);
@@ -893,8 +895,12 @@ template <typename R, int MT, bool SPLIT, bool MIL, bool ANTI> const void *asian
 
 // Kernel for (payoff, M specialisation, split, scheme, lane length) at precision R; nullptr for
 // an unknown payoff.
-template <typename R, int MT, bool SPLIT, bool MIL> const void *select_by_payoff(int payoff, bool long_lanes)
+template <typename R, int MT, bool SPLIT, bool MIL>
+const void *select_by_payoff(int payoff, bool long_lanes, bool positive = false)
 {
+    if constexpr (SPLIT) {
+        if (payoff == kLookback && positive) return (const void *)level_kernel<R, MT, kLookback, true, MIL, false, false, true>;
+    }
     switch (payoff) {
     case kEuropean: return (const void *)level_kernel<R, MT, kEuropean, SPLIT, MIL>;
     case kAsian: return asian_kernel<R, MT, SPLIT, MIL, false>(long_lanes);
@@ -920,13 +926,14 @@ template <typename R, bool MIL> const void *select_small_kernel(int payoff)
 }
 
 // mt = -1 selects the kernel of levels with M^l < 4; MIL the Milstein kernels.
-template <typename R, bool MIL> const void *select_scheme(int payoff, int mt, bool split, bool long_lanes)
+template <typename R, bool MIL>
+const void *select_scheme(int payoff, int mt, bool split, bool long_lanes, bool positive = false)
 {
     if (mt < 0) return select_small_kernel<R, MIL>(payoff);
     if (mt == 4)
-        return split ? select_by_payoff<R, 4, true, MIL>(payoff, long_lanes)
+        return split ? select_by_payoff<R, 4, true, MIL>(payoff, long_lanes, positive)
                      : select_by_payoff<R, 4, false, MIL>(payoff, long_lanes);
-    return split ? select_by_payoff<R, 0, true, MIL>(payoff, long_lanes)
+    return split ? select_by_payoff<R, 0, true, MIL>(payoff, long_lanes, positive)
                  : select_by_payoff<R, 0, false, MIL>(payoff, long_lanes);
 }
 

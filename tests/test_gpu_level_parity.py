@@ -261,3 +261,26 @@ def test_level0_ranges_inside_one_philox_block(mlmc, precision):
         yo = oracle.level_samples(0, 4, N, op, seed=13, first=first, stream=precision)
         assert np.max(np.abs(y - yo)) <= _bound(precision, 0, 4, p), (first, N)
         np.testing.assert_allclose(sums[0], y.sum(), rtol=1e-6)
+
+
+@pytest.mark.parametrize("lanes", [2, 8])
+def test_split_lookback_with_sign_changes(mlmc, lanes):
+    """sigma sqrt(h) = 0.5 (sigma = 4, level 3): a step factor 1 + d is negative whenever the
+    normal is below -2, so paths change sign and chunks of split paths start below zero.  The
+    kernel that keeps each chunk's running minimum must be the one chosen: the maximum of a chunk
+    that starts negative is its start times the chunk's relative minimum.  FP64 paths (near-zero
+    factors amplify FP32 rounding beyond the per-sample bound)."""
+    p = mlmc.Problem(payoff="lookback", S0=100.0, r=0.05, sigma=4.0, T=1.0, K=100.0, cash=1.0)
+    op = oracle_problem(oracle, p)
+    level, M, N, seed = 3, 4, 2001, 8
+    _, y = run_level(mlmc, level, M, N, 0, p, seed, "fp64", launch={"lanes_per_path": lanes})
+    yo = oracle.level_samples(level, M, N, op, seed=seed, stream="fp64")
+    flips = 0
+    for s in range(200):
+        _, fine, _ = oracle.sample_paths(level, M, s, op, seed=seed, stream="fp64")
+        flips += int(np.any(fine < 0))
+    assert flips > 20, flips  # the regime is the one described
+    # Y is a difference of fine and coarse payoffs that reach 1e5: the bound scales with them
+    fine = oracle.level_samples(level, M, N, op, seed=seed, stream="fp64", mode=oracle.MODE_FINE_ONLY)
+    scale = 1.0 + np.abs(fine) + np.abs(fine - yo)
+    assert np.max(np.abs(y - yo) / scale) <= 1e-9
