@@ -523,8 +523,8 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     }
 }
 
-// One thread per sample, NS samples per thread and iteration (idx, idx + T, ...), over the
-// samples [first, first + N) (the arguments as for regular_range below).
+// One thread per sample, NS samples per thread and iteration (i, i + T, ...) of each span, over
+// the samples [first, first + N) (the arguments as for regular_range below).
 template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false,
           bool LONG = false>
 __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
@@ -575,9 +575,10 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
 }
 
 // Samples [first, first + N) of a level with M^l >= 4, shared by T threads of which this is
-// thread t (T a multiple of 32; t and T count whole warps, so loop exits are warp uniform).
-// Groups of P = p.lanes lanes take one sample each; moments go into m / b1..b4 / nb, and Y of
-// sample first + i into y_out[i] when y_out is not NULL.
+// thread t (T a multiple of 32).  Whole paths: one thread per sample (multi_range).  Split paths:
+// groups of P = p.lanes lanes take one sample each, and since the lanes of a group join by
+// shuffles, t and T count whole warps and the loop exits are warp uniform.  Moments go into
+// m / b1..b4 / nb, and Y of sample first + i into y_out[i] when y_out is not NULL.
 template <typename R, int MT, int PAY, bool SPLIT, bool MIL, bool RK = true, bool ANTI = false,
           bool LONG = false, bool POS = false>
 __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t first, uint64_t N,
