@@ -250,7 +250,10 @@ typedef struct mlmc_result {
  *   formulas are floored at half the extrapolation from the level below.
  *   eps > 0; M in {2, 4, 8}; 1 <= Lmin <= Lmax < MLMC_MAX_LEVELS, M^Lmax <= 2^24; N0 >= 2.
  *   model, payoff  host, read only.  out  host, written on success and on MLMC_ENOTCONV.
- *   stream  void* cudaStream_t (NULL = default); synchronised before return.
+ *   stream  void* cudaStream_t (NULL = default); synchronised before return.  A round's level
+ *           launches run on `stream` and on three streams of the library's own, which wait for
+ *           the work queued on `stream` before the round and which `stream` waits for after it;
+ *           results do not depend on how the launches overlap.
  * Errors: MLMC_EINVAL, MLMC_ECUDA, MLMC_ENOMEM; MLMC_ENOTCONV when Lmax is reached first
  * (out then holds the estimate at L = Lmax); MLMC_ENONFINITE when a round's level sums are
  * not finite (explicit Euler--Maruyama on QUINTIC_ODE, Sec. 5), out left untouched.
