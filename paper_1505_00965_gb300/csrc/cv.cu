@@ -623,8 +623,8 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
     const size_t ws_bytes = sums_workspace(ws_blocks, 8);
     const int stride = 16;  // doubles per level in the round buffer: 8 level sums + 2 mean sums
     static_assert(stride <= kDriverSumsPerLevel, "round buffer");
-    // a round's levels spread over `st` and the set's own streams as in mlmc_estimate; a level's
-    // path kernel and lattice-mean kernel share one stream and its workspace slot
+    // a round's launches spread over `st` and the set's own streams as in mlmc_estimate; a
+    // control-variate level's path kernel and lattice-mean kernel take one turn each
     const size_t ws_slot = (ws_bytes + 255) / 256 * 256;
     DriverScratch *sc = nullptr;
     rc = acquire_scratch(ws_slot * kDriverStreams, &sc);
@@ -684,9 +684,11 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
                 if (!rc)
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
                                          nullptr, ws, std::min(cb, ws_blocks), sk);
+                // the lattice mean is independent of the path kernel: the next stream and its slot
+                const int km = issued++ % kDriverStreams;
                 if (!rc)
-                    rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, ws, ws_bytes,
-                                        false, sk);
+                    rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, slots[km],
+                                        ws_bytes, false, streams[km]);
                 launches += 1 + (drep[l] + mean_replicates_per_launch(ws_bytes) - 1) / mean_replicates_per_launch(ws_bytes);
             } else {
                 Plan plan;
