@@ -263,14 +263,16 @@ def test_level0_ranges_inside_one_philox_block(mlmc, precision):
         np.testing.assert_allclose(sums[0], y.sum(), rtol=1e-6)
 
 
+@pytest.mark.parametrize("scheme,sigma", [("em", 4.0), ("milstein", 10.0)])
 @pytest.mark.parametrize("lanes", [2, 8])
-def test_split_lookback_with_sign_changes(mlmc, lanes):
-    """sigma sqrt(h) = 0.5 (sigma = 4, level 3): a step factor 1 + d is negative whenever the
-    normal is below -2, so paths change sign and chunks of split paths start below zero.  The
-    kernel that keeps each chunk's running minimum must be the one chosen: the maximum of a chunk
-    that starts negative is its start times the chunk's relative minimum.  FP64 paths (near-zero
-    factors amplify FP32 rounding beyond the per-sample bound)."""
-    p = mlmc.Problem(payoff="lookback", S0=100.0, r=0.05, sigma=4.0, T=1.0, K=100.0, cash=1.0)
+def test_split_lookback_with_sign_changes(mlmc, lanes, scheme, sigma):
+    """Level 3 (h = 1/64).  Euler--Maruyama with sigma = 4: a step factor 1 + d is negative
+    whenever the normal is below -2.  Milstein with sigma = 10: the factor's least value
+    1/2 + r h - sigma^2 h / 2 is below zero.  Paths change sign and chunks of split paths start
+    below zero, so the kernel that keeps each chunk's running minimum must be the one chosen: the
+    maximum of a chunk that starts negative is its start times the chunk's relative minimum.
+    FP64 paths (near-zero factors amplify FP32 rounding beyond the per-sample bound)."""
+    p = mlmc.Problem(payoff="lookback", scheme=scheme, S0=100.0, r=0.05, sigma=sigma, T=1.0, K=100.0, cash=1.0)
     op = oracle_problem(oracle, p)
     level, M, N, seed = 3, 4, 2001, 8
     _, y = run_level(mlmc, level, M, N, 0, p, seed, "fp64", launch={"lanes_per_path": lanes})
