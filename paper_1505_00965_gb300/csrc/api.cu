@@ -689,12 +689,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (rc) return rc;
     double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
     cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
-    cudaStream_t streams[kDriverStreams];
-    void *slots[kDriverStreams];
-    for (int k = 0; k < kDriverStreams; ++k) {
-        streams[k] = k ? sc->aux[k - 1] : st;
-        slots[k] = (char *)sc->ws + ws_slot * k;
-    }
+    RoundStreams rs(sc, st, ws_slot);
     auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         free_scratch(sc);
@@ -702,8 +697,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     };
     // the completion tickets are zero after every finished launch; clear them in case an earlier
     // call on this set stopped between a launch and its completion
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kDriverStreams && e == cudaSuccess; ++k) e = cudaMemsetAsync(slots[k], 0, kTicketBytes, st);
+    cudaError_t e = rs.clear_tickets(kTicketBytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
@@ -715,11 +709,7 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
         const std::vector<uint64_t> dN = drv.next_samples();
         const int L = drv.finest_level();
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        if ((e = cudaEventRecord(sc->fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        for (int k = 1; k < kDriverStreams; ++k)
-            if ((e = cudaStreamWaitEvent(streams[k], sc->fork, 0)) != cudaSuccess)
-                return cuda_fail(e, "cudaStreamWaitEvent");
-        int issued = 0;
+        if ((e = rs.fork(sc)) != cudaSuccess) return cuda_fail(e, "fork of the round's streams");
         for (int l = L; l >= 0; --l) {
             if (!dN[l]) continue;
             Plan plan;
@@ -733,20 +723,15 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
             fill_params(p, l, M, dN[l], drv.samples_taken(l), model, payoff, seed, MLMC_TAG_PATHS, plan.lanes,
                         precision);
             p.out = d_sums + 4 * l;
-            const int k = issued++ % kDriverStreams;
-            rc = launch_level(plan, p, slots[k], streams[k]);
+            const int k = rs.take();
+            rc = launch_level(plan, p, rs.slot[k], rs.stream[k]);
             if (rc) {
                 free_scratch(sc);  // waits for the launches already queued on the set's streams
                 return rc;
             }
             ++launches;
         }
-        for (int k = 1; k < kDriverStreams; ++k) {
-            if ((e = cudaEventRecord(sc->join[k - 1], streams[k])) != cudaSuccess)
-                return cuda_fail(e, "cudaEventRecord");
-            if ((e = cudaStreamWaitEvent(st, sc->join[k - 1], 0)) != cudaSuccess)
-                return cuda_fail(e, "cudaStreamWaitEvent");
-        }
+        if ((e = rs.join(sc)) != cudaSuccess) return cuda_fail(e, "join of the round's streams");
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
         d2h_bytes += (L + 1) * 4 * sizeof(double);

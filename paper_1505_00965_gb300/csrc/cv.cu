@@ -631,19 +631,13 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
     if (rc) return rc;
     double *d_sums = sc->d_sums, *h_sums = sc->h_sums;
     cudaEvent_t ev0 = sc->ev0, ev1 = sc->ev1;
-    cudaStream_t streams[kDriverStreams];
-    void *slots[kDriverStreams];
-    for (int k = 0; k < kDriverStreams; ++k) {
-        streams[k] = k ? sc->aux[k - 1] : st;
-        slots[k] = (char *)sc->ws + ws_slot * k;
-    }
+    RoundStreams rs(sc, st, ws_slot);
     auto cleanup = [&]() { release_scratch(sc); };
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         free_scratch(sc);
         return fail(MLMC_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     };
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kDriverStreams && e == cudaSuccess; ++k) e = cudaMemsetAsync(slots[k], 0, kTicketBytes, st);
+    cudaError_t e = rs.clear_tickets(kTicketBytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     AdaptiveMLMC drv(eps, M, Lmin, Lmax, N0);
@@ -667,16 +661,12 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
         const std::vector<uint64_t> dN = drv.next_samples();
         const int L = drv.finest_level();
         if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        if ((e = cudaEventRecord(sc->fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        for (int k = 1; k < kDriverStreams; ++k)
-            if ((e = cudaStreamWaitEvent(streams[k], sc->fork, 0)) != cudaSuccess)
-                return cuda_fail(e, "cudaStreamWaitEvent");
-        int issued = 0;
+        if ((e = rs.fork(sc)) != cudaSuccess) return cuda_fail(e, "fork of the round's streams");
         for (int l = L; l >= 0; --l) {
             if (!dN[l]) continue;
-            const int k = issued++ % kDriverStreams;
-            void *ws = slots[k];
-            const cudaStream_t sk = streams[k];
+            const int k = rs.take();
+            void *ws = rs.slot[k];
+            const cudaStream_t sk = rs.stream[k];
             if (uses(l)) {
                 drep[l] = mean_replicates(cv->info[l].kappa, dN[l], nrep[l]);
                 int cb = 0;
@@ -685,10 +675,10 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
                                          nullptr, ws, std::min(cb, ws_blocks), sk);
                 // the lattice mean is independent of the path kernel: the next stream and its slot
-                const int km = issued++ % kDriverStreams;
+                const int km = rs.take();
                 if (!rc)
-                    rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, slots[km],
-                                        ws_bytes, false, streams[km]);
+                    rc = launch_cv_mean(cv, l, drep[l], nrep[l], seed, d_sums + stride * l + 8, nullptr, rs.slot[km],
+                                        ws_bytes, false, rs.stream[km]);
                 launches += 1 + (drep[l] + mean_replicates_per_launch(ws_bytes) - 1) / mean_replicates_per_launch(ws_bytes);
             } else {
                 Plan plan;
@@ -708,12 +698,7 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
                 return rc;
             }
         }
-        for (int k = 1; k < kDriverStreams; ++k) {
-            if ((e = cudaEventRecord(sc->join[k - 1], streams[k])) != cudaSuccess)
-                return cuda_fail(e, "cudaEventRecord");
-            if ((e = cudaStreamWaitEvent(st, sc->join[k - 1], 0)) != cudaSuccess)
-                return cuda_fail(e, "cudaStreamWaitEvent");
-        }
+        if ((e = rs.join(sc)) != cudaSuccess) return cuda_fail(e, "join of the round's streams");
         if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         e = cudaMemcpyAsync(h_sums, d_sums, (L + 1) * stride * sizeof(double), cudaMemcpyDeviceToHost, st);
         d2h_bytes += (L + 1) * stride * sizeof(double);

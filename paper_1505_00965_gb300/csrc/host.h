@@ -74,4 +74,47 @@ int acquire_scratch(size_t ws_bytes, DriverScratch **out);
 void release_scratch(DriverScratch *s);
 void free_scratch(DriverScratch *s);
 
+// The streams of one driver call and their workspace slots: slot k (slot_bytes from the set's
+// workspace, which holds kDriverStreams of them) belongs to stream k, the caller's stream for
+// k = 0 and the set's own streams after it, so launches that share a slot are ordered.  A round
+// forks the set's streams from the caller's stream, takes streams in turn, and joins them back.
+struct RoundStreams {
+    cudaStream_t stream[kDriverStreams];
+    void *slot[kDriverStreams];
+    int next = 0;
+
+    RoundStreams(const DriverScratch *sc, cudaStream_t st, size_t slot_bytes)
+    {
+        for (int k = 0; k < kDriverStreams; ++k) {
+            stream[k] = k ? sc->aux[k - 1] : st;
+            slot[k] = (char *)sc->ws + slot_bytes * k;
+        }
+    }
+    // zero every slot's completion ticket (in the caller's stream's order)
+    cudaError_t clear_tickets(size_t ticket_bytes) const
+    {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kDriverStreams && e == cudaSuccess; ++k)
+            e = cudaMemsetAsync(slot[k], 0, ticket_bytes, stream[0]);
+        return e;
+    }
+    cudaError_t fork(const DriverScratch *sc)
+    {
+        next = 0;
+        cudaError_t e = cudaEventRecord(sc->fork, stream[0]);
+        for (int k = 1; k < kDriverStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(stream[k], sc->fork, 0);
+        return e;
+    }
+    int take() { return next++ % kDriverStreams; }
+    cudaError_t join(const DriverScratch *sc)
+    {
+        cudaError_t e = cudaSuccess;
+        for (int k = 1; k < kDriverStreams && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(sc->join[k - 1], stream[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(stream[0], sc->join[k - 1], 0);
+        }
+        return e;
+    }
+};
+
 }  // namespace mlmcgb
