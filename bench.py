@@ -414,6 +414,65 @@ def gpu_arm(args) -> None:
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ one kernel on fixed arguments
+
+def case_arm(args) -> None:
+    """Launch one level kernel (or the control variate's lattice-mean kernel) on fixed
+    arguments a few times and print its CUDA-event time per launch: the command that profiler
+    captures of a single kernel run.  Not a benchmark line."""
+    import torch
+
+    from paper_1505_00965_gb300 import mlmc
+
+    c = dict(kv.split("=", 1) for kv in args.case.split(",") if kv)
+    level, m, n = int(c.get("level", 6)), int(c.get("M", 4)), int(float(c.get("N", 1e6)))
+    reps, warm = int(c.get("reps", 3)), int(c.get("warmup", 1))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if "cv_mean" in c:
+        import numpy as np
+
+        R = int(c["cv_mean"])
+        cv = mlmc.mlmc_cv_create(4, mlmc.Problem(payoff="asian"))
+        theta = (np.random.default_rng(1).standard_normal(mlmc.MLMC_CV_PARAMS) * 0.2).astype(np.float32)
+        mlmc.mlmc_cv_set_params(cv, 0, theta)
+        d = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for _ in range(warm):
+            mlmc.mlmc_cv_mean_sums(cv, 0, R, 0, 1, d, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            mlmc.mlmc_cv_mean_sums(cv, 0, R, 0, 1, d, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(reps, 1)
+        print(f"cv mean sample: {R} replicates, {ms:.4f} ms per launch, "
+              f"{ms * 1e6 / (R * mlmc.MLMC_CV_LATTICE_POINTS):.4f} ns per lattice point")
+        mlmc.mlmc_cv_free(cv)
+        return
+    prob = mlmc.Problem(payoff=c.get("payoff", "asian"), kind=c.get("kind", "gbm"), scheme=c.get("scheme", "em"))
+    launch = {k: int(c[k]) for k in ("lanes_per_path", "threads_per_block", "blocks", "samples_per_thread") if k in c}
+    precision = c.get("precision", "fp32")
+    ws_bytes = mlmc.mlmc_level_workspace_bytes(level, m, n, precision, launch)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
+    d_sums = torch.zeros(4, dtype=torch.float64, device="cuda")
+
+    def once():
+        mlmc.mlmc_level_sums_async(level, m, n, 0, prob, 1, d_sums, ws, ws_bytes, precision=precision,
+                                   launch=launch, stream=stream)
+
+    for _ in range(warm):
+        once()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(reps, 1)
+    print(f"case {args.case}: {ms:.4f} ms/launch, {n * m ** level / ms / 1e9:.4g} T coupled steps/s, "
+          f"sums={d_sums.tolist()}")
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,7 +481,14 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and control-variate reports")
+    ap.add_argument("--case", default="", metavar="K=V,...",
+                    help="time one kernel instead: level, M, N, payoff, kind, scheme, precision, "
+                         "lanes_per_path, threads_per_block, blocks, samples_per_thread, reps, warmup; "
+                         "or cv_mean=R (the lattice-mean kernel over R replicates)")
     args = ap.parse_args(argv)
+    if args.case:
+        case_arm(args)
+        return
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -117,7 +117,7 @@ typedef enum mlmc_precision {
 enum { MLMC_TAG_PATHS = 0, MLMC_TAG_CV_MEAN = 1, MLMC_TAG_CV_TRAIN = 2 };
 
 /* Launch shape of one level kernel.  Zero in a field means "choose automatically".
- *   threads_per_block  multiple of 32, 32..1024
+ *   threads_per_block  multiple of 32, 32..1024 (at most 512 with samples_per_thread = 2)
  *   lanes_per_path     1 (one thread per sample) or a power of two up to 32: that many lanes of
  *                      one warp split the time steps of one sample into equal chunks and join
  *                      them by a product scan (GBM's step is multiplicative); requires
@@ -128,7 +128,12 @@ typedef struct mlmc_launch {
     int32_t threads_per_block;
     int32_t lanes_per_path;
     int32_t blocks;
-    int32_t reserved;      /* must be 0 */
+    int32_t samples_per_thread;  /* 1 or 2 (0 = automatic): with 2, each thread of a one-thread-
+                              per-sample launch steps two samples' paths in lockstep (two
+                              independent Philox and step chains for the scheduler to interleave);
+                              FP32 Euler--Maruyama paths of the coupled or single-level estimator
+                              with M^l >= 4 and lanes_per_path = 1 only.  The samples and their Y
+                              are the same; the FP32 moment sums add them in another order. */
 } mlmc_launch;
 
 /* Message describing the last failure on this host thread ("" if none). */
@@ -352,15 +357,37 @@ typedef struct mlmc_cv_level_info {
                               (var_g / var_lattice is the lattice rule's gain over plain sampling) */
 } mlmc_cv_level_info;
 
+/* Where the time of one mlmc_cv_train call went (host clock, milliseconds) and how it trained. */
+typedef struct mlmc_cv_train_stats {
+    double data_ms;        /* training data of every level, target standardisation, initial weights */
+    double train_ms;       /* the training launch (host clock, launch to completion) */
+    double train_kernel_ms;/* the same launch timed by CUDA events on the training stream */
+    double eval_ms;        /* held-out variance ratios */
+    double cost_ms;        /* timed kernel costs and the lattice statistics of every level */
+    double total_ms;       /* the whole call */
+    int64_t steps;         /* Adam steps per network (epochs x batches per epoch) */
+    int32_t cluster;       /* CTAs per thread-block cluster: one cluster trains one level's network */
+    int32_t levels;        /* networks trained side by side in the one launch */
+} mlmc_cv_train_stats;
+
 /* Create a control variate for one problem with no trained level (every level plain).
  * M as mlmc_estimate; model, payoff host, read only.  *out receives the handle. */
 int mlmc_cv_create(int M, const mlmc_model *model, const mlmc_payoff *payoff, mlmc_cv **out);
 
 /* Train networks for levels 0 .. opts->levels - 1 (opts NULL = defaults) on samples drawn under
  * tag MLMC_TAG_CV_TRAIN with `seed`, then measure each level's variance ratio and kernel costs
- * and decide which levels use it.  Synchronises `stream`.  *out receives the handle. */
+ * and decide which levels use it.  Synchronises `stream`.  *out receives the handle.
+ * Training minimises the mean squared error of g against the standardised Y with Adam
+ * (beta1 0.9, beta2 0.999, 1e-8) over mini-batches taken in order, `epochs` passes over the
+ * first nine tenths of the samples; all levels train at once in one launch (one thread-block
+ * cluster of 16 CTAs per level where the GPU can place it, else 8), forward, backward, gradient
+ * and update of every step inside it.  MLMC_ECUDA if no cluster of 8 fits. */
 int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uint64_t seed,
                   const mlmc_cv_options *opts, void *stream, mlmc_cv **out);
+
+/* Timings and shape of the mlmc_cv_train call that made `cv` (zeros for a handle from
+ * mlmc_cv_create).  The paper has no counterpart (cost accounting of the learned part). */
+int mlmc_cv_train_info(const mlmc_cv *cv, mlmc_cv_train_stats *out);
 
 /* Release a handle (NULL is ignored). */
 int mlmc_cv_free(mlmc_cv *cv);
@@ -393,7 +420,8 @@ int mlmc_cv_training_data(const mlmc_cv *cv, int level, uint64_t N, uint64_t fir
 
 /* The network on given inputs: params host [MLMC_CV_PARAMS]; d_X device [N][8]; d_G device [N].
  * mlmc_mlp_grad: loss (1/N) sum (g - Y)^2 and its gradient (host outputs) for rows d_X, d_Y
- * (device); N a multiple of 32, at most 65536.  Both synchronise `stream`. */
+ * (device); N a multiple of 32, at most 65536.  The gradient comes from the training kernel's
+ * own forward and backward code (one step, no update).  Both synchronise `stream`. */
 int mlmc_mlp_forward(const float *params, const float *d_X, uint64_t N, float *d_G, void *stream);
 int mlmc_mlp_grad(const float *params, const float *d_X, const float *d_Y, uint64_t N, float *grad,
                   double *loss, void *stream);
@@ -407,7 +435,8 @@ int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t N0, const m
 /*
  * ---------------------------------------------------------------- autotuner
  * mlmc_autotune -- time candidate launch shapes of the level kernel (threads per block in
- * {128, 256, 512}, every valid lanes_per_path, one or two waves of resident blocks) for
+ * {128, 256, 512}, every valid lanes_per_path, one or two samples per thread where the two-sample
+ * kernel applies, one or two waves of resident blocks) for
  * levels 0..max_level of (precision, payoff, M) at N = 2^10, 2^13, ... (up to 2e9 fine steps per
  * launch), keeping the fastest per size class.  Whenever a caller leaves launch fields at zero
  * the library then uses the tuned values of the nearest size class at or below N.  A different
@@ -423,8 +452,9 @@ int mlmc_autotune_load(const char *path, int *entries);
 int mlmc_autotune_clear(void);
 /* Number of table entries. */
 int mlmc_autotune_entries(void);
-/* Tuned shape for (precision, payoff, M, level, N): threads_per_block, lanes_per_path, and in
- * `blocks` the number of waves of resident blocks; MLMC_EINVAL if the table has none. */
+/* Tuned shape for (precision, payoff, M, level, N): threads_per_block, lanes_per_path,
+ * samples_per_thread, and in `blocks` the number of waves of resident blocks; MLMC_EINVAL if the
+ * table has none. */
 int mlmc_autotune_lookup(int precision, int payoff, int M, int level, uint64_t N, mlmc_launch *out);
 
 /* Number of streaming multiprocessors of the current device, or -1 with an error message. */

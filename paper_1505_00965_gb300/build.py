@@ -15,13 +15,21 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmlmc_gb300.so")
-SOURCES = ["api.cu", "batch.cu", "cv.cu", "level_anti_fp32.cu", "level_anti_fp64.cu", "level_fp32.cu", "level_fp32_mil.cu",
+SOURCES = ["api.cu", "batch.cu", "cv.cu", "level_anti_fp32.cu", "level_anti_fp64.cu", "level_fp32.cu", "level_fp32_mil.cu", "level_fp32_ns2.cu",
            "level_fp64.cu", "level_fp64_mil.cu", "ode.cu", "tune.cu"]
-HEADERS = ["cv_kernels.cuh", "driver.h", "engine.h", "host.h", "level_kernel.cuh", "mlp.cuh", "rng.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]
+
+
+def headers() -> list[str]:
+    """Every header a translation unit can include: all of csrc/*.h, csrc/*.cuh and include/*.h
+    (a change to any of them rebuilds every object)."""
+    out = []
+    for d in (CSRC, os.path.join(ROOT, "include")):
+        out += [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".h", ".cuh"))]
+    return out
 
 
 def _stale(target: str, deps: list[str]) -> bool:
@@ -33,7 +41,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mlmc.h")]
+    hdrs = headers()
     objs = []
     jobs = []
     for src in SOURCES:

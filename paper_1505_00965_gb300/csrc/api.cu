@@ -27,6 +27,9 @@ thread_local std::string g_error;
 
 // Least cost of a launch with fewer items than one wave, in waves (see plan_level)
 constexpr double kLoneWaveCost = 0.25;
+// Samples per thread of one-thread-per-sample FP32 launches when neither the caller nor the
+// autotuner chose.
+constexpr int kDefaultSamplesPerThread = 1;
 
 }  // namespace
 
@@ -123,7 +126,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
 {
     if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
         return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
-    if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
+    const int ns_req = launch ? launch->samples_per_thread : 0;
+    if (ns_req < 0 || ns_req > 2) return fail(MLMC_EINVAL, "samples_per_thread must be 0 (automatic), 1 or 2");
     const long nf = ipow(M, level);
     const int unit = std::max(M, 4);  // a lane's chunk holds whole Philox blocks and coarse steps
     // a shape chosen by the autotuner fills the fields the caller left at zero
@@ -188,7 +192,18 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     const bool small = nf < 4;
     const int mt = small ? -1 : (M == 4 ? 4 : 0);
     const bool long_lanes = nf / lanes > kLongLaneSteps;
-    plan->kernel = precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split, scheme, long_lanes)
+    // samples per thread: the two-sample kernel exists for FP32 Euler--Maruyama whole paths
+    const bool ns2_ok = !split && !small && precision == MLMC_FP32_PATH && scheme == MLMC_EULER_MARUYAMA &&
+                        threads <= kNs2MaxThreads;
+    int ns = ns_req ? ns_req : (have_tuned && tuned.ns ? tuned.ns : kDefaultSamplesPerThread);
+    if (ns == 2 && !ns2_ok) {
+        if (ns_req == 2)
+            return fail(MLMC_EINVAL, "samples_per_thread 2 needs FP32 Euler--Maruyama paths with M^l >= 4, "
+                        "lanes_per_path 1 and at most %d threads per block", kNs2MaxThreads);
+        ns = 1;
+    }
+    plan->kernel = ns == 2 ? level_ns2_kernel_fp32(payoff, mt, long_lanes)
+                 : precision == MLMC_FP32_PATH ? level_kernel_fp32(payoff, mt, split, scheme, long_lanes)
                                                : level_kernel_fp64(payoff, mt, split, scheme, long_lanes);
     if (!plan->kernel) return fail(MLMC_EINVAL, "no kernel for payoff %d", payoff);
     int max_blocks = 0;
@@ -199,7 +214,7 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     if (!blocks) {
         // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels
         const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
-                                   : (double)std::max<uint64_t>(N, 1) * lanes;
+                                   : std::ceil((double)std::max<uint64_t>(N, 1) * lanes / ns);
         const double need = std::ceil(items / threads);
         const int oversub = have_tuned ? std::max(1, tuned.oversub) : 1;
         blocks = (int)std::min<double>(need, (double)max_blocks * oversub);
@@ -208,6 +223,7 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     plan->threads = threads;
     plan->lanes = lanes;
     plan->blocks = blocks;
+    plan->ns = ns;
     return MLMC_OK;
 }
 
@@ -217,7 +233,8 @@ static int plan_ode(int level, int M, uint64_t N, int precision, int scheme, con
 {
     if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH && precision != MLMC_FP64_STREAM32)
         return fail(MLMC_EINVAL, "precision must be MLMC_FP64, MLMC_FP32_PATH or MLMC_FP64_STREAM32");
-    if (launch && launch->reserved != 0) return fail(MLMC_EINVAL, "mlmc_launch.reserved must be 0");
+    if (launch && launch->samples_per_thread > 1)
+        return fail(MLMC_EINVAL, "the quintic ODE kernel takes one sample per thread");
     if (launch && launch->lanes_per_path > 1)
         return fail(MLMC_EINVAL, "the quintic ODE runs one thread per sample (lanes_per_path %d)",
                     launch->lanes_per_path);
@@ -282,8 +299,11 @@ int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *
     if (launch && launch->lanes_per_path > 1)
         return fail(MLMC_EINVAL, "the antithetic estimator runs one thread per sample (lanes_per_path %d)",
                     launch->lanes_per_path);
+    if (launch && launch->samples_per_thread > 1)
+        return fail(MLMC_EINVAL, "the antithetic kernels take one sample per thread");
     mlmc_launch one = launch ? *launch : mlmc_launch{0, 0, 0, 0};
     one.lanes_per_path = 1;
+    one.samples_per_thread = 1;
     int rc = plan_level(level, M, N, precision, payoff->kind, model->scheme, &one, plan);
     if (rc || ipow(M, level) < 4) return rc;
     const int mt = M == 4 ? 4 : 0;

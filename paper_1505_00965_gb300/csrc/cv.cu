@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cv_kernels.cuh"
+#include "train_kernel.cuh"
 #include "driver.h"
 #include "engine.h"
 #include "host.h"
@@ -25,6 +26,7 @@ struct mlmc_cv {
     float *d_params[MLMC_CV_MAX_LEVELS];
     float h_params[MLMC_CV_MAX_LEVELS][kNumParams];
     mlmc_cv_level_info info[MLMC_CV_MAX_LEVELS];
+    mlmc_cv_train_stats train;  // zero unless made by mlmc_cv_train
 };
 
 namespace {
@@ -175,48 +177,67 @@ void init_params(float *w, uint64_t seed)
     for (int i = 0; i < kHidden; ++i) w[kOffW3 + i] = (float)(next() / std::sqrt((double)kHidden));
 }
 
-struct TrainBuffers {
-    float *Z1 = nullptr, *Z2 = nullptr, *DZ1 = nullptr, *DZ2 = nullptr, *H1 = nullptr, *H2 = nullptr;
-    float *G = nullptr, *D = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *params = nullptr;
-    unsigned *step = nullptr;
-    int alloc(int B)
-    {
-        const size_t act = (size_t)B * kHidden * sizeof(float);
-        for (float **b : {&Z1, &Z2, &DZ1, &DZ2, &H1, &H2}) CUDA_TRY(cudaMalloc(b, act));
-        CUDA_TRY(cudaMalloc(&G, B * sizeof(float)));
-        CUDA_TRY(cudaMalloc(&D, B * sizeof(float)));
-        for (float **b : {&grad, &m1, &m2, &params}) CUDA_TRY(cudaMalloc(b, kNumParams * sizeof(float)));
-        CUDA_TRY(cudaMalloc(&step, sizeof(unsigned)));
-        return MLMC_OK;
-    }
-    void release()
-    {
-        for (float *b : {Z1, Z2, DZ1, DZ2, H1, H2, G, D, grad, m1, m2, params})
-            if (b) cudaFree(b);
-        if (step) cudaFree(step);
-        *this = TrainBuffers();
-    }
-};
-
-// Queue one training step (forward, backward, gradient, Adam) on rows [off, off + B).
-int queue_step(TrainBuffers &tb, const float *X, const float *Y, uint64_t off, int B, float mu, float inv_sd,
-               float lr, cudaStream_t st, bool update)
+// Launch the training kernel (train) or one gradient evaluation (!train) for `jobs` networks, one
+// thread-block cluster of `cluster` CTAs each.
+int launch_training(const TrainArgs &args, int jobs, int cluster, bool train, cudaStream_t st)
 {
-    const float *cparams = tb.params;
-    void *fargs[] = {(void *)&cparams, (void *)&X, &off, &B, &tb.Z1, &tb.Z2, &tb.G, &tb.step};
-    CUDA_TRY(cudaLaunchKernel((const void *)train_forward_kernel, dim3((B + 255) / 256), dim3(256), fargs, 0, st));
-    void *bargs[] = {(void *)&cparams, (void *)&Y, &off, &B, &mu, &inv_sd, &tb.Z1, &tb.Z2, &tb.G,
-                     &tb.D, &tb.DZ1, &tb.DZ2, &tb.H1, &tb.H2};
-    CUDA_TRY(cudaLaunchKernel((const void *)train_backward_kernel, dim3((B + 127) / 128), dim3(128), bargs, 0, st));
-    void *gargs[] = {(void *)&X, &off, &B, &tb.D, &tb.DZ1, &tb.DZ2, &tb.H1, &tb.H2, &tb.grad};
-    CUDA_TRY(cudaLaunchKernel((const void *)train_grad_kernel, dim3((kNumParams + 255) / 256), dim3(256), gargs, 0,
-                              st));
-    if (update) {
-        void *aargs[] = {&tb.params, &tb.grad, &tb.m1, &tb.m2, &tb.step, &lr};
-        CUDA_TRY(cudaLaunchKernel((const void *)adam_kernel, dim3((kNumParams + 255) / 256), dim3(256), aargs, 0,
-                                  st));
-    }
+    const void *k = train ? (const void *)train_cluster_kernel<true> : (const void *)train_cluster_kernel<false>;
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
+    if (cluster > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(cluster * jobs));
+    cfg.blockDim = dim3(kTrainThreads);
+    cfg.dynamicSmemBytes = sizeof(TrainSmem);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TrainArgs a = args;
+    void *kargs[] = {&a};
+    CUDA_TRY(cudaLaunchKernelExC(&cfg, k, kargs));
     return MLMC_OK;
+}
+
+// Whether a cluster of `cluster` training CTAs fits on this GPU (the SMs of one GPC must hold it).
+bool training_cluster_fits(int cluster, bool train)
+{
+    const void *k = train ? (const void *)train_cluster_kernel<true> : (const void *)train_cluster_kernel<false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)) != cudaSuccess)
+        return false;
+    if (cluster > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cluster);
+    cfg.blockDim = dim3(kTrainThreads);
+    cfg.dynamicSmemBytes = sizeof(TrainSmem);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n >= 1;
+}
+
+// Largest cluster (16, 8, 4 or 2 CTAs; at least `least`) that fits and splits B rows into slices
+// of whole 16-row tiles; 0 if none.
+int training_cluster(int B, int least, bool train)
+{
+    for (int c = kTrainMaxCluster; c >= least; c /= 2)
+        if (B % (16 * c) == 0 && training_cluster_fits(c, train)) return c;
+    return 0;
 }
 
 double seconds_per_sample(cudaEvent_t a, cudaEvent_t b, uint64_t n)
@@ -386,23 +407,30 @@ int mlmc_mlp_grad(const float *params, const float *d_X, const float *d_Y, uint6
     if (!params || !d_X || !d_Y || !grad || !loss) return fail(MLMC_EINVAL, "NULL argument");
     if (N == 0 || N % 32 || N > 65536) return fail(MLMC_EINVAL, "N must be a positive multiple of 32, at most 65536");
     cudaStream_t st = (cudaStream_t)stream;
-    TrainBuffers tb;
-    int rc = tb.alloc((int)N);
-    if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(tb.params, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tb.step, 0, sizeof(unsigned), st);
-        rc = e == cudaSuccess ? queue_step(tb, d_X, d_Y, 0, (int)N, 0.f, 1.f, 0.f, st, false)
-                              : fail(MLMC_ECUDA, "upload failed: %s", cudaGetErrorString(e));
-    }
+    const int cluster = training_cluster((int)N, 2, false);
+    if (!cluster) return fail(MLMC_ECUDA, "no thread-block cluster for the gradient kernel fits this GPU");
+    float *d_buf = nullptr;  // parameters, gradient, then N outputs g
+    CUDA_TRY(cudaMallocAsync(&d_buf, sizeof(float) * (2 * kNumParams + N), st));
+    TrainArgs a = {};
+    a.job[0] = TrainJob{d_X, d_Y, d_buf, 0.f, 1.f};
+    a.B = (int)N;
+    a.steps = 1;
+    a.epochs = 1;
+    a.lr = 0.f;
+    a.grad_out = d_buf + kNumParams;
+    a.g_out = d_buf + 2 * kNumParams;
     std::vector<float> g(N), y(N);
+    cudaError_t e = cudaMemcpyAsync(d_buf, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, st);
+    int rc = e == cudaSuccess ? launch_training(a, 1, cluster, false, st)
+                              : fail(MLMC_ECUDA, "upload failed: %s", cudaGetErrorString(e));
     if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(grad, tb.grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), tb.G, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(grad, a.grad_out, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), a.g_out, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(y.data(), d_Y, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = fail(MLMC_ECUDA, "network gradient failed: %s", cudaGetErrorString(e));
     }
-    tb.release();
+    cudaFreeAsync(d_buf, st);
     if (rc) return rc;
     double acc = 0.0;
     for (uint64_t i = 0; i < N; ++i) acc += ((double)g[i] - y[i]) * ((double)g[i] - y[i]);
@@ -429,7 +457,8 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
     mlmc_cv *cv = nullptr;
     int rc = mlmc_cv_create(M, model, payoff, &cv);
     if (rc) return rc;
-    // training runs on a private stream (graph capture needs one) once `stream` has drained
+    // training runs on a private stream once `stream` has drained
+    const auto t_begin = std::chrono::steady_clock::now();
     cudaStream_t st = nullptr;
     {
         cudaError_t e0 = cudaStreamSynchronize((cudaStream_t)stream);
@@ -439,20 +468,19 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
             return fail(MLMC_ECUDA, "training stream: %s", cudaGetErrorString(e0));
         }
     }
-    float *d_X = nullptr, *d_Y = nullptr, *d_Gv = nullptr;
-    TrainBuffers tb;
+    const int cluster = training_cluster(B, kTrainMinClusterAdam, true);
+    if (!cluster) {
+        cudaStreamDestroy(st);
+        mlmc_cv_free(cv);
+        return fail(MLMC_ECUDA, "no thread-block cluster of %d or more training CTAs fits this GPU", kTrainMinClusterAdam);
+    }
+    float *d_X = nullptr, *d_Y = nullptr, *d_Gv = nullptr, *d_P = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     auto cleanup = [&](int code) {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
         if (d_X) cudaFree(d_X);
         if (d_Y) cudaFree(d_Y);
         if (d_Gv) cudaFree(d_Gv);
-        tb.release();
+        if (d_P) cudaFree(d_P);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (st) cudaStreamDestroy(st);
@@ -465,59 +493,67 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         cudaError_t e_ = (expr);                                                                    \
         if (e_ != cudaSuccess) return cleanup(fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_))); \
     } while (0)
-    CV_TRY(cudaMalloc(&d_X, sizeof(float) * 8 * n_train));
-    CV_TRY(cudaMalloc(&d_Y, sizeof(float) * n_train));
+    CV_TRY(cudaMalloc(&d_X, sizeof(float) * 8 * n_train * levels));
+    CV_TRY(cudaMalloc(&d_Y, sizeof(float) * n_train * levels));
     CV_TRY(cudaMalloc(&d_Gv, sizeof(float) * n_train));
+    CV_TRY(cudaMalloc(&d_P, sizeof(float) * kNumParams * levels));
     CV_TRY(cudaEventCreate(&ev0));
     CV_TRY(cudaEventCreate(&ev1));
-    rc = tb.alloc(B);
-    if (rc) return cleanup(rc);
-    std::vector<float> hY(n_train), hG(n_val);
+    std::vector<float> hY(n_train * levels), hG(n_val);
+    std::vector<double> mu(levels), sd(levels);
+    // 1. training data of every level from the method itself (independent tag), target
+    // standardisation, initial weights
+    TrainArgs targs = {};
     for (int l = 0; l < levels; ++l) {
-        // 1. training data from the method itself (independent tag)
-        rc = mlmc_cv_training_data(cv, l, n_train, 0, seed, d_X, d_Y, st);
+        float *X = d_X + 8 * n_train * l, *Yd = d_Y + n_train * l;
+        rc = mlmc_cv_training_data(cv, l, n_train, 0, seed, X, Yd, st);
         if (rc) return cleanup(rc);
-        CV_TRY(cudaMemcpy(hY.data(), d_Y, sizeof(float) * n_train, cudaMemcpyDeviceToHost));
-        double mu = 0.0, m2 = 0.0;
-        for (uint64_t i = 0; i < n_fit; ++i) mu += hY[i];
-        mu /= (double)n_fit;
-        for (uint64_t i = 0; i < n_fit; ++i) m2 += (hY[i] - mu) * (hY[i] - mu);
-        const double sd = std::sqrt(std::max(m2 / (double)n_fit, 1e-300));
-        // 2. initial weights, Adam state
+        const float *hy = hY.data() + n_train * l;
+        CV_TRY(cudaMemcpy((void *)hy, Yd, sizeof(float) * n_train, cudaMemcpyDeviceToHost));
+        double m = 0.0, v = 0.0;
+        for (uint64_t i = 0; i < n_fit; ++i) m += hy[i];
+        m /= (double)n_fit;
+        for (uint64_t i = 0; i < n_fit; ++i) v += (hy[i] - m) * (hy[i] - m);
+        mu[l] = m;
+        sd[l] = std::sqrt(std::max(v / (double)n_fit, 1e-300));
         float w[kNumParams];
         init_params(w, o.init_seed + 7919ull * (uint64_t)l);
-        CV_TRY(cudaMemcpy(tb.params, w, sizeof(w), cudaMemcpyHostToDevice));
-        CV_TRY(cudaMemset(tb.m1, 0, sizeof(float) * kNumParams));
-        CV_TRY(cudaMemset(tb.m2, 0, sizeof(float) * kNumParams));
-        CV_TRY(cudaMemset(tb.step, 0, sizeof(unsigned)));
-        // 3. one epoch of steps captured once, replayed `epochs` times
-        const uint64_t steps = n_fit / B;
-        CV_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (uint64_t s = 0; s < steps && !rc; ++s)
-            rc = queue_step(tb, d_X, d_Y, s * B, B, (float)mu, (float)(1.0 / sd), lr, st, true);
-        cudaError_t ce = cudaStreamEndCapture(st, &graph);
-        if (rc) return cleanup(rc);
-        CV_TRY(ce);
-        CV_TRY(cudaGraphInstantiate(&exec, graph, 0));
-        for (int ep = 0; ep < epochs; ++ep) CV_TRY(cudaGraphLaunch(exec, st));
-        CV_TRY(cudaStreamSynchronize(st));
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
+        CV_TRY(cudaMemcpy(d_P + kNumParams * l, w, sizeof(w), cudaMemcpyHostToDevice));
+        targs.job[l] = TrainJob{X, Yd, d_P + kNumParams * l, (float)m, (float)(1.0 / sd[l])};
+    }
+    const auto t_data = std::chrono::steady_clock::now();
+    // 2. every level's network trained side by side: one cluster per level, one launch
+    targs.B = B;
+    targs.steps = (int)(n_fit / (uint64_t)B);
+    targs.epochs = epochs;
+    targs.lr = lr;
+    CV_TRY(cudaEventRecord(ev0, st));
+    rc = launch_training(targs, levels, cluster, true, st);
+    if (rc) return cleanup(rc);
+    CV_TRY(cudaEventRecord(ev1, st));
+    CV_TRY(cudaEventSynchronize(ev1));
+    float train_kernel_ms = 0.f;
+    CV_TRY(cudaEventElapsedTime(&train_kernel_ms, ev0, ev1));
+    const auto t_trained = std::chrono::steady_clock::now();
+    double eval_ms = 0.0, cost_ms = 0.0;
+    for (int l = 0; l < levels; ++l) {
+        const auto t_eval0 = std::chrono::steady_clock::now();
+        float w[kNumParams];
         // 4. undo the target standardisation in the last layer: g = sd * net + mu
-        CV_TRY(cudaMemcpy(w, tb.params, sizeof(w), cudaMemcpyDeviceToHost));
-        for (int i = 0; i < kHidden; ++i) w[kOffW3 + i] = (float)(w[kOffW3 + i] * sd);
-        w[kOffB3] = (float)(w[kOffB3] * sd + mu);
+        CV_TRY(cudaMemcpy(w, d_P + kNumParams * l, sizeof(w), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < kHidden; ++i) w[kOffW3 + i] = (float)(w[kOffW3 + i] * sd[l]);
+        w[kOffB3] = (float)(w[kOffB3] * sd[l] + mu[l]);
         rc = mlmc_cv_set_params(cv, l, w, 1.0);
         if (rc) return cleanup(rc);
+        const float *d_Xl = d_X + 8 * n_train * l;
+        const float *hYl = hY.data() + n_train * l;
         // 5. held-out variance ratio
-        rc = mlmc_mlp_forward(w, d_X + 8 * n_fit, n_val, d_Gv, st);
+        rc = mlmc_mlp_forward(w, d_Xl + 8 * n_fit, n_val, d_Gv, st);
         if (rc) return cleanup(rc);
         CV_TRY(cudaMemcpy(hG.data(), d_Gv, sizeof(float) * n_val, cudaMemcpyDeviceToHost));
         double sy = 0, syy = 0, sr = 0, srr = 0, sg = 0, sgg = 0;
         for (uint64_t i = 0; i < n_val; ++i) {
-            const double y = hY[n_fit + i], g = hG[i], r = y - g;
+            const double y = hYl[n_fit + i], g = hG[i], r = y - g;
             sy += y; syy += y * y; sr += r; srr += r * r; sg += g; sgg += g * g;
         }
         const double nv = (double)n_val;
@@ -525,7 +561,9 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         inf.var_plain = std::max(syy / nv - (sy / nv) * (sy / nv), 0.0);
         inf.var_resid = std::max(srr / nv - (sr / nv) * (sr / nv), 0.0);
         inf.var_g = std::max(sgg / nv - (sg / nv) * (sg / nv), 0.0);
-        inf.train_loss = inf.var_resid / (sd * sd);
+        inf.train_loss = inf.var_resid / (sd[l] * sd[l]);
+        const auto t_cost0 = std::chrono::steady_clock::now();
+        eval_ms += std::chrono::duration<double, std::milli>(t_cost0 - t_eval0).count();
         // 6. measured cost per sample of the plain, control-variate and mean kernels
         // (sizes large enough that every timed launch runs for a millisecond or more: small
         // launches would measure launch latency and idle SMs, not the cost per sample)
@@ -590,10 +628,28 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
                          std::max(inf.var_plain * inf.t_plain, 1e-300);
         inf.used = inf.work_ratio < 1.0 ? 1 : 0;
         inf.trained = 1;
+        cost_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_cost0).count();
     }
 #undef CV_TRY
     cleanup(MLMC_OK);
+    mlmc_cv_train_stats &ts = cv->train;
+    ts.data_ms = std::chrono::duration<double, std::milli>(t_data - t_begin).count();
+    ts.train_ms = std::chrono::duration<double, std::milli>(t_trained - t_data).count();
+    ts.train_kernel_ms = train_kernel_ms;
+    ts.eval_ms = eval_ms;
+    ts.cost_ms = cost_ms;
+    ts.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
+    ts.steps = (int64_t)targs.steps * epochs;
+    ts.cluster = cluster;
+    ts.levels = levels;
     *out = cv;
+    return MLMC_OK;
+}
+
+int mlmc_cv_train_info(const mlmc_cv *cv, mlmc_cv_train_stats *out)
+{
+    if (!cv || !out) return fail(MLMC_EINVAL, "cv and out must not be NULL");
+    *out = cv->train;
     return MLMC_OK;
 }
 

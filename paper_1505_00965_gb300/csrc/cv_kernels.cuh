@@ -375,141 +375,4 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restric
     }
 }
 
-// ------------------------------------------------------------------ training (one mini-batch)
-
-// Forward pass of a mini-batch of B rows starting at row `off` of (X, Y): stores z1, z2 and g
-// for the backward pass; thread 0 of block 0 advances the Adam step counter.
-__global__ void __launch_bounds__(256) train_forward_kernel(const float *__restrict__ params, const float *X,
-                                                            uint64_t off, int B, float *Z1, float *Z2, float *G,
-                                                            unsigned *step)
-{
-    __shared__ MlpShared net;
-    __shared__ uint32_t xw_all[8][128];
-    load_mlp(net, params);
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1u;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int base = (blockIdx.x * 8 + warp) * 32;  // first batch row of this warp
-    if (base >= B) return;                          // whole warps only (B is a multiple of 32)
-    uint32_t *xw = xw_all[warp];
-    const float *xr = X + 8 * (off + base + lane);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) xw[lane * 4 + j] = pack_bf16x2(xr[2 * j], xr[2 * j + 1]);
-    __syncwarp();
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int tile = 0; tile < 2; ++tile) {
-        TileActs acts;
-        float r0, r1;
-        mlp_tile(net, xw + tile * 64, r0, r1, &acts);
-        const int row0 = base + tile * 16 + g, row1 = row0 + 8;
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int o = 8 * nt + 2 * t;
-            Z1[row0 * kHidden + o] = acts.z1[nt][0];
-            Z1[row0 * kHidden + o + 1] = acts.z1[nt][1];
-            Z1[row1 * kHidden + o] = acts.z1[nt][2];
-            Z1[row1 * kHidden + o + 1] = acts.z1[nt][3];
-            Z2[row0 * kHidden + o] = acts.z2[nt][0];
-            Z2[row0 * kHidden + o + 1] = acts.z2[nt][1];
-            Z2[row1 * kHidden + o] = acts.z2[nt][2];
-            Z2[row1 * kHidden + o + 1] = acts.z2[nt][3];
-        }
-        if (t == 0) {
-            G[row0] = r0;
-            G[row1] = r1;
-        }
-    }
-}
-
-__device__ __forceinline__ float bf16_round(float v)
-{
-    const uint32_t w = pack_bf16x2(0.f, v);
-    return __uint_as_float(w & 0xFFFF0000u);
-}
-
-// Backward pass per row (FP32): loss (1/B) sum (g - (Y - mu) / sd)^2.  Writes
-// D = dL/dg, DZ2 = dL/dz2, DZ1 = dL/dz1, H1 = bf16(GELU(z1)) (the layer-2 input the forward
-// used) and H2 = GELU(z2).
-__global__ void __launch_bounds__(128) train_backward_kernel(const float *__restrict__ params, const float *Y,
-                                                             uint64_t off, int B, float mu, float inv_sd,
-                                                             const float *Z1, const float *Z2, const float *G,
-                                                             float *D, float *DZ1, float *DZ2, float *H1, float *H2)
-{
-    __shared__ float W2s[kHidden * kHidden];
-    __shared__ float w3s[kHidden];
-    for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) W2s[i] = bf16_round(params[kOffW2 + i]);
-    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) w3s[i] = params[kOffW3 + i];
-    __syncthreads();
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= B) return;
-    const float target = (Y[off + row] - mu) * inv_sd;
-    const float d = 2.0f * (G[row] - target) / (float)B;
-    D[row] = d;
-    float dh1[kHidden];
-#pragma unroll
-    for (int i = 0; i < kHidden; ++i) dh1[i] = 0.f;
-    for (int o = 0; o < kHidden; ++o) {
-        const float z2 = Z2[row * kHidden + o];
-        const float dz2 = d * w3s[o] * gelu_grad(z2);
-        DZ2[row * kHidden + o] = dz2;
-        H2[row * kHidden + o] = gelu(z2);
-#pragma unroll
-        for (int i = 0; i < kHidden; ++i) dh1[i] = fmaf(dz2, W2s[o * kHidden + i], dh1[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < kHidden; ++i) {
-        const float z1 = Z1[row * kHidden + i];
-        DZ1[row * kHidden + i] = dh1[i] * gelu_grad(z1);
-        H1[row * kHidden + i] = bf16_round(gelu(z1));
-    }
-}
-
-// Parameter gradients: one thread per parameter, sums over the B rows of the batch.
-__global__ void __launch_bounds__(256) train_grad_kernel(const float *X, uint64_t off, int B, const float *D,
-                                                         const float *DZ1, const float *DZ2, const float *H1,
-                                                         const float *H2, float *grad)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kNumParams) return;
-    float acc = 0.f;
-    if (i < kOffB1) {  // W1[u][k]
-        const int u = i / kInputs, k = i % kInputs;
-        for (int r = 0; r < B; ++r) acc = fmaf(DZ1[r * kHidden + u], bf16_round(X[8 * (off + r) + k]), acc);
-    } else if (i < kOffW2) {  // b1[u]
-        const int u = i - kOffB1;
-        for (int r = 0; r < B; ++r) acc += DZ1[r * kHidden + u];
-    } else if (i < kOffB2) {  // W2[o][u]
-        const int o = (i - kOffW2) / kHidden, u = (i - kOffW2) % kHidden;
-        for (int r = 0; r < B; ++r) acc = fmaf(DZ2[r * kHidden + o], H1[r * kHidden + u], acc);
-    } else if (i < kOffW3) {  // b2[o]
-        const int o = i - kOffB2;
-        for (int r = 0; r < B; ++r) acc += DZ2[r * kHidden + o];
-    } else if (i < kOffB3) {  // w3[o]
-        const int o = i - kOffW3;
-        for (int r = 0; r < B; ++r) acc = fmaf(D[r], H2[r * kHidden + o], acc);
-    } else {  // b3
-        for (int r = 0; r < B; ++r) acc += D[r];
-    }
-    grad[i] = acc;
-}
-
-// Adam update of the FP32 master parameters (step counter advanced by the forward kernel).
-__global__ void __launch_bounds__(256) adam_kernel(float *params, const float *grad, float *m1, float *m2,
-                                                   const unsigned *step, float lr)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kNumParams) return;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float gi = grad[i];
-    const float a = b1 * m1[i] + (1.f - b1) * gi;
-    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
-    m1[i] = a;
-    m2[i] = v;
-    const float t = (float)*step;
-    const float ah = a / (1.f - powf(b1, t));
-    const float vh = v / (1.f - powf(b2, t));
-    params[i] -= lr * ah / (sqrtf(vh) + 1e-8f);
-}
-
 }  // namespace mlmcgb

@@ -64,6 +64,10 @@ const void *level_kernel_fp64_milstein(int payoff, int mt, bool split, bool long
 // Antithetic level kernels (level_anti_fp32.cu, level_anti_fp64.cu): mt = 4 (M = 4) or 0 (M = 2).
 const void *level_anti_kernel_fp32(int payoff, int mt, int scheme, bool long_lanes);
 const void *level_anti_kernel_fp64(int payoff, int mt, int scheme, bool long_lanes);
+// Two samples per thread (level_fp32_ns2.cu): FP32 paths, Euler--Maruyama, one thread per sample,
+// mt = 4 or 0; at most 512 threads per block.
+const void *level_ns2_kernel_fp32(int payoff, int mt, bool long_lanes);
+constexpr int kNs2MaxThreads = 512;
 // Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
 const void *ode_level_kernel(int precision, int scheme);
 const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive = false);

@@ -31,6 +31,7 @@ int max_resident_blocks(const void *kernel, int threads, int *out);
 struct Plan {
     const void *kernel;
     int threads, lanes, blocks;
+    int ns = 1;  // samples per thread (2: the two-sample kernel)
 };
 int plan_level(int level, int M, uint64_t N, int precision, int payoff, int scheme, const mlmc_launch *launch,
                Plan *plan);
@@ -49,6 +50,7 @@ int check_estimate_args(double eps, int M, int Lmin, int Lmax, uint64_t N0, int 
 struct TunedShape {
     int threads, lanes, oversub;
     double ns_per_sample;
+    int ns = 0;  // samples per thread (0 = not tuned: the planner's default)
 };
 bool tuned_lookup(int precision, int payoff, int M, int level, uint64_t N, TunedShape *out);
 

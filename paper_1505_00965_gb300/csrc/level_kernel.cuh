@@ -808,6 +808,30 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
     finish_sums(m, p);
 }
 
+// Two samples per thread and iteration, one thread per sample (no split, no antithetic path): the
+// two samples' Philox and step chains are independent, so each scheduler has twice the
+// instruction-level parallelism per warp, at about 1.5 times the registers.  A kernel of its own
+// (not a runtime branch of level_kernel) so that the one-sample kernels keep their register count;
+// at most 512 threads per block, which lets it hold up to 128 registers.
+template <typename R, int MT, int PAY, bool LONG = false>
+__global__ void __launch_bounds__(512) level_ns2_kernel(const LevelParams p)
+{
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
+    int nb = 0;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, T = (uint64_t)gridDim.x * blockDim.x;
+    if (p.nf == 4) {
+        if (p.y_out)
+            multi_range<R, MT, PAY, false, 2, true, 1, false, LONG>(p, p.first, p.N, t, T, m, b1, b2, b3, b4, nb, p.y_out);
+        else
+            multi_range<R, MT, PAY, false, 2, true, 1, false, LONG>(p, p.first, p.N, t, T, m, b1, b2, b3, b4, nb, nullptr);
+    } else {
+        multi_range<R, MT, PAY, false, 2, true, 0, false, LONG>(p, p.first, p.N, t, T, m, b1, b2, b3, b4, nb, p.y_out);
+    }
+    fold_batch<R>(m, b1, b2, b3, b4);
+    finish_sums(m, p);
+}
+
 // Levels with M^l < 4 (level 0, and level 1 when M = 2).
 template <typename R, int PAY, bool MIL>
 __global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
@@ -968,6 +992,30 @@ template <typename R> const void *select_anti_kernel(int payoff, int mt, int sch
     if (mt == 0)
         return scheme == 1 ? select_anti_by_payoff<R, 0, true>(payoff, long_lanes)
                            : select_anti_by_payoff<R, 0, false>(payoff, long_lanes);
+    return nullptr;
+}
+
+// Two-samples-per-thread kernels (Euler--Maruyama, one thread per sample, mt = 4 or 0).
+template <typename R, int MT> const void *select_ns2_by_payoff(int payoff, bool long_lanes)
+{
+    switch (payoff) {
+    case kEuropean: return (const void *)level_ns2_kernel<R, MT, kEuropean>;
+    case kAsian:
+        if constexpr (kBlockedSum<R, kAsian>) {
+            if (long_lanes) return (const void *)level_ns2_kernel<R, MT, kAsian, true>;
+        }
+        return (const void *)level_ns2_kernel<R, MT, kAsian>;
+    case kLookback: return (const void *)level_ns2_kernel<R, MT, kLookback>;
+    case kDigital: return (const void *)level_ns2_kernel<R, MT, kDigital>;
+    case kLinear: return (const void *)level_ns2_kernel<R, MT, kLinear>;
+    case kGeoAsian: return (const void *)level_ns2_kernel<R, MT, kGeoAsian>;
+    default: return nullptr;
+    }
+}
+template <typename R> const void *select_ns2_kernel(int payoff, int mt, bool long_lanes)
+{
+    if (mt == 4) return select_ns2_by_payoff<R, 4>(payoff, long_lanes);
+    if (mt == 0) return select_ns2_by_payoff<R, 0>(payoff, long_lanes);
     return nullptr;
 }
 

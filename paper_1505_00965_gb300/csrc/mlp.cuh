@@ -59,14 +59,6 @@ __device__ __forceinline__ float gelu(float z)
     return fmaf(hz, tanh_approx(u), hz);
 }
 
-__device__ __forceinline__ float gelu_grad(float z)
-{
-    const float u = 0.7978845608028654f * fmaf(0.044715f * z * z, z, z);
-    const float t = tanh_approx(u);
-    const float du = 0.7978845608028654f * fmaf(3.0f * 0.044715f, z * z, 1.0f);
-    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
-}
-
 // d += a * b for one m16n8k16 tile, bfloat16 operands, FP32 accumulators.
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
 {
@@ -92,18 +84,10 @@ __device__ __forceinline__ void load_mlp(MlpShared &s, const float *__restrict__
     if (threadIdx.x == 0) s.b3 = params[kOffB3];
 }
 
-// Layer values of one m16 tile kept for training: z1 and z2 accumulators (FP32) per n-tile.
-struct TileActs {
-    float z1[8][4];
-    float z2[8][4];
-};
-
 // g for the 16 samples of one tile.  xw: the warp's staging area, xw[row * 4 + t] holds the
 // bfloat16 pair (x[2t], x[2t+1]) of tile row `row`.  Returns g for rows g and g + 8 of this
-// lane's group (every lane of the group gets both).  If acts is not NULL the layer values
-// are stored there.
-__device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw, float &out0, float &out1,
-                                         TileActs *acts)
+// lane's group (every lane of the group gets both).
+__device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw, float &out0, float &out1)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // layer 1: A = x (16 x 16, columns 8..15 zero), B[k][n] = W1[n][k]
@@ -115,10 +99,7 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
         float c[4] = {s.b1[o], s.b1[o + 1], s.b1[o], s.b1[o + 1]};
         mma_bf16(c, a, s.W1[(8 * nt + g) * 4 + t], 0u);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (acts) acts->z1[nt][i] = c[i];
-            h1[nt][i] = gelu(c[i]);
-        }
+        for (int i = 0; i < 4; ++i) h1[nt][i] = gelu(c[i]);
     }
     // layer 2: A = GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1), B[k][n] = W2[n][k]
     uint32_t a2[4][4];
@@ -137,10 +118,6 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
         const uint32_t *w = &s.W2[(8 * nt + g) * kW2Stride];
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma_bf16(c, a2[kt], w[8 * kt + t], w[8 * kt + t + 4]);
-        if (acts) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acts->z2[nt][i] = c[i];
-        }
         // layer 3: dot product with w3 over this lane's units, rows g and g + 8
         p0 = fmaf(s.w3[o], gelu(c[0]), p0);
         p0 = fmaf(s.w3[o + 1], gelu(c[1]), p0);
@@ -167,7 +144,7 @@ __device__ __forceinline__ float warp_mlp(const MlpShared &s, uint32_t *xw, cons
 #pragma unroll 1
     for (int tile = 0; tile < 2; ++tile) {
         float r0, r1;
-        mlp_tile(s, xw + tile * 64, r0, r1, nullptr);
+        mlp_tile(s, xw + tile * 64, r0, r1);
         // sample (tile * 16 + row) is lane tile * 16 + row; row < 8 holds r0 of group row
         const int row = lane & 15;
         const float v0 = __shfl_sync(0xffffffffu, r0, (row & 7) * 4);

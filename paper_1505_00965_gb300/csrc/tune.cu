@@ -1,8 +1,9 @@
 // tune.cu -- the autotuner: measured choice of the level kernel's launch shape.
 //
 // For each (precision, payoff, M, level) and size class (N rounded down to a power of two) it
-// times candidate shapes -- threads per block, lanes per path (the time-parallel split), and a
-// grid of one or two waves of resident blocks -- with CUDA events and keeps the fastest.  The
+// times candidate shapes -- threads per block, lanes per path (the time-parallel split), samples
+// per thread (one, or two in lockstep: the FP32 one-thread-per-sample kernels), and a grid of one
+// or two waves of resident blocks -- with CUDA events and keeps the fastest.  The
 // planner uses the table whenever the caller leaves the launch shape to the library.  Results
 // do not depend on the grid; a different lanes_per_path changes path roundoff only.
 #include <cuda_runtime.h>
@@ -45,13 +46,16 @@ int load_file(const char *path, int *entries)
     char line[512];
     int n = 0;
     while (std::fgets(line, sizeof(line), f)) {
-        int prec, pay, M, level, lg, threads, lanes, oversub;
+        int prec, pay, M, level, lg, threads, lanes, oversub, spt = 1;
         double ns;
-        if (std::sscanf(line,
-                        " {\"precision\": %d, \"payoff\": %d, \"M\": %d, \"level\": %d, \"log2N\": %d, "
-                        "\"threads\": %d, \"lanes\": %d, \"oversub\": %d, \"ns_per_sample\": %lf}",
-                        &prec, &pay, &M, &level, &lg, &threads, &lanes, &oversub, &ns) == 9) {
-            g_table[Key(prec, pay, M, level, lg)] = TunedShape{threads, lanes, oversub, ns};
+        // entries written before the samples-per-thread field existed read as one sample per thread
+        const int got = std::sscanf(line,
+                                    " {\"precision\": %d, \"payoff\": %d, \"M\": %d, \"level\": %d, \"log2N\": %d, "
+                                    "\"threads\": %d, \"lanes\": %d, \"oversub\": %d, \"ns_per_sample\": %lf, "
+                                    "\"samples_per_thread\": %d}",
+                                    &prec, &pay, &M, &level, &lg, &threads, &lanes, &oversub, &ns, &spt);
+        if (got >= 9 && spt >= 1 && spt <= 2) {
+            g_table[Key(prec, pay, M, level, lg)] = TunedShape{threads, lanes, oversub, ns, spt};
             ++n;
         }
     }
@@ -140,21 +144,26 @@ int mlmc_autotune(int M, int max_level, int precision, int payoff, void *stream,
         for (int lg = 10; lg <= 26; lg += 3) {
             const uint64_t N = 1ull << lg;
             if ((double)N * (double)nf > 2.0e9) break;
-            TunedShape best{256, 1, 1, 1e300};
+            TunedShape best{256, 1, 1, 1e300, 1};
             for (int threads : {128, 256, 512}) {
                 for (int lanes : lanes_set) {
+                  for (int spt : {1, 2}) {
+                    // two samples per thread: FP32 whole paths of levels with M^l >= 4
+                    if (spt == 2 && (lanes > 1 || nf < 4 || precision != MLMC_FP32_PATH || threads > kNs2MaxThreads))
+                        continue;
                     for (int oversub : {1, 2}) {
                         Plan plan;
-                        mlmc_launch probe{threads, lanes, 0, 0};
+                        mlmc_launch probe{threads, lanes, 0, spt};
                         rc = plan_level(level, M, N, precision, payoff, MLMC_EULER_MARUYAMA, &probe, &plan);
                         if (rc) continue;
                         int resident = 0;
                         if (max_resident_blocks(plan.kernel, threads, &resident)) continue;
-                        const double items = nf < 4 ? std::ceil((double)N * nf / 4.0) + 1.0 : (double)N * lanes;
+                        const double items = nf < 4 ? std::ceil((double)N * nf / 4.0) + 1.0
+                                                    : std::ceil((double)N * lanes / spt);
                         const int blocks = (int)std::max(1.0, std::min(std::ceil(items / threads),
                                                                        (double)resident * oversub));
                         if (oversub == 2 && blocks <= resident) continue;  // same grid as one wave
-                        mlmc_launch shape{threads, lanes, std::min(blocks, max_blocks), 0};
+                        mlmc_launch shape{threads, lanes, std::min(blocks, max_blocks), spt};
                         float ms = 0.f;
                         for (int rep = 0; rep < 2 && rc == MLMC_OK; ++rep) {
                             e = cudaEventRecord(e0, st);
@@ -177,8 +186,9 @@ int mlmc_autotune(int M, int max_level, int precision, int payoff, void *stream,
                             return rc;
                         }
                         const double ns = 1e6 * ms / 3.0 / (double)N;
-                        if (ns < best.ns_per_sample) best = TunedShape{threads, lanes, oversub, ns};
+                        if (ns < best.ns_per_sample) best = TunedShape{threads, lanes, oversub, ns, spt};
                     }
+                  }
                 }
             }
             if (best.ns_per_sample < 1e300) {
@@ -206,9 +216,9 @@ int mlmc_autotune_save(const char *path)
         const TunedShape &s = kv.second;
         std::fprintf(f,
                      " {\"precision\": %d, \"payoff\": %d, \"M\": %d, \"level\": %d, \"log2N\": %d, \"threads\": %d, "
-                     "\"lanes\": %d, \"oversub\": %d, \"ns_per_sample\": %.6g}%s\n",
+                     "\"lanes\": %d, \"oversub\": %d, \"ns_per_sample\": %.6g, \"samples_per_thread\": %d}%s\n",
                      std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), s.threads,
-                     s.lanes, s.oversub, s.ns_per_sample, ++i < g_table.size() ? "," : "");
+                     s.lanes, s.oversub, s.ns_per_sample, s.ns > 0 ? s.ns : 1, ++i < g_table.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
     std::fclose(f);
@@ -239,7 +249,7 @@ int mlmc_autotune_lookup(int precision, int payoff, int M, int level, uint64_t N
     out->threads_per_block = s.threads;
     out->lanes_per_path = s.lanes;
     out->blocks = s.oversub;
-    out->reserved = 0;
+    out->samples_per_thread = s.ns > 0 ? s.ns : 1;
     return MLMC_OK;
 }
 

@@ -54,7 +54,7 @@ class mlmc_payoff(ctypes.Structure):
 
 class mlmc_launch(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("lanes_per_path", ctypes.c_int32),
-                ("blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks", ctypes.c_int32), ("samples_per_thread", ctypes.c_int32)]
 
 
 class mlmc_problem(ctypes.Structure):
@@ -95,6 +95,12 @@ class mlmc_cv_level_info(ctypes.Structure):
                 ("work_ratio", ctypes.c_double), ("train_loss", ctypes.c_double), ("var_lattice", ctypes.c_double)]
 
 
+class mlmc_cv_train_stats(ctypes.Structure):
+    _fields_ = [("data_ms", ctypes.c_double), ("train_ms", ctypes.c_double), ("train_kernel_ms", ctypes.c_double),
+                ("eval_ms", ctypes.c_double), ("cost_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("cluster", ctypes.c_int32), ("levels", ctypes.c_int32)]
+
+
 _fptr = ctypes.POINTER(ctypes.c_float)
 _SIGNATURES = {
     "mlmc_last_error": ([], ctypes.c_char_p),
@@ -111,6 +117,7 @@ _SIGNATURES = {
     "mlmc_cv_train": ([_i32, _pm, _pp, _u64, ctypes.POINTER(mlmc_cv_options), _vp, ctypes.POINTER(_vp)], _i32),
     "mlmc_cv_free": ([_vp], _i32),
     "mlmc_cv_info": ([_vp, _i32, ctypes.POINTER(mlmc_cv_level_info)], _i32),
+    "mlmc_cv_train_info": ([_vp, ctypes.POINTER(mlmc_cv_train_stats)], _i32),
     "mlmc_cv_get_params": ([_vp, _i32, _fptr], _i32),
     "mlmc_cv_set_params": ([_vp, _i32, _fptr, _dbl], _i32),
     "mlmc_cv_level_sums": ([_vp, _i32, _u64, _u64, _u64, _vp, _vp, _vp, _vp], _i32),
@@ -181,7 +188,7 @@ def _launch(launch) -> mlmc_launch | None:
     if isinstance(launch, mlmc_launch):
         return launch
     return mlmc_launch(int(launch.get("threads_per_block", 0)), int(launch.get("lanes_per_path", 0)),
-                       int(launch.get("blocks", 0)), 0)
+                       int(launch.get("blocks", 0)), int(launch.get("samples_per_thread", 0)))
 
 
 def _prec(precision) -> int:
@@ -379,6 +386,12 @@ def mlmc_cv_info(cv: ControlVariate, level: int) -> dict:
     return {name: getattr(info, name) for name, _ in mlmc_cv_level_info._fields_}
 
 
+def mlmc_cv_train_info(cv: ControlVariate) -> dict:
+    st = mlmc_cv_train_stats()
+    _check(_lib.mlmc_cv_train_info(cv.handle, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in mlmc_cv_train_stats._fields_}
+
+
 def mlmc_cv_get_params(cv: ControlVariate, level: int):
     import numpy as np
 
@@ -464,9 +477,9 @@ def mlmc_autotune_entries() -> int:
 
 
 def mlmc_autotune_lookup(precision, payoff: str, M: int, level: int, N: int):
-    """(threads_per_block, lanes_per_path, waves) or None."""
+    """(threads_per_block, lanes_per_path, waves, samples_per_thread) or None."""
     out = mlmc_launch()
     st = _lib.mlmc_autotune_lookup(_prec(precision), PAYOFFS[payoff], M, level, N, ctypes.byref(out))
     if st != MLMC_OK:
         return None
-    return out.threads_per_block, out.lanes_per_path, out.blocks
+    return out.threads_per_block, out.lanes_per_path, out.blocks, out.samples_per_thread

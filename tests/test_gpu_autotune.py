@@ -30,6 +30,7 @@ def test_autotune_then_parity(mlmc, tmp_path):
     for level in range(6):
         shape = mlmc.mlmc_autotune_lookup("fp32", "asian", 4, level, 1 << 16)
         assert shape is not None and shape[0] in (128, 256, 512) and shape[1] in (1, 2, 4, 8, 16, 32)
+        assert shape[3] in (1, 2) and (shape[3] == 1 or (shape[1] == 1 and level >= 1 and shape[0] <= 512))
     p = mlmc.Problem(payoff="asian", **GBM)
     op = oracle_problem(oracle, p)
     for level, N in [(0, 5000), (3, 2000), (5, 600)]:

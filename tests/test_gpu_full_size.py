@@ -163,6 +163,8 @@ TOP_CASES = [
     ("M4_level1_straight_line", 4, 1, dict(payoff="asian"), oracle.MODE_COUPLED),
     ("M4_level3_lookback", 4, 3, dict(payoff="lookback"), oracle.MODE_COUPLED),
     ("M4_level5_split8", 4, 5, dict(payoff="asian"), oracle.MODE_COUPLED),
+    ("M4_level1_ns2", 4, 1, dict(payoff="asian"), oracle.MODE_COUPLED),
+    ("M4_level3_lookback_ns2", 4, 3, dict(payoff="lookback"), oracle.MODE_COUPLED),
     ("antithetic_M4_level2", 4, 2, dict(payoff="asian", estimator="antithetic"), oracle.MODE_ANTITHETIC),
     ("antithetic_M2_level1", 2, 1, dict(payoff="lookback", estimator="antithetic"), oracle.MODE_ANTITHETIC),
 ]
@@ -179,6 +181,10 @@ def test_sample_indices_at_top_of_64_bits(mlmc, name, M, level, fields, mode, pr
     p = mlmc.Problem(**fields, **GBM)
     op = oracle_problem(oracle, p)
     launch = {"lanes_per_path": 8} if name.endswith("split8") else None
+    if name.endswith("ns2"):
+        if precision != "fp32":
+            pytest.skip("two samples per thread: FP32 kernels")
+        launch = {"lanes_per_path": 1, "samples_per_thread": 2}
     sums, y = run_level(mlmc, level, M, N, first, p, seed, precision, launch=launch)
     yo = oracle.level_samples(level, M, N, op, seed=seed, first=first, stream=precision, mode=mode)
     assert np.all(np.isfinite(y))
@@ -205,16 +211,20 @@ def test_quintic_sample_indices_at_top_of_64_bits(mlmc, level, first, N):
 
 @pytest.mark.parametrize("estimator,mode", [("coupled", oracle.MODE_COUPLED), ("antithetic", oracle.MODE_ANTITHETIC)])
 @pytest.mark.parametrize("scheme", ["em", "milstein"])
-@pytest.mark.parametrize("M,level,lanes", [(4, 7, 1), (2, 13, 1), (4, 8, 2), (2, 14, 4)])
+@pytest.mark.parametrize("M,level,lanes", [(4, 7, 1), (2, 13, 1), (4, 8, 2), (2, 14, 4), (4, 7, -2), (2, 13, -2)])
 def test_long_lane_kernels(mlmc, M, level, lanes, scheme, estimator, mode):
     """Lanes of more than 4096 steps take the FP32 arithmetic-Asian kernels that add the running
-    sum in partials of 256 steps (one thread per path, and split paths)."""
-    if estimator == "antithetic" and lanes > 1:
-        pytest.skip("the antithetic estimator runs one thread per path")
+    sum in partials of 256 steps (one thread per path, and split paths; lanes = -2: one thread
+    per path, two samples per thread)."""
+    if estimator == "antithetic" and lanes != 1:
+        pytest.skip("the antithetic estimator runs one thread per path, one sample per thread")
+    if lanes == -2 and scheme != "em":
+        pytest.skip("two samples per thread: Euler--Maruyama kernels")
     N, first, seed = 67, 2 ** 40 + 1, 5
     p = mlmc.Problem(payoff="asian", scheme=scheme, estimator=estimator, **GBM)
     op = oracle_problem(oracle, p)
-    launch = {"lanes_per_path": lanes} if lanes > 1 else {"lanes_per_path": 1}
+    launch = ({"lanes_per_path": lanes} if lanes > 1 else
+              {"lanes_per_path": 1, "samples_per_thread": 2} if lanes == -2 else {"lanes_per_path": 1})
     sums, y = run_level(mlmc, level, M, N, first, p, seed, "fp32", launch=launch)
     yo = oracle.level_samples(level, M, N, op, seed=seed, first=first, stream="fp32", mode=mode)
     assert np.max(np.abs(y - yo)) <= _bound("fp32", level, M)

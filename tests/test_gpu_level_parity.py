@@ -121,6 +121,53 @@ def test_other_refinement_factors(mlmc, M, level, N, lanes, payoff, precision):
     _check_level(mlmc, level, M, N, 3, payoff, precision, launch={"lanes_per_path": lanes})
 
 
+@pytest.mark.parametrize("payoff", PAYOFFS)
+@pytest.mark.parametrize("M,level,N,first", [(4, 1, 20011, 977), (4, 2, 8191, 5), (4, 3, 4001, 123456789),
+                                             (4, 5, 1201, 2 ** 33 + 3), (4, 6, 601, 11), (4, 7, 257, 0),
+                                             (2, 2, 5001, 3), (2, 5, 2001, 3), (8, 2, 2001, 3)])
+def test_two_samples_per_thread_match_oracle(mlmc, M, level, N, first, payoff):
+    """The two-samples-per-thread kernels (FP32 Euler--Maruyama, one thread per sample) step two
+    samples in lockstep: every sample against the oracle, ragged tails (odd N, so a thread's
+    second sample runs past the range and is dropped) included."""
+    _check_level(mlmc, level, M, N, first, payoff, "fp32",
+                 launch={"lanes_per_path": 1, "samples_per_thread": 2, "threads_per_block": 256})
+
+
+@pytest.mark.parametrize("threads,blocks,spt", [(32, 1, 2), (64, 3, 2), (512, 0, 2), (96, 5, 2)])
+def test_two_samples_per_thread_launch_shapes(mlmc, threads, blocks, spt):
+    """Grid strides of the two-sample loop: any grid gives the samples of the one-sample kernel,
+    and sums equal to the sums of its own samples."""
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    ref_sums, ref_y = run_level(mlmc, 3, 4, 5003, 1, p, 9, "fp32", launch={"samples_per_thread": 1})
+    sums, y = run_level(mlmc, 3, 4, 5003, 1, p, 9, "fp32",
+                        launch={"threads_per_block": threads, "blocks": blocks, "samples_per_thread": spt})
+    assert np.max(np.abs(y - ref_y)) <= _bound("fp32", 3, 4, p)
+    own = moment_sums(y)
+    for k in range(4):
+        assert abs(sums[k] - own[k]) <= 32 * U["fp32"] * np.sum(np.abs(y) ** (k + 1)), k
+
+
+def test_two_samples_per_thread_rejected_where_not_built(mlmc):
+    """samples_per_thread = 2 exists for FP32 Euler--Maruyama whole paths only."""
+    import torch
+
+    d = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ws_bytes = mlmc.mlmc_level_workspace_bytes(3, 4, 100, "fp32", None)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
+    for prob, level, prec, launch in [
+        (mlmc.Problem(payoff="asian", **GBM), 3, "fp64", {"samples_per_thread": 2}),
+        (mlmc.Problem(payoff="asian", scheme="milstein", **GBM), 3, "fp32", {"samples_per_thread": 2}),
+        (mlmc.Problem(payoff="asian", **GBM), 0, "fp32", {"samples_per_thread": 2}),
+        (mlmc.Problem(payoff="asian", **GBM), 5, "fp32", {"samples_per_thread": 2, "lanes_per_path": 4}),
+        (mlmc.Problem(payoff="asian", **GBM), 3, "fp32", {"samples_per_thread": 2, "threads_per_block": 1024}),
+        (mlmc.Problem(payoff="asian", estimator="antithetic", **GBM), 3, "fp32", {"samples_per_thread": 2}),
+        (mlmc.Problem(payoff="asian", **GBM), 3, "fp32", {"samples_per_thread": 3}),
+    ]:
+        with pytest.raises(mlmc.MLMCError) as ei:
+            mlmc.mlmc_level_sums_async(level, 4, 100, 0, prob, 1, d, ws, ws_bytes, precision=prec, launch=launch)
+        assert ei.value.status == mlmc.MLMC_EINVAL
+
+
 @pytest.mark.parametrize("threads,blocks", [(32, 1), (64, 3), (1024, 0), (256, 7)])
 def test_launch_shapes_agree(mlmc, threads, blocks):
     """Grid-stride loops and the two-stage reduction: any launch shape gives the same samples
@@ -219,14 +266,16 @@ def test_milstein_matches_oracle(mlmc, M, level, N, lanes, payoff, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("level,lanes", [(0, 1), (2, 1), (4, 1), (5, 8)])
-def test_single_level_estimator_matches_oracle(mlmc, level, lanes, precision):
+@pytest.mark.parametrize("level,lanes,spt", [(0, 1, 0), (2, 1, 0), (4, 1, 0), (5, 8, 0), (1, 1, 2), (4, 1, 2)])
+def test_single_level_estimator_matches_oracle(mlmc, level, lanes, spt, precision):
     """The single-level estimator P_l (standard Monte Carlo, Sec. 3) against the oracle's
-    fine-only mode."""
+    fine-only mode (spt = 2: the two-samples-per-thread kernels, FP32 only)."""
+    if spt == 2 and precision != "fp32":
+        pytest.skip("two samples per thread: FP32 kernels")
     p = mlmc.Problem(payoff="asian", estimator="single", **GBM)
     op = oracle_problem(oracle, p)
     N = 1201
-    sums, y = run_level(mlmc, level, 4, N, 3, p, 5, precision, launch={"lanes_per_path": lanes})
+    sums, y = run_level(mlmc, level, 4, N, 3, p, 5, precision, launch={"lanes_per_path": lanes, "samples_per_thread": spt})
     yo = oracle.level_samples(level, 4, N, op, seed=5, first=3, stream=precision, mode=oracle.MODE_FINE_ONLY)
     assert np.max(np.abs(y - yo)) <= _bound(precision, level, 4, p)
 
