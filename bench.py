@@ -91,6 +91,13 @@ def parse_clock_lines(lines: list[str]) -> dict:
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def bias_estimate(mean: list, alpha: float, m: int = M) -> float:
+    """The driver's bias estimate on the finest two levels, max(|m_L|, |m_{L-1}| / M^alpha) /
+    (M^alpha - 1) (Theorem of Sec. 5: the estimate's bias is what MSE < eps^2 leaves to it)."""
+    ma = m ** max(alpha, 0.5)
+    return max(abs(mean[-1]), abs(mean[-2]) / ma) / (ma - 1.0)
+
+
 def combine_over_ranks(dev_s: float, wall_s: float, steps: float, launches: float, group=None) -> tuple:
     """Max of the times and sum of the work over ranks (identity without a process group)."""
     import torch
@@ -127,10 +134,17 @@ def _oracle_job(args):
 TRAFFIC_BYTES_PER_LAUNCH = 52992
 TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one level_kernel launch (lookback, "
                  "level 6, N=1e6, 608 blocks); algorithmic bytes 19.5 KB of block partials")
+# FP64 instructions (DFMA + DADD + DMUL, thread level) per coupled step of the FP64 Asian kernel, from
+# ncu's per-opcode counters on one launch (level 6, N = 1e5, one thread per sample).
+FP64_INSTR_PER_STEP = 36.51
+FP64_INSTR_BASIS = ("ncu smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on of one level_kernel<double> "
+                    "launch (Asian, level 6, N=1e5): 20.76 + 8.26 + 7.50 per coupled step; deeper and shallower "
+                    "levels differ by their per-sample share")
 
-ORACLE_SAMPLE = dict(eps=2e-2, seeds=(1, 2, 3, 4))
+ORACLE_SAMPLE = dict(eps=2e-2, seeds=tuple(range(1, 9)))
 ORACLE_SAMPLE_TEXT = ("oracle adaptive MLMC of the same two options and model at eps=2e-2 (not 1e-3), "
-                      "seeds 1..4, FP32 stream; estimates run in parallel processes")
+                      "seeds 1..8 (16 estimates), FP32 stream; estimates run in parallel processes, one per "
+                      "host core")
 
 
 def run_oracle_sample(pool_size: int) -> tuple[float, float, int, float]:
@@ -259,9 +273,16 @@ def side_workloads(mlmc, stream) -> dict:
         anti[p] = statistics.median(times)
     out["antithetic_time_to_eps_ms"] = anti
     prob = mlmc.Problem(payoff="asian", cash=1.0, **GBM)
+    # trained twice: the first call also loads the control-variate kernels (lazy module loading);
+    # the second is the cost of training a further problem in a running process
+    t = time.perf_counter()
+    cv = mlmc.mlmc_cv_train(M, prob, seed=2024, levels=4, epochs=20, n_train=1_000_000, stream=stream)
+    train_s_first = time.perf_counter() - t
+    mlmc.mlmc_cv_free(cv)
     t = time.perf_counter()
     cv = mlmc.mlmc_cv_train(M, prob, seed=2024, levels=4, epochs=20, n_train=1_000_000, stream=stream)
     train_s = time.perf_counter() - t
+    train_info = mlmc.mlmc_cv_train_info(cv)
     levels = []
     for l in range(4):
         i = mlmc.mlmc_cv_info(cv, l)
@@ -272,12 +293,27 @@ def side_workloads(mlmc, stream) -> dict:
                        "used": bool(i["used"]), "ns_per_sample_plain": 1e9 * i["t_plain"],
                        "ns_per_sample_cv": 1e9 * i["t_cv"], "ns_per_lattice_point": 1e9 * i["t_mean"]})
     eps_cv = 5e-4
-    a = mlmc.mlmc_estimate_cv(eps_cv, cv, 1, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
-    b = mlmc.mlmc_estimate(eps_cv, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)
-    c = mlmc.mlmc_estimate(eps_cv, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64", stream=stream)
-    out["learned_cv"] = {"payoff": "asian", "train_s": train_s, "levels": levels, "eps": eps_cv,
-                         "time_to_eps_ms": {"fp32_cv": a.wall_ms, "fp32_plain": b.wall_ms, "fp64_plain": c.wall_ms},
-                         "estimate": {"fp32_cv": a.P, "fp32_plain": b.P, "fp64_plain": c.P}}
+    seeds = range(1, 9)
+    mlmc.mlmc_estimate_cv(eps_cv, cv, 1, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)  # warm-up
+    a = [mlmc.mlmc_estimate_cv(eps_cv, cv, s, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream) for s in seeds]
+    b = [mlmc.mlmc_estimate(eps_cv, prob, s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream) for s in seeds]
+    c = [mlmc.mlmc_estimate(eps_cv, prob, s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64", stream=stream)
+         for s in seeds]
+    med = lambda rs: statistics.median(r.wall_ms for r in rs)
+    cv_ms, plain_ms, fp64_ms = med(a), med(b), med(c)
+    saving = plain_ms - cv_ms
+    out["learned_cv"] = {
+        "payoff": "asian", "train_s": train_s, "train_s_first_call": train_s_first,
+        "training": {k: train_info[k] for k in ("data_ms", "train_ms", "train_kernel_ms", "eval_ms", "cost_ms",
+                                                "total_ms", "steps", "cluster", "levels")},
+        "levels": levels, "eps": eps_cv, "seeds": "1..8 (medians)",
+        "time_to_eps_ms": {"fp32_cv": cv_ms, "fp32_plain": plain_ms, "fp64_plain": fp64_ms,
+                           "fp32_cv_with_training": cv_ms + 1e3 * train_s},
+        # estimates after which training has paid for itself: training time / saving per estimate
+        "break_even_estimates": (1e3 * train_s / saving) if saving > 0 else None,
+        "estimate_median": {"fp32_cv": statistics.median(r.P for r in a),
+                            "fp32_plain": statistics.median(r.P for r in b),
+                            "fp64_plain": statistics.median(r.P for r in c)}}
     mlmc.mlmc_cv_free(cv)
     return out
 
@@ -368,6 +404,7 @@ def gpu_arm(args) -> None:
                 "kernel_path_steps_per_s": steps / (kern_ms / 1e3)}
     # SFU: two hardware approximations per normal (log2 and sqrt per pair, sine and cosine per
     # pair), one normal per fine step, against the MUFU throughput the build's own probe measures
+    probe = {}
     try:
         from paper_1505_00965_gb300 import peaks as peak_probe
 
@@ -379,10 +416,25 @@ def gpu_arm(args) -> None:
     except Exception as exc:  # the probe is a report; the benchmark line stands without it
         roofline["sfu"] = {"unavailable": str(exc)[:200]}
 
-    # plain FP64 GPU MLMC on the same GPU, same eps (outside the timed region; Asian, first seed)
-    fp64 = mlmc.mlmc_estimate(EPS, problems["asian"], seeds[0], M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64",
-                              stream=stream)
-    fp32_asian_median = statistics.median(tte["asian"][:len(seeds)])
+    # plain FP64 GPU MLMC on the same GPU, same eps (outside the timed region; Asian, the rank's
+    # eight seeds, median as for FP32), and its kernels against the FP64 pipe's measured rate
+    fp64_runs = [mlmc.mlmc_estimate(EPS, problems["asian"], s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, precision="fp64",
+                                    stream=stream) for s in seeds]
+    fp64_ms = statistics.median(r.wall_ms for r in fp64_runs)
+    fp32_asian_median = statistics.median(tte["asian"])
+    fp64_steps = sum(r.path_steps for r in fp64_runs)
+    fp64_kern_s = sum(r.kernel_ms for r in fp64_runs) / 1e3
+    roofline_fp64 = {"bound": "fp64", "kernel": "level_kernel<double> and level_small_kernel<double> (FP64 paths, "
+                                                "Asian, all levels of the eight estimates)",
+                     "path_steps_per_s": fp64_steps / fp64_kern_s, "unit": "FP64 instructions/s",
+                     "fp64_instructions_per_step": FP64_INSTR_PER_STEP, "fp64_instructions_basis": FP64_INSTR_BASIS}
+    try:
+        achieved64 = FP64_INSTR_PER_STEP * fp64_steps / fp64_kern_s
+        roofline_fp64.update({"achieved": achieved64, "peak": probe["dfma_per_s"], "frac": achieved64 / probe["dfma_per_s"],
+                              "peak_basis": f"probe_peaks.cu: {probe['dfma_per_sm_per_clk']:.3f} FP64 FMA per SM "
+                                            "per clock (one FP64 instruction per operation)"})
+    except Exception as exc:
+        roofline_fp64["unavailable"] = str(exc)[:200]
     extras = {} if args.no_extras else side_workloads(mlmc, stream)
     value = steps_all / dev_s
     line = {
@@ -393,10 +445,17 @@ def gpu_arm(args) -> None:
                    "seeds_per_gpu": SEEDS_PER_RANK, "precision": "FP32 paths, FP64 moment sums",
                    "l2": "512 MiB buffer written before every timed step, outside its events (the kernels read "
                          "no input arrays; they are compute bound)"},
-        "time_to_eps_ms": {p: statistics.median(v) for p, v in tte.items()},
+        # the Asian estimates converge (bias test passed, MSE <= eps^2): time-to-eps
+        "time_to_eps_ms": {"asian": fp32_asian_median},
+        # the lookback estimates stop at L = Lmax with the bias test failing (discretely monitored
+        # maximum, weak order 1/2): the time to run to Lmax and the bias left there
+        "lookback_time_to_Lmax_ms": statistics.median(tte["lookback"]),
+        "lookback_bias_estimate_at_Lmax": statistics.median(
+            bias_estimate(r.mean, r.alpha) for q, r in last if q == "lookback"),
         "converged_fraction": {p: sum(v) / len(v) for p, v in conv.items()},
-        "fp64_gpu_time_to_eps_ms": {"asian": fp64.wall_ms},
-        "fp64_vs_fp32_time_to_eps": {"asian": fp64.wall_ms / fp32_asian_median},
+        "fp64_gpu_time_to_eps_ms": {"asian": fp64_ms, "seeds": "1..8 (median)"},
+        "fp64_vs_fp32_time_to_eps": {"asian": fp64_ms / fp32_asian_median},
+        "roofline_fp64": roofline_fp64,
         "estimates": {p: [r.P for q, r in last if q == p] for p in PAYOFFS},
         "gpu_launches": int(launches_all),
         "e2e": {"value": steps_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -429,6 +488,38 @@ def case_arm(args) -> None:
     reps, warm = int(c.get("reps", 3)), int(c.get("warmup", 1))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if "train" in c:
+        # the control variate's training launch: levels 0..train-1 of the Asian call
+        prob = mlmc.Problem(payoff="asian", **GBM)
+        for _ in range(max(reps, 1)):
+            cv = mlmc.mlmc_cv_train(m, prob, seed=2024, levels=int(c["train"]), epochs=int(c.get("epochs", 20)),
+                                    n_train=int(float(c.get("n_train", 1e6))), stream=stream)
+            info = mlmc.mlmc_cv_train_info(cv)
+            print(f"case {args.case}: training kernel {info['train_kernel_ms']:.3f} ms for {info['steps']} steps "
+                  f"({1e3 * info['train_kernel_ms'] / max(info['steps'], 1):.2f} us per step), cluster "
+                  f"{info['cluster']}, mlmc_cv_train {info['total_ms']:.1f} ms")
+            mlmc.mlmc_cv_free(cv)
+        return
+    if "cv_level" in c:
+        # the control-variate level kernel on a seeded random network (Asian call)
+        import numpy as np
+
+        lv = int(c["cv_level"])
+        cv = mlmc.mlmc_cv_create(m, mlmc.Problem(payoff="asian", **GBM))
+        theta = (np.random.default_rng(1).standard_normal(mlmc.MLMC_CV_PARAMS) * 0.2).astype(np.float32)
+        mlmc.mlmc_cv_set_params(cv, lv, theta)
+        d = torch.zeros(8, dtype=torch.float64, device="cuda")
+        for _ in range(warm):
+            mlmc.mlmc_cv_level_sums(cv, lv, n, 0, 1, d, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            mlmc.mlmc_cv_level_sums(cv, lv, n, 0, 1, d, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(reps, 1)
+        print(f"case {args.case}: {ms:.4f} ms per call (synchronising), {ms * 1e6 / n:.4f} ns per sample")
+        mlmc.mlmc_cv_free(cv)
+        return
     if "cv_mean" in c:
         import numpy as np
 
