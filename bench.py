@@ -343,6 +343,40 @@ def gpu_arm(args) -> None:
         return out
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    # launch shapes: the autotuner's table (threads per block, lanes per path, samples per thread
+    # and grid waves, measured per level and size class), made before the warm-up steps
+    tuning = {"table": "planner"}
+    if not args.no_autotune:
+        import tempfile
+
+        t = time.perf_counter()
+        mlmc.mlmc_autotune_clear()
+        for p in PAYOFFS:
+            mlmc.mlmc_autotune(M=M, max_level=LMAX, precision="fp32", payoff=p, stream=stream)
+        tuning = {"tune_s": time.perf_counter() - t, "entries": mlmc.mlmc_autotune_entries()}
+        with tempfile.TemporaryDirectory() as tmp:
+            path = os.path.join(tmp, "tuned.json")
+            mlmc.mlmc_autotune_save(path)
+            # one untimed step on each table, twice in turn (the faster of each kept)
+            shape_ms = {"planner": [], "autotuned": []}
+            for _ in range(2):
+                for which in ("planner", "autotuned"):
+                    mlmc.mlmc_autotune_clear()
+                    if which == "autotuned":
+                        mlmc.mlmc_autotune_load(path)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    one_step()
+                    torch.cuda.synchronize()
+                    shape_ms[which].append(1e3 * (time.perf_counter() - t0))
+            tuning["step_ms"] = {k: min(v) for k, v in shape_ms.items()}
+            # the timed steps run on the table that ran the untimed step faster
+            mlmc.mlmc_autotune_clear()
+            if tuning["step_ms"]["autotuned"] < tuning["step_ms"]["planner"]:
+                mlmc.mlmc_autotune_load(path)
+                tuning["table"] = "autotuned"
+            else:
+                tuning["table"] = "planner (the autotuned table ran the step slower)"
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
@@ -458,6 +492,7 @@ def gpu_arm(args) -> None:
         "roofline_fp64": roofline_fp64,
         "estimates": {p: [r.P for q, r in last if q == p] for p in PAYOFFS},
         "gpu_launches": int(launches_all),
+        "launch_shapes": tuning,
         "e2e": {"value": steps_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h / args.steps),
                 "note": "mlmc_estimate through the C ABI: arguments by value (kernel parameters), results "
@@ -572,6 +607,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and control-variate reports")
+    ap.add_argument("--no-autotune", action="store_true", help="time the planner's launch shapes, not a tuned table")
     ap.add_argument("--case", default="", metavar="K=V,...",
                     help="time one kernel instead: level, M, N, payoff, kind, scheme, precision, "
                          "lanes_per_path, threads_per_block, blocks, samples_per_thread, reps, warmup; "

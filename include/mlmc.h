@@ -206,8 +206,16 @@ int mlmc_level_sums_async(int level, int M, uint64_t N, uint64_t first,
  * exits.
  *   Arguments as mlmc_level_sums_async, without the workspace.  d_sums (device, 4 doubles)
  *   is overwritten; d_y (device or NULL) receives Y per sample.
+ *   A grid that the planner sizes above 2048 blocks (small blocks on a large range) is cut
+ *   to 2048 blocks, each striding over more samples: the samples and d_y are those of
+ *   mlmc_level_sums_async, and the sums equal its sums bit for bit only when its grid has at
+ *   most 2048 blocks; otherwise they add the same samples in another order (FP32 batches of
+ *   32 and block partials), within the oracle tolerances of both.
  *   The first call on each device looks up the array's device address (with that device
- *   current) and caches it; make that first call before any stream capture.
+ *   current) and caches it; make that first call before any stream capture.  mlmc_shutdown
+ *   forgets the cached address of the current device: call it before resetting the device
+ *   (a reset or a new primary context moves the array), so that the next call looks it up
+ *   again.
  *   All calls share the one array: each call clears the completion word on `stream` before
  *   its launch, and calls whose work overlaps on the GPU (different streams, or different
  *   host threads without ordering) race on it.
@@ -295,6 +303,30 @@ typedef struct mlmc_problem {
  */
 int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, int Lmin, int Lmax, uint64_t N0,
                         int precision, void *stream, mlmc_result *results);
+
+/* One level range of a batch: samples [first, first + N) of `level` of one problem (its eps is
+ * not used). */
+typedef struct mlmc_level_task {
+    mlmc_problem problem;
+    int32_t level;
+    int32_t reserved;                /* must be 0 */
+    uint64_t first, N;               /* N at most 2^32 - 1 */
+} mlmc_level_task;
+
+/*
+ * mlmc_level_sums_batch -- the level estimator (Sec. 5, Eq. Yldef; Eq. mlmc:Yzero at l = 0) for
+ * n ranges at once, through the batched driver's own round: the same chunk list of about equal
+ * work, persistent kernel and fixed-order per-task reduction as one round of
+ * mlmc_estimate_batch (launched directly, not from a graph).
+ *   tasks host [n]; M and precision (MLMC_FP64 or MLMC_FP32_PATH) shared by all tasks.
+ *   sums host [n][4]: sum Y^k, k = 1..4, of each task's samples (zeros for N = 0).
+ *   d_y device or NULL: if not NULL, Y of every sample, task after task in order (sum of N
+ *   doubles); deep levels split paths over lanes as the batched rounds do, so Y carries that
+ *   split's roundoff.  Synchronises `stream`.
+ * GBM problems with the coupled Euler--Maruyama estimator only.  Errors as mlmc_estimate_batch.
+ */
+int mlmc_level_sums_batch(int n, const mlmc_level_task *tasks, int M, int precision, double *sums,
+                          double *d_y, void *stream);
 
 /*
  * ---------------------------------------------------------------- learned control variate
@@ -460,7 +492,9 @@ int mlmc_autotune_lookup(int precision, int payoff, int M, int level, uint64_t N
 /* Number of streaming multiprocessors of the current device, or -1 with an error message. */
 int mlmc_device_sm_count(void);
 
-/* Release every device resource the library holds on the current device. */
+/* Release every device resource the library holds on the current device (the adaptive drivers'
+ * pooled buffers) and forget the cached address of the allocation-free entry point's scratch.
+ * Call it before cudaDeviceReset or any other teardown of the device's primary context. */
 int mlmc_shutdown(void);
 
 #ifdef __cplusplus

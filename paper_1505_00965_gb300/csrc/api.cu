@@ -392,6 +392,18 @@ int launch_level(const Plan &plan, LevelParams &p, void *ws, cudaStream_t st)
 
 namespace mlmcgb {
 
+// Cached device address of the allocation-free entry point's scratch, per device (looked up on
+// first use; cleared by mlmc_shutdown, since a device reset moves the array).
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_ptr[kMaxDevices] = {};
+static void noalloc_forget(int dev)
+{
+    if (dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    g_noalloc_ptr[dev] = nullptr;
+}
+
 // Device buffers of the adaptive drivers (workspace, level sums, pinned host copy, timing
 // events), kept between calls in a per-device pool: allocating and pinning them on every call
 // cost more than the kernels of a small estimate.  A call takes a set from the pool (or makes
@@ -479,6 +491,7 @@ int mlmc_shutdown(void)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
+    noalloc_forget(dev);
     CUDA_TRY(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lock(g_pool_mutex);
     for (size_t i = 0; i < g_pool.size();) {
@@ -549,9 +562,6 @@ constexpr int kNoAllocMaxBlocks = 2048;
 constexpr size_t kNoAllocScratchBytes = kTicketBytes + (size_t)kNoAllocMaxBlocks * 4 * sizeof(double);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device.  In host code the array's name
 // only stands in for the symbol, so the address is looked up once per device, with that device

@@ -126,7 +126,73 @@ struct BatchBuffers {
         CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
         return MLMC_OK;
     }
+
+    // The same round as direct launches (upload, kernel, reduction, download of n_tasks sums).
+    int launch_direct(cudaStream_t st, const void *kernel, int blocks, size_t n_tasks)
+    {
+        const LevelParams *d_tasks = (const LevelParams *)(d_stage + off_tasks);
+        const BatchChunk *d_chunks = (const BatchChunk *)(d_stage + off_chunks);
+        const BatchRange *d_ranges = (const BatchRange *)(d_stage + off_ranges);
+        const BatchHeader *d_header = (const BatchHeader *)d_stage;
+        CUDA_TRY(cudaMemcpyAsync(d_stage, h_stage, stage_bytes, cudaMemcpyHostToDevice, st));
+        void *kargs[] = {(void *)&d_tasks, (void *)&d_chunks, (void *)&d_header, (void *)&d_counter,
+                         (void *)&d_chunk_sums};
+        CUDA_TRY(cudaLaunchKernel(kernel, dim3(blocks), dim3(kBatchThreads), kargs, 0, st));
+        void *rargs[] = {(void *)&d_ranges, (void *)&d_header, (void *)&d_chunk_sums, (void *)&d_task_sums,
+                         (void *)&d_counter};
+        CUDA_TRY(cudaLaunchKernel(batch_reduce_kernel(), dim3((unsigned)((n_tasks + 255) / 256)), dim3(256), rargs, 0,
+                                  st));
+        CUDA_TRY(cudaMemcpyAsync(h_task_sums, d_task_sums, n_tasks * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return MLMC_OK;
+    }
 };
+
+// Fine steps per chunk of a round with `total` fine steps of new work: about four chunks per
+// resident block, at least 2^14 and at most 2^22 steps.
+double chunk_steps(double total, int blocks)
+{
+    return std::min(std::max(total / (4.0 * blocks), 16384.0), 4194304.0);
+}
+
+// Append one task (samples [first, first + N) of `level` of one problem) and its chunks of about
+// W fine steps to a round.  y_out (device or NULL) receives Y of the task's samples in order.
+void add_task(std::vector<LevelParams> &tasks, std::vector<BatchChunk> &chunks, std::vector<BatchRange> &ranges,
+              const mlmc_problem &pr, int level, int M, uint64_t first, uint64_t N, double W, int precision,
+              double *y_out)
+{
+    const long nf = ipow(M, level);
+    const uint64_t spc = (uint64_t)std::max(1.0, std::floor(W / (double)nf));
+    LevelParams p;
+    fill_params(p, level, M, N, first, &pr.model, &pr.payoff, pr.seed, MLMC_TAG_PATHS, batch_lanes(nf, M, spc),
+                precision);
+    p.y_out = y_out;
+    BatchRange r;
+    r.begin = (uint32_t)chunks.size();
+    for (uint64_t off = 0; off < N; off += spc) {
+        BatchChunk c;
+        c.first = first + off;
+        c.task = (uint32_t)tasks.size();
+        c.count = (uint32_t)std::min<uint64_t>(spc, N - off);
+        chunks.push_back(c);
+    }
+    r.end = (uint32_t)chunks.size();
+    ranges.push_back(r);
+    tasks.push_back(p);
+}
+
+// Checks shared by the batched entry points: GBM, the coupled Euler--Maruyama estimator.
+int check_batch_problem(const mlmc_problem &pr, int i)
+{
+    int rc = check_problem(&pr.model, &pr.payoff);
+    if (!rc && pr.model.kind != MLMC_MODEL_GBM) rc = fail(MLMC_ENOTIMPL, "batches run GBM problems");
+    if (!rc && (pr.model.scheme != MLMC_EULER_MARUYAMA || pr.payoff.estimator != MLMC_COUPLED))
+        rc = fail(MLMC_EINVAL, "batches run the coupled Euler--Maruyama estimator");
+    if (rc) {
+        std::string msg = mlmc_last_error();
+        return fail(rc, "problem %d: %s", i, msg.c_str());
+    }
+    return MLMC_OK;
+}
 
 }  // namespace
 }  // namespace mlmcgb
@@ -142,17 +208,10 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
     if (rc) return rc;
     if (precision == MLMC_FP64_STREAM32) return fail(MLMC_EINVAL, "batches run MLMC_FP64 or MLMC_FP32_PATH");
     for (int i = 0; i < n; ++i) {
-        rc = check_problem(&problems[i].model, &problems[i].payoff);
-        if (!rc && problems[i].model.kind != MLMC_MODEL_GBM)
-            rc = fail(MLMC_ENOTIMPL, "batches run GBM problems");
-        if (!rc && (problems[i].model.scheme != MLMC_EULER_MARUYAMA || problems[i].payoff.estimator != MLMC_COUPLED))
-            rc = fail(MLMC_EINVAL, "batches run the coupled Euler--Maruyama estimator");
+        rc = check_batch_problem(problems[i], i);
         if (!rc && !(problems[i].eps > 0 && std::isfinite(problems[i].eps)))
-            rc = fail(MLMC_EINVAL, "eps must be positive and finite");
-        if (rc) {
-            std::string msg = mlmc_last_error();
-            return fail(rc, "problem %d: %s", i, msg.c_str());
-        }
+            rc = fail(MLMC_EINVAL, "problem %d: eps must be positive and finite", i);
+        if (rc) return rc;
     }
     const int mt = M == 4 ? 4 : 0;
     const void *kernel = precision == MLMC_FP32_PATH ? batch_kernel_fp32(mt) : batch_kernel_fp64(mt);
@@ -207,29 +266,14 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
             for (int l = 0; l <= drv[i].finest_level(); ++l) total += (double)dN[l] * (double)ipow(M, l);
         }
         if (total == 0.0) break;
-        const double W = std::min(std::max(total / (4.0 * blocks), 16384.0), 4194304.0);
+        const double W = chunk_steps(total, blocks);
         for (int i = 0; i < n; ++i) {
             if (!drv[i].active()) continue;
             const std::vector<uint64_t> &dN = drv[i].next_samples();
             for (int l = 0; l <= drv[i].finest_level(); ++l) {
                 if (!dN[l]) continue;
-                const long nf = ipow(M, l);
-                const uint64_t spc = (uint64_t)std::max(1.0, std::floor(W / (double)nf));
-                LevelParams p;
-                fill_params(p, l, M, dN[l], drv[i].samples_taken(l), &problems[i].model, &problems[i].payoff,
-                            problems[i].seed, MLMC_TAG_PATHS, batch_lanes(nf, M, spc), precision);
-                BatchRange r;
-                r.begin = (uint32_t)chunks.size();
-                for (uint64_t off = 0; off < dN[l]; off += spc) {
-                    BatchChunk c;
-                    c.first = p.first + off;
-                    c.task = (uint32_t)tasks.size();
-                    c.count = (uint32_t)std::min<uint64_t>(spc, dN[l] - off);
-                    chunks.push_back(c);
-                }
-                r.end = (uint32_t)chunks.size();
-                ranges.push_back(r);
-                tasks.push_back(p);
+                add_task(tasks, chunks, ranges, problems[i], l, M, drv[i].samples_taken(l), dN[l], W, precision,
+                         nullptr);
                 refs.push_back({i, l});
             }
         }
@@ -286,4 +330,67 @@ extern "C" int mlmc_estimate_batch(int n, const mlmc_problem *problems, int M, i
         return MLMC_ENOTCONV;
     }
     return MLMC_OK;
+}
+
+extern "C" int mlmc_level_sums_batch(int n, const mlmc_level_task *tasks, int M, int precision, double *sums,
+                                     double *d_y, void *stream)
+{
+    if (n < 1 || !tasks || !sums) return fail(MLMC_EINVAL, "need n >= 1 and non-NULL tasks and sums");
+    if (M != 2 && M != 4 && M != 8) return fail(MLMC_EINVAL, "M must be 2, 4 or 8");
+    if (precision != MLMC_FP64 && precision != MLMC_FP32_PATH)
+        return fail(MLMC_EINVAL, "batches run MLMC_FP64 or MLMC_FP32_PATH");
+    int rc = MLMC_OK;
+    double total = 0.0;
+    uint64_t n_y = 0;
+    for (int i = 0; i < n; ++i) {
+        rc = check_batch_problem(tasks[i].problem, i);
+        if (!rc) rc = check_level(tasks[i].level, M);
+        if (!rc && tasks[i].reserved != 0) rc = fail(MLMC_EINVAL, "task %d: reserved must be 0", i);
+        if (!rc && tasks[i].first + tasks[i].N < tasks[i].first) rc = fail(MLMC_EINVAL, "task %d: first + N overflows", i);
+        if (!rc && tasks[i].N > 0xFFFFFFFFull) rc = fail(MLMC_EINVAL, "task %d: N above 2^32 - 1", i);
+        if (rc) return rc;
+        total += (double)tasks[i].N * (double)ipow(M, tasks[i].level);
+        n_y += tasks[i].N;
+    }
+    const int mt = M == 4 ? 4 : 0;
+    const void *kernel = precision == MLMC_FP32_PATH ? batch_kernel_fp32(mt) : batch_kernel_fp64(mt);
+    int blocks = 0;
+    rc = max_resident_blocks(kernel, kBatchThreads, &blocks);
+    if (rc) return rc;
+    std::vector<LevelParams> lp;
+    std::vector<BatchChunk> chunks;
+    std::vector<BatchRange> ranges;
+    const double W = chunk_steps(total, blocks);
+    uint64_t y_off = 0;
+    std::vector<int> real;  // tasks with samples, in order
+    for (int i = 0; i < n; ++i) {
+        if (tasks[i].N == 0) continue;
+        add_task(lp, chunks, ranges, tasks[i].problem, tasks[i].level, M, tasks[i].first, tasks[i].N, W, precision,
+                 d_y ? d_y + y_off : nullptr);
+        y_off += tasks[i].N;
+        real.push_back(i);
+    }
+    std::memset(sums, 0, sizeof(double) * 4 * (size_t)n);
+    (void)n_y;
+    if (real.empty()) return MLMC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchBuffers buf;
+    rc = buf.reserve(lp.size(), chunks.size());
+    if (!rc) {
+        buf.header()->n_tasks = (uint32_t)lp.size();
+        buf.header()->n_chunks = (uint32_t)chunks.size();
+        std::memcpy(buf.ranges(), ranges.data(), ranges.size() * sizeof(BatchRange));
+        std::memcpy(buf.tasks(), lp.data(), lp.size() * sizeof(LevelParams));
+        std::memcpy(buf.chunks(), chunks.data(), chunks.size() * sizeof(BatchChunk));
+        rc = buf.launch_direct(st, kernel, blocks, lp.size());
+    }
+    if (!rc) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(MLMC_ECUDA, "batched level sums failed: %s", cudaGetErrorString(e));
+    }
+    if (!rc)
+        for (size_t t = 0; t < real.size(); ++t)
+            for (int k = 0; k < 4; ++k) sums[4 * real[t] + k] = buf.h_task_sums[4 * t + k];
+    buf.release();
+    return rc;
 }

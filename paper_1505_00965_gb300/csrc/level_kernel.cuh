@@ -848,12 +848,15 @@ __global__ void __launch_bounds__(1024) level_small_kernel(const LevelParams p)
 // ------------------------------------------------------------------ batched rounds
 
 // All samples of one chunk, by the threads of one block, on the code path of the chunk's task.
+// Y of sample first + i goes to y[i] when the task has per-sample output (p.y_out, indexed from
+// the task's first sample; NULL in the adaptive driver's rounds).
 template <typename R, int MT>
 __device__ __forceinline__ void batch_chunk(const LevelParams &p, uint64_t first, uint64_t count,
                                             double m[4], float &b1, float &b2, float &b3, float &b4,
                                             int &nb)
 {
     const uint64_t t = threadIdx.x, T = blockDim.x;
+    double *y = p.y_out ? p.y_out + (first - p.first) : nullptr;
 #define MLMC_BATCH_CASES(CALL)                                                                  \
     switch (p.payoff) {                                                                         \
     case kEuropean: CALL(kEuropean); break;                                                     \
@@ -864,9 +867,9 @@ __device__ __forceinline__ void batch_chunk(const LevelParams &p, uint64_t first
     case kGeoAsian: CALL(kGeoAsian); break;                                                     \
     default: break;                                                                             \
     }
-#define MLMC_SMALL(PAY) small_range<R, PAY, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
-#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, nullptr)
+#define MLMC_SMALL(PAY) small_range<R, PAY, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, y)
+#define MLMC_SPLIT(PAY) regular_range<R, MT, PAY, true, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, y)
+#define MLMC_PLAIN(PAY) regular_range<R, MT, PAY, false, false, false>(p, first, count, t, T, m, b1, b2, b3, b4, nb, y)
     if (p.small) {
         MLMC_BATCH_CASES(MLMC_SMALL)
     } else if (p.lanes > 1) {

@@ -137,8 +137,9 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
 __device__ __forceinline__ float warp_mlp(const MlpShared &s, uint32_t *xw, const float x[8])
 {
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) xw[lane * 4 + j] = pack_bf16x2(x[2 * j], x[2 * j + 1]);
+    // one 16-byte store per lane (four 4-byte stores at a stride of 4 words conflicted 4 ways)
+    *reinterpret_cast<uint4 *>(&xw[lane * 4]) = make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]),
+                                                           pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
     __syncwarp();
     float mine = 0.f;
 #pragma unroll 1

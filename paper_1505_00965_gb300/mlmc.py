@@ -61,6 +61,11 @@ class mlmc_problem(ctypes.Structure):
     _fields_ = [("model", mlmc_model), ("payoff", mlmc_payoff), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+class mlmc_level_task(ctypes.Structure):
+    _fields_ = [("problem", mlmc_problem), ("level", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("first", ctypes.c_uint64), ("N", ctypes.c_uint64)]
+
+
 class mlmc_result(ctypes.Structure):
     _fields_ = [("P", ctypes.c_double), ("eps", ctypes.c_double), ("L", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -133,6 +138,7 @@ _SIGNATURES = {
     "mlmc_autotune_entries": ([], _i32),
     "mlmc_autotune_lookup": ([_i32, _i32, _i32, _i32, _u64, _pl], _i32),
     "mlmc_estimate_batch": ([_i32, ctypes.c_void_p, _i32, _i32, _i32, _u64, _i32, _vp, ctypes.c_void_p], _i32),
+    "mlmc_level_sums_batch": ([_i32, ctypes.c_void_p, _i32, _i32, _dptr, _vp, _vp], _i32),
     "mlmc_estimate": ([_dbl, _i32, _i32, _i32, _u64, _pm, _pp, _u64, _i32, _vp, ctypes.POINTER(mlmc_result)], _i32),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
@@ -316,6 +322,19 @@ def mlmc_estimate_batch(problems, M: int = 4, Lmin: int = 2, Lmax: int = 8, N0: 
     if st not in (MLMC_OK, MLMC_ENOTCONV):
         _check(st)
     return [_estimate_from(MLMC_OK if res[i].converged else MLMC_ENOTCONV, res[i]) for i in range(n)]
+
+
+def mlmc_level_sums_batch(tasks, M: int = 4, precision="fp32", d_y=None, stream=None):
+    """Level sums of many (Problem, seed, level, first, N) ranges in one batched round.  Returns
+    a list of four sums per task; d_y (device buffer or None) receives every sample's Y."""
+    n = len(tasks)
+    arr = (mlmc_level_task * n)()
+    for i, (prob, seed, level, first, N) in enumerate(tasks):
+        arr[i] = mlmc_level_task(mlmc_problem(prob.model(), prob.payoff_struct(), 1.0, seed), level, 0, first, N)
+    out = (ctypes.c_double * (4 * n))()
+    _check(_lib.mlmc_level_sums_batch(n, ctypes.cast(arr, ctypes.c_void_p), M, _prec(precision), out, _addr(d_y),
+                                      _addr(stream)))
+    return [list(out[4 * i:4 * i + 4]) for i in range(n)]
 
 
 def mlmc_estimate(eps: float, problem: Problem, seed: int, M: int = 4, Lmin: int = 2, Lmax: int = 8,

@@ -168,3 +168,23 @@ def test_quintic_model_arguments_rejected_on_host(kw, launch, msg):
         mlmc.mlmc_level_sums_ex(2, 4, 100, 0, mlmc.Problem(**kw), 1, launch=launch)
     assert ei.value.status == mlmc.MLMC_EINVAL
     assert msg in str(ei.value)
+
+
+def test_batched_level_sums_arguments_rejected_on_host():
+    """mlmc_level_sums_batch checks every task before any device work."""
+    from paper_1505_00965_gb300 import mlmc
+
+    ok = mlmc.Problem(payoff="asian")
+    cases = [
+        ([(ok, 1, 2, 0, 10)], dict(M=3), "M must be"),
+        ([(ok, 1, 2, 0, 10)], dict(precision="fp64_stream32"), "batches run"),
+        ([(ok, 1, 16, 0, 10)], {}, "level 16 out of range"),
+        ([(mlmc.Problem(payoff="asian", scheme="milstein"), 1, 2, 0, 10)], {}, "coupled Euler--Maruyama"),
+        ([(ok, 1, 2, 2 ** 64 - 5, 10)], {}, "overflows"),
+        ([(ok, 1, 2, 0, 2 ** 32)], {}, "2^32"),
+    ]
+    for tasks, kw, msg in cases:
+        with pytest.raises(mlmc.MLMCError) as ei:
+            mlmc.mlmc_level_sums_batch(tasks, **kw)
+        assert ei.value.status in (mlmc.MLMC_EINVAL, mlmc.MLMC_ENOTIMPL)
+        assert msg in str(ei.value), (msg, str(ei.value))

@@ -44,3 +44,27 @@ def test_autotune_then_parity(mlmc, tmp_path):
     assert mlmc.mlmc_autotune_load(str(path)) == n
     est = mlmc.mlmc_estimate(1e-2, p, 1)
     assert est.converged
+
+
+def test_tuned_two_samples_per_thread_keeps_parity(mlmc, tmp_path):
+    """A table entry with two samples per thread (as the tuner may choose for FP32 whole paths)
+    drives the planner's launches, which keep every sample equal to the oracle's; on levels where
+    the two-sample kernel does not exist (level 0) the planner falls back to one sample."""
+    path = tmp_path / "ns2.json"
+    lines = []
+    for level in (0, 1, 3, 5):
+        lines.append(f' {{"precision": 1, "payoff": 2, "M": 4, "level": {level}, "log2N": 10, "threads": 128, '
+                     f'"lanes": 1, "oversub": 2, "ns_per_sample": 1.0, "samples_per_thread": 2}}')
+    path.write_text('{"entries": [\n' + ",\n".join(lines) + "\n]}\n")
+    assert mlmc.mlmc_autotune_load(str(path)) == 4
+    assert mlmc.mlmc_autotune_lookup("fp32", "lookback", 4, 3, 5000) == (128, 1, 2, 2)
+    p = mlmc.Problem(payoff="lookback", **GBM)
+    op = oracle_problem(oracle, p)
+    for level, N in [(0, 5003), (1, 4001), (3, 2001), (5, 601)]:
+        sums, y = run_level(mlmc, level, 4, N, 13, p, 3, "fp32")
+        yo = oracle.level_samples(level, 4, N, op, seed=3, first=13, stream="fp32")
+        bound = 8.0 * (2.0 ** -24 * np.sqrt(4 ** level + 1) + 2e-6) * 100.0 * np.exp(0.05)
+        assert np.max(np.abs(y - yo)) <= bound, level
+        assert abs(sums[0] - y.sum()) <= 32 * 2.0 ** -24 * np.abs(y).sum()
+    est = mlmc.mlmc_estimate(1e-2, p, 2)
+    assert est.L >= 2

@@ -86,3 +86,44 @@ def test_batch_repeats_exactly_and_reports_lmax(mlmc, workloads):
         if not x.converged:
             assert x.L == 4 and x.status == mlmc.MLMC_ENOTCONV
         assert math.isfinite(x.P) and x.rounds >= 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_chunks_match_oracle_per_sample(mlmc, precision):
+    """One batched round (the batch kernel's chunk list, including split lanes on deep levels and
+    the packed level-0 blocks) writes every sample's Y: each equals the oracle's sample on the
+    identical stream within the per-sample bound of the level parity tests, and each task's sums
+    are the sums of its own samples."""
+    import torch
+
+    import oracle
+
+    from gpu_helpers import moment_sums, oracle_problem
+
+    u, ez = (2.0 ** -24, 2e-6) if precision == "fp32" else (2.0 ** -53, 1e-15)
+    specs = [("european", 0.2, 100.0, 0, 20011, 3), ("asian", 0.3, 95.0, 1, 4001, 977), ("lookback", 0.25, 105.0, 3, 1501, 7),
+             ("digital", 0.2, 100.0, 4, 777, 2 ** 33 + 1), ("asian", 0.2, 100.0, 6, 301, 11),
+             ("lookback", 0.4, 90.0, 7, 129, 0), ("european", 0.3, 110.0, 2, 0, 5), ("asian", 0.2, 100.0, 8, 33, 1)]
+    tasks = [(mlmc.Problem(payoff=p, sigma=s, K=k, cash=1.0), 40 + i, l, first, N)
+             for i, (p, s, k, l, N, first) in enumerate(specs)]
+    total = sum(t[4] for t in tasks)
+    d_y = torch.zeros(total, dtype=torch.float64, device="cuda")
+    sums = mlmc.mlmc_level_sums_batch(tasks, precision=precision, d_y=d_y)
+    y_all = d_y.cpu().numpy()
+    off = 0
+    for (prob, seed, level, first, N), s in zip(tasks, sums):
+        y = y_all[off:off + N]
+        off += N
+        if N == 0:
+            assert s == [0.0, 0.0, 0.0, 0.0]
+            continue
+        yo = oracle.level_samples(level, 4, N, oracle_problem(oracle, prob), seed=seed, first=first, stream=precision)
+        bound = 8.0 * (u * math.sqrt(4 ** level + 1) + ez) * prob.S0 * math.exp(prob.r * prob.T)
+        diff = np.abs(y - yo)
+        if prob.payoff == "digital" and precision == "fp32":
+            diff = diff[diff < 0.25 * prob.cash]  # threshold flips, checked in the level parity tests
+        assert np.max(diff) <= bound, (prob.payoff, level, float(np.max(diff)), bound)
+        own = moment_sums(y)
+        tol = 1e-12 if precision == "fp64" else 32 * u
+        for k in range(4):
+            assert abs(s[k] - own[k]) <= tol * np.sum(np.abs(y) ** (k + 1)) + 1e-300, (level, k)

@@ -88,6 +88,12 @@ def _check_level(mlmc, level, M, N, first, payoff, precision, launch=None, seed=
     m_gpu, m_orc = np.mean(y[keep]), np.mean(yo[keep])
     tol = RTOL_MEAN[precision] * max(abs(m_orc), sbar)
     assert abs(m_gpu - m_orc) <= tol, f"mean {m_gpu!r} vs {m_orc!r} (tol {tol:.3e})"
+    # the same samples on both sides: the means differ by roundoff alone, which must stay far
+    # below the level's statistical error (the relative bound above is loose on deep levels,
+    # where m_l is small against the price scale)
+    se = np.std(yo[keep], ddof=1) / math.sqrt(keep.sum()) if keep.sum() > 1 else 0.0
+    if se > 0:
+        assert abs(m_gpu - m_orc) <= 0.1 * se, f"mean error {abs(m_gpu - m_orc):.3e} against SE {se:.3e}"
     ref = moment_sums(yo[keep])
     got = moment_sums(y[keep])
     for k in range(1, 4):
@@ -166,6 +172,24 @@ def test_two_samples_per_thread_rejected_where_not_built(mlmc):
         with pytest.raises(mlmc.MLMCError) as ei:
             mlmc.mlmc_level_sums_async(level, 4, 100, 0, prob, 1, d, ws, ws_bytes, precision=prec, launch=launch)
         assert ei.value.status == mlmc.MLMC_EINVAL
+
+
+@pytest.mark.parametrize("payoff", ["asian", "lookback", "digital"])
+@pytest.mark.parametrize("level,N", [(0, 10_000_000), (1, 4_000_000)])
+def test_fp32_presum_error_on_level_variance(mlmc, payoff, level, N):
+    """FP32 paths add batches of at most 32 samples in FP32 before the FP64 sums.  The level
+    variance V = S2/N - (S1/N)^2 from the device's sums against V from FP64 sums of the device's
+    own samples: their difference is the pre-sum's error alone, at most
+    32u (sum Y^2 + 2 |m| sum |Y|) / N, which cancellation amplifies by E[Y^2]/V relative to V
+    (about 3.5 at level 0 of the Asian call); the test bounds it and requires it below 1e-5 of V."""
+    p = mlmc.Problem(payoff=payoff, **GBM)
+    sums, y = run_level(mlmc, level, 4, N, 0, p, 3, "fp32", launch={"lanes_per_path": 1})
+    own = moment_sums(y)
+    m_dev, m_own = sums[0] / N, own[0] / N
+    v_dev, v_own = sums[1] / N - m_dev ** 2, own[1] / N - m_own ** 2
+    bound = 32 * U["fp32"] * (own[1] + 2 * abs(m_own) * np.sum(np.abs(y))) / N
+    assert abs(v_dev - v_own) <= bound, (v_dev, v_own, bound)
+    assert abs(v_dev - v_own) <= 1e-5 * v_own, (v_dev, v_own)
 
 
 @pytest.mark.parametrize("threads,blocks", [(32, 1), (64, 3), (1024, 0), (256, 7)])

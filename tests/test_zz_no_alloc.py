@@ -63,6 +63,53 @@ def test_noalloc_matches_async_on_two_calls(mlmc, precision, rtol, payoff, level
         np.testing.assert_array_equal(y, ref_y)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_noalloc_grid_cut_to_its_scratch(mlmc, precision):
+    """64-thread blocks over a million samples: the planner sizes the grid beyond the 2048 blocks
+    the fixed scratch holds, and the entry point cuts it to 2048.  Every sample is the async
+    form's (and the oracle's); the sums add the same samples in another order."""
+    import oracle
+
+    from gpu_helpers import moment_sums, oracle_problem
+
+    level, N, first, seed = 2, 1_000_003, 5, 7
+    launch = {"threads_per_block": 64}
+    prob = mlmc.Problem(payoff="asian", **GBM)
+    assert mlmc.mlmc_level_workspace_bytes(level, 4, N, precision, {"threads_per_block": 64, "blocks": 4096}) > 0
+    ref_sums, ref_y = run_level(mlmc, level, 4, N, first, prob, seed, precision, launch=launch)
+    for _ in range(2):
+        sums, y = _noalloc_via_c_abi(mlmc, level, 4, N, first, prob, seed, precision, launch)
+        np.testing.assert_array_equal(y, ref_y)
+        own = moment_sums(y)
+        u = 2.0 ** -24 if precision == "fp32" else 2.0 ** -53
+        for k in range(4):
+            scale = np.sum(np.abs(y) ** (k + 1))
+            assert abs(sums[k] - ref_sums[k]) <= 64 * u * scale, (k, sums[k], ref_sums[k])
+            assert abs(sums[k] - own[k]) <= 32 * u * scale, (k, sums[k], own[k])
+    op = oracle_problem(oracle, prob)
+    bound = 8.0 * ((2.0 ** -24 if precision == "fp32" else 2.0 ** -53) * np.sqrt(17) +
+                   (2e-6 if precision == "fp32" else 1e-15)) * 100.0 * np.exp(0.05)
+    for a in (0, N // 2, N - 1000):
+        yo = oracle.level_samples(level, 4, 1000, op, seed=seed, first=first + a, stream=precision)
+        assert np.max(np.abs(y[a:a + 1000] - yo)) <= bound
+
+
+def test_noalloc_takes_no_device_memory(mlmc):
+    """After the first call (which loads the kernel and looks up the scratch), further calls do
+    not change the device's free memory."""
+    import torch
+
+    prob = mlmc.Problem(payoff="lookback", **GBM)
+    _noalloc_via_c_abi(mlmc, 3, 4, 20_001, 0, prob, 3, "fp32", {})
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        _noalloc_via_c_abi(mlmc, 3, 4, 20_001, 0, prob, 3, "fp32", {})
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0, (free0, free1)
+
+
 def test_noalloc_rejects_grid_beyond_its_scratch(mlmc):
     import torch
 
