@@ -272,6 +272,20 @@ def side_workloads(mlmc, stream) -> dict:
                  for s in range(1, 9)]
         anti[p] = statistics.median(times)
     out["antithetic_time_to_eps_ms"] = anti
+    # the same estimates with their rounds on the device (one graph launch each: a driver kernel
+    # configures the level kernels by device-side graph updates) against the host rounds
+    prev = mlmc.mlmc_set_driver_mode("device")
+    try:
+        dev = {}
+        for p in PAYOFFS:
+            prob = mlmc.Problem(payoff=p, cash=1.0, **GBM)
+            mlmc.mlmc_estimate(EPS, prob, 1, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream)  # builds the graph
+            dev[p] = statistics.median(
+                mlmc.mlmc_estimate(EPS, prob, s, M=M, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream).wall_ms
+                for s in range(1, 9))
+        out["device_rounds_wall_ms"] = dev
+    finally:
+        mlmc.mlmc_set_driver_mode(prev)
     prob = mlmc.Problem(payoff="asian", cash=1.0, **GBM)
     # trained twice: the first call also loads the control-variate kernels (lazy module loading);
     # the second is the cost of training a further problem in a running process

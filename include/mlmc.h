@@ -235,7 +235,8 @@ typedef struct mlmc_result {
     int32_t L;                       /* finest level used */
     int32_t converged;               /* 1 if the bias test passed */
     int32_t rounds;                  /* sampling rounds taken */
-    int32_t reserved;
+    int32_t device_rounds;           /* 1 if the rounds ran on the device (one graph launch), 0 if
+                                        the host ran them (mlmc_set_driver_mode) */
     uint64_t N[MLMC_MAX_LEVELS];      /* samples per level */
     double sums[MLMC_MAX_LEVELS][4];  /* sum Y^k per level */
     double mean[MLMC_MAX_LEVELS];     /* sample mean of Y_l */
@@ -244,11 +245,35 @@ typedef struct mlmc_result {
     double alpha, beta;              /* fitted weak and variance rates (base M) */
     double total_cost;               /* sum_l N_l C_l */
     double path_steps;               /* sum_l N_l M^l: coupled fine steps simulated */
-    double kernel_ms;                /* device time of the level kernels */
+    double kernel_ms;                /* device time of the level kernels (device rounds: of the whole
+                                        graph, driver kernels included) */
     double wall_ms;                  /* host wall time of the call */
-    uint64_t launches;               /* level-kernel launches made */
-    uint64_t d2h_bytes;              /* bytes copied device to host (the round sums) */
+    uint64_t launches;               /* kernel launches made (device rounds: level kernels and
+                                        driver iterations) */
+    uint64_t d2h_bytes;              /* bytes copied device to host (host rounds: the round sums;
+                                        device rounds: the final state, once) */
 } mlmc_result;
+
+/* Where mlmc_estimate runs its rounds.  The paper has no counterpart (host/device placement of
+ * the driver's arithmetic).
+ *   MLMC_DRIVER_HOST (default): every round's sums come back to the host, which decides the next
+ *     round (on GB300 with its Grace host the faster form: a round trip costs about 16 us, the
+ *     device form's driver kernel about 35 us, most of it the FP64 update's dependent chain);
+ *   MLMC_DRIVER_DEVICE: on the device or MLMC_ENOTIMPL (no host round trip: the whole estimate
+ *     is one graph launch, for callers whose host must not take part between rounds);
+ *   MLMC_DRIVER_AUTO: on the device where the device form covers the problem (GBM, coupled or
+ *     antithetic estimator), on the host otherwise or where the device form cannot be built.
+ * Device rounds: one CUDA graph per problem shape (cached per device until mlmc_shutdown) whose
+ * WHILE node repeats a one-warp driver kernel -- the host driver's FP64 update of means,
+ * variances, rates, N_l, the bias test and the added level, in the same order -- and the level
+ * kernels it configures by device-side graph updates (sample range, lanes per path, grid; the
+ * host planner's built-in shapes, not an autotuned table).  The host launches the graph once and
+ * reads the final state once.  Both forms run the same kernels on the same ranges and grids, so
+ * their estimates agree; only a decision taken exactly at a rounding boundary of CUDA's FP64 log
+ * or pow could differ.  Process-wide; *previous (host, may be NULL) receives the mode it replaces.
+ * MLMC_EINVAL for an unknown mode (the mode is then unchanged). */
+enum { MLMC_DRIVER_AUTO = 0, MLMC_DRIVER_HOST = 1, MLMC_DRIVER_DEVICE = 2 };
+int mlmc_set_driver_mode(int mode, int *previous);
 
 /*
  * mlmc_estimate -- adaptive multilevel Monte Carlo estimate of E[h(X(T))] to root-mean-square

@@ -492,6 +492,7 @@ int mlmc_shutdown(void)
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     noalloc_forget(dev);
+    graph_driver_release(dev);
     CUDA_TRY(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lock(g_pool_mutex);
     for (size_t i = 0; i < g_pool.size();) {
@@ -701,6 +702,18 @@ extern "C" int mlmc_estimate(double eps, int M, int Lmin, int Lmax, uint64_t N0,
     if (payoff->estimator != MLMC_COUPLED && payoff->estimator != MLMC_ANTITHETIC)
         return fail(MLMC_EINVAL, "the adaptive driver needs the coupled or antithetic estimator");
     cudaStream_t st = (cudaStream_t)stream;
+
+    // rounds on the device (one graph launch) unless the host is asked for or must run them
+    const int mode = graph_driver_mode();
+    if (mode != MLMC_DRIVER_HOST) {
+        if (!graph_driver_covers(model, payoff)) {
+            if (mode == MLMC_DRIVER_DEVICE)
+                return fail(MLMC_ENOTIMPL, "device-side rounds cover GBM with the coupled or antithetic estimator");
+        } else {
+            rc = estimate_on_device(eps, M, Lmin, Lmax, N0, model, payoff, seed, precision, st, out, t_start);
+            if (rc != MLMC_ENOTIMPL || mode == MLMC_DRIVER_DEVICE) return rc;
+        }
+    }
 
     // A round's level launches go round-robin over `st` and the set's own streams, deepest level
     // first: the blocks of the next launch fill the SMs that one launch's last partial wave

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstddef>
 #include <cstdint>
 
@@ -36,6 +37,17 @@ struct Plan {
 int plan_level(int level, int M, uint64_t N, int precision, int payoff, int scheme, const mlmc_launch *launch,
                Plan *plan);
 // plan_level for GBM, the one-thread-per-sample plan of the QUINTIC_ODE kernel otherwise.
+// Whether every fine and coarse step factor 1 + d of a GBM path on this level is positive for any
+// normal the stream can produce (the split lookback kernels then keep no running minimum).
+bool positive_step_factors(const mlmc_model *m, int level, int M);
+// Device-side rounds of mlmc_estimate (graph_driver.cu): mode, coverage, the estimate (MLMC_ENOTIMPL
+// with nothing launched where the graph cannot be built), and release of a device's cached graphs.
+int graph_driver_mode();
+bool graph_driver_covers(const mlmc_model *model, const mlmc_payoff *payoff);
+int estimate_on_device(double eps, int M, int Lmin, int Lmax, uint64_t N0, const mlmc_model *model,
+                       const mlmc_payoff *payoff, uint64_t seed, int precision, cudaStream_t st, mlmc_result *out,
+                       std::chrono::steady_clock::time_point t_start);
+void graph_driver_release(int dev);
 int plan_problem(int level, int M, uint64_t N, int precision, const mlmc_model *model, const mlmc_payoff *payoff,
                  const mlmc_launch *launch, Plan *plan);
 void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,

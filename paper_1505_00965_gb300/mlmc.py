@@ -68,7 +68,7 @@ class mlmc_level_task(ctypes.Structure):
 
 class mlmc_result(ctypes.Structure):
     _fields_ = [("P", ctypes.c_double), ("eps", ctypes.c_double), ("L", ctypes.c_int32),
-                ("converged", ctypes.c_int32), ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("rounds", ctypes.c_int32), ("device_rounds", ctypes.c_int32),
                 ("N", ctypes.c_uint64 * MLMC_MAX_LEVELS),
                 ("sums", (ctypes.c_double * 4) * MLMC_MAX_LEVELS),
                 ("mean", ctypes.c_double * MLMC_MAX_LEVELS), ("var", ctypes.c_double * MLMC_MAX_LEVELS),
@@ -112,6 +112,7 @@ _SIGNATURES = {
     "mlmc_version": ([], ctypes.c_char_p),
     "mlmc_device_sm_count": ([], _i32),
     "mlmc_shutdown": ([], _i32),
+    "mlmc_set_driver_mode": ([_i32, ctypes.POINTER(_i32)], _i32),
     "mlmc_level_sums": ([_i32, _i32, _u64, _pm, _pp, _u64, _dptr, _dptr], _i32),
     "mlmc_level_sums_ex": ([_i32, _i32, _u64, _u64, _pm, _pp, _u64, _i32, _i32, _pl, _vp, _dptr, _dptr], _i32),
     "mlmc_level_workspace_bytes": ([_i32, _i32, _u64, _i32, _pl], _sz),
@@ -290,6 +291,7 @@ class Estimate:
     wall_ms: float = 0.0
     launches: int = 0
     d2h_bytes: int = 0
+    device_rounds: bool = False
 
 
 def _estimate_from(st: int, r: mlmc_result) -> "Estimate":
@@ -299,7 +301,7 @@ def _estimate_from(st: int, r: mlmc_result) -> "Estimate":
                     mean=[r.mean[l] for l in range(L + 1)], var=[r.var[l] for l in range(L + 1)],
                     cost=[r.cost[l] for l in range(L + 1)], alpha=r.alpha, beta=r.beta, total_cost=r.total_cost,
                     path_steps=r.path_steps, kernel_ms=r.kernel_ms, wall_ms=r.wall_ms, launches=int(r.launches),
-                    d2h_bytes=int(r.d2h_bytes))
+                    d2h_bytes=int(r.d2h_bytes), device_rounds=bool(r.device_rounds))
 
 
 def mlmc_estimate_batch(problems, M: int = 4, Lmin: int = 2, Lmax: int = 8, N0: int = 10_000, precision="fp32",
@@ -322,6 +324,16 @@ def mlmc_estimate_batch(problems, M: int = 4, Lmin: int = 2, Lmax: int = 8, N0: 
     if st not in (MLMC_OK, MLMC_ENOTCONV):
         _check(st)
     return [_estimate_from(MLMC_OK if res[i].converged else MLMC_ENOTCONV, res[i]) for i in range(n)]
+
+
+DRIVER_MODES = {"auto": 0, "host": 1, "device": 2}
+
+
+def mlmc_set_driver_mode(mode) -> str:
+    """Where mlmc_estimate runs its rounds ("auto", "host" or "device"); returns the previous mode."""
+    prev = ctypes.c_int(0)
+    _check(_lib.mlmc_set_driver_mode(DRIVER_MODES[mode] if isinstance(mode, str) else int(mode), ctypes.byref(prev)))
+    return {v: k for k, v in DRIVER_MODES.items()}[prev.value]
 
 
 def mlmc_level_sums_batch(tasks, M: int = 4, precision="fp32", d_y=None, stream=None):

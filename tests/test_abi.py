@@ -188,3 +188,19 @@ def test_batched_level_sums_arguments_rejected_on_host():
             mlmc.mlmc_level_sums_batch(tasks, **kw)
         assert ei.value.status in (mlmc.MLMC_EINVAL, mlmc.MLMC_ENOTIMPL)
         assert msg in str(ei.value), (msg, str(ei.value))
+
+
+def test_driver_mode_switch_on_host():
+    """mlmc_set_driver_mode validates its argument and reports the mode it replaces (no GPU)."""
+    from paper_1505_00965_gb300 import mlmc
+
+    prev = mlmc.mlmc_set_driver_mode("host")
+    assert prev == "host"  # the default
+    try:
+        assert mlmc.mlmc_set_driver_mode("device") == "host"
+        with pytest.raises(mlmc.MLMCError) as ei:
+            mlmc.mlmc_set_driver_mode(3)
+        assert ei.value.status == mlmc.MLMC_EINVAL
+        assert mlmc.mlmc_set_driver_mode("auto") == "device"
+    finally:
+        mlmc.mlmc_set_driver_mode(prev)

@@ -132,3 +132,67 @@ def test_concurrent_estimates_on_two_streams(mlmc):
     torch.cuda.synchronize()
     for r, o in zip(ref, out):
         assert o is not None and o.P == r.P and o.N == r.N and o.sums == r.sums
+
+
+@pytest.fixture()
+def driver_mode(mlmc):
+    prev = mlmc.mlmc_set_driver_mode("auto")
+    yield mlmc
+    mlmc.mlmc_set_driver_mode(prev)
+
+
+@pytest.mark.parametrize("payoff,estimator,precision,eps,seed,Lmax", [
+    ("asian", "coupled", "fp32", 1e-3, 1, 8), ("lookback", "coupled", "fp32", 3e-3, 2, 8),
+    ("european", "coupled", "fp64", 1e-2, 3, 8), ("digital", "coupled", "fp32", 2e-3, 4, 8),
+    ("asian", "antithetic", "fp32", 1e-3, 5, 8), ("lookback", "coupled", "fp32", 1e-3, 6, 5),
+    ("asian", "coupled", "fp64_stream32", 3e-3, 7, 8)])
+def test_device_rounds_equal_host_rounds(driver_mode, payoff, estimator, precision, eps, seed, Lmax):
+    """The rounds run on the device (one graph launch: a driver kernel configures the level
+    kernels by device-side graph updates) take the host driver's decisions: the same rounds,
+    N_l and level sums, so the same estimate, bit for bit."""
+    mlmc = driver_mode
+    p = mlmc.Problem(payoff=payoff, estimator=estimator, **GBM)
+    mlmc.mlmc_set_driver_mode("host")
+    h = mlmc.mlmc_estimate(eps, p, seed, precision=precision, Lmax=Lmax)
+    mlmc.mlmc_set_driver_mode("device")
+    d = mlmc.mlmc_estimate(eps, p, seed, precision=precision, Lmax=Lmax)
+    d2 = mlmc.mlmc_estimate(eps, p, seed, precision=precision, Lmax=Lmax)  # the cached graph, again
+    assert not h.device_rounds and d.device_rounds and d2.device_rounds
+    for x in (d, d2):
+        assert x.N == h.N and x.L == h.L and x.rounds == h.rounds and x.converged == h.converged
+        assert x.sums == h.sums and x.P == h.P and x.status == h.status
+        assert x.alpha == pytest.approx(h.alpha, rel=1e-12) and x.beta == pytest.approx(h.beta, rel=1e-12)
+        assert x.d2h_bytes > 0 and x.kernel_ms > 0
+
+
+def test_device_rounds_match_oracle_driver(driver_mode):
+    """The device driver's FP64 arithmetic takes the oracle driver's N_l schedule."""
+    mlmc = driver_mode
+    mlmc.mlmc_set_driver_mode("device")
+    for payoff, eps, seed in (("european", 1e-2, 1), ("asian", 5e-3, 2)):
+        p = mlmc.Problem(payoff=payoff, **GBM)
+        est = mlmc.mlmc_estimate(eps, p, seed, precision="fp64")
+        ref = oracle_driver.estimate(eps, oracle.Problem(payoff=payoff, Q=1.0,
+                                                         **{k: v for k, v in GBM.items() if k != "cash"}), seed,
+                                     stream="fp64")
+        assert est.device_rounds
+        assert est.N == ref.N and est.L == ref.L and est.converged == ref.converged
+        assert abs(est.P - ref.P) <= 1e-12 * abs(ref.P)
+
+
+def test_device_rounds_fall_back_for_other_models(driver_mode):
+    """The quintic ODE keeps the host rounds: "auto" runs them there, "device" refuses, and the
+    diverging explicit scheme still stops with MLMC_ENONFINITE."""
+    mlmc = driver_mode
+    q = mlmc.Problem(kind="quintic", scheme="tamed", payoff="second_moment", T=1.0)
+    a = mlmc.mlmc_estimate(1e-2, q, 1)
+    assert not a.device_rounds
+    g = mlmc.mlmc_estimate(1e-2, mlmc.Problem(payoff="european", **GBM), 1)
+    assert g.device_rounds
+    mlmc.mlmc_set_driver_mode("device")
+    with pytest.raises(mlmc.MLMCError) as ei:
+        mlmc.mlmc_estimate(1e-2, q, 1)
+    assert ei.value.status == mlmc.MLMC_ENOTIMPL
+    with pytest.raises(mlmc.MLMCError):
+        mlmc.mlmc_set_driver_mode(7)
+    assert mlmc.mlmc_set_driver_mode("auto") == "device"
