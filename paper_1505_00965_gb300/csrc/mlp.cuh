@@ -59,6 +59,58 @@ __device__ __forceinline__ float gelu(float z)
     return fmaf(hz, tanh_approx(u), hz);
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed FP32 arithmetic of sm_100 and
+// later (fma / mul / add .rn.f32x2: each half rounds exactly as the scalar instruction would).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
+
+// GELU of both halves: the operations of gelu() in the same order, two values per instruction
+// (bit-identical to gelu() on each half).
+__device__ __forceinline__ f32x2 gelu2(f32x2 z)
+{
+    const f32x2 p = f2_fma(f2_mul(z, z), f2_splat(0.035677408136300125f), f2_splat(0.7978845608028654f));
+    float u0, u1;
+    f2_unpack(f2_mul(z, p), u0, u1);
+    const f32x2 hz = f2_mul(z, f2_splat(0.5f));
+    return f2_fma(hz, f2_pack(tanh_approx(u0), tanh_approx(u1)), hz);
+}
+
+// The bfloat16 pair of a packed pair (low half in the low 16 bits).
+__device__ __forceinline__ uint32_t pack_bf16x2_f2(f32x2 v)
+{
+    float lo, hi;
+    f2_unpack(v, lo, hi);
+    return pack_bf16x2(lo, hi);
+}
+
 // d += a * b for one m16n8k16 tile, bfloat16 operands, FP32 accumulators.
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
 {
@@ -92,25 +144,20 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // layer 1: A = x (16 x 16, columns 8..15 zero), B[k][n] = W1[n][k]
     uint32_t a[4] = {xw[g * 4 + t], xw[(g + 8) * 4 + t], 0u, 0u};
-    float h1[8][4];
+    // layer 1, then A = GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1); GELU on the
+    // accumulator pairs (columns 2t, 2t + 1 of rows g and g + 8) with packed FP32 arithmetic
+    uint32_t a2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int o = 8 * nt + 2 * t;
         float c[4] = {s.b1[o], s.b1[o + 1], s.b1[o], s.b1[o + 1]};
         mma_bf16(c, a, s.W1[(8 * nt + g) * 4 + t], 0u);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) h1[nt][i] = gelu(c[i]);
+        a2[nt >> 1][(nt & 1) * 2] = pack_bf16x2_f2(gelu2(f2_pack(c[0], c[1])));
+        a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2_f2(gelu2(f2_pack(c[2], c[3])));
     }
-    // layer 2: A = GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1), B[k][n] = W2[n][k]
-    uint32_t a2[4][4];
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        a2[kt][0] = pack_bf16x2(h1[2 * kt][0], h1[2 * kt][1]);
-        a2[kt][1] = pack_bf16x2(h1[2 * kt][2], h1[2 * kt][3]);
-        a2[kt][2] = pack_bf16x2(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
-        a2[kt][3] = pack_bf16x2(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
-    }
-    float p0 = 0.f, p1 = 0.f;
+    // layer 2, B[k][n] = W2[n][k]; layer 3: the dot product with w3 over this lane's units, rows g
+    // and g + 8, in packed pairs (units o and o + 1 summed at the end)
+    f32x2 q0 = f2_splat(0.f), q1 = f2_splat(0.f);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int o = 8 * nt + 2 * t;
@@ -118,12 +165,15 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
         const uint32_t *w = &s.W2[(8 * nt + g) * kW2Stride];
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma_bf16(c, a2[kt], w[8 * kt + t], w[8 * kt + t + 4]);
-        // layer 3: dot product with w3 over this lane's units, rows g and g + 8
-        p0 = fmaf(s.w3[o], gelu(c[0]), p0);
-        p0 = fmaf(s.w3[o + 1], gelu(c[1]), p0);
-        p1 = fmaf(s.w3[o], gelu(c[2]), p1);
-        p1 = fmaf(s.w3[o + 1], gelu(c[3]), p1);
+        const f32x2 w3 = f2_pack(s.w3[o], s.w3[o + 1]);
+        q0 = f2_fma(w3, gelu2(f2_pack(c[0], c[1])), q0);
+        q1 = f2_fma(w3, gelu2(f2_pack(c[2], c[3])), q1);
     }
+    float p0, p1, e0, e1;
+    f2_unpack(q0, p0, e0);
+    f2_unpack(q1, p1, e1);
+    p0 += e0;
+    p1 += e1;
     p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
     p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
     p1 += __shfl_xor_sync(0xffffffffu, p1, 1);

@@ -188,7 +188,8 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
     ok = mbar_wait(&s.mbar, phase) && ok;
     phase ^= 1u;
     tc_fence_after();
-    // epilogue 1: GELU(z1 + b1) as bfloat16 into the layer-2 A operand, 16 columns at a time
+    // epilogue 1: GELU(z1 + b1) as bfloat16 into the layer-2 A operand, 16 columns at a time, in
+    // packed FP32 pairs
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float z[16];
@@ -196,7 +197,8 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
         uint32_t h[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            h[j] = pack_bf16x2(gelu(z[2 * j] + s.b1[16 * c + 2 * j]), gelu(z[2 * j + 1] + s.b1[16 * c + 2 * j + 1]));
+            h[j] = pack_bf16x2_f2(gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]),
+                                               f2_pack(s.b1[16 * c + 2 * j], s.b1[16 * c + 2 * j + 1]))));
         *reinterpret_cast<uint4 *>(s.a2 + cm_byte(tid, 16 * c, 1024)) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(s.a2 + cm_byte(tid, 16 * c + 8, 1024)) = make_uint4(h[4], h[5], h[6], h[7]);
     }
@@ -214,15 +216,23 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
     ok = mbar_wait(&s.mbar, phase) && ok;
     phase ^= 1u;
     tc_fence_after();
-    // epilogue 2: g = b3 + sum_o w3_o GELU(z2_o + b2_o)
-    float g = s.b3;
+    // epilogue 2: g = b3 + sum_o w3_o GELU(z2_o + b2_o), in packed FP32 pairs (even and odd units
+    // summed apart, then together)
+    f32x2 q = f2_splat(0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float z[16];
         tmem_ld16(taddr + 16u * c, z);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) g = fmaf(s.w3[16 * c + j], gelu(z[j] + s.b2[16 * c + j]), g);
+        for (int j = 0; j < 8; ++j) {
+            const int o = 16 * c + 2 * j;
+            const f32x2 h = gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]), f2_pack(s.b2[o], s.b2[o + 1])));
+            q = f2_fma(f2_pack(s.w3[o], s.w3[o + 1]), h, q);
+        }
     }
+    float qe, qo;
+    f2_unpack(q, qe, qo);
+    const float g = s.b3 + (qe + qo);
     tc_fence_before();  // the next tile's MMAs overwrite the accumulator after the next barrier
     return g;
 }

@@ -135,6 +135,23 @@ __device__ __forceinline__ void gelu_and_grad(float z, float &h, float &dh)
     dh = fmaf(0.5f, t, 0.5f) + hz * fmaf(-t, t, 1.0f) * du;
 }
 
+// gelu_and_grad on both halves of a packed pair (packed FP32 arithmetic, the same operations;
+// the last line's add is a fused multiply-add here).
+__device__ __forceinline__ void gelu_and_grad2(f32x2 z, f32x2 &h, f32x2 &dh)
+{
+    const f32x2 z2 = f2_mul(z, z);
+    const f32x2 u = f2_mul(z, f2_fma(z2, f2_splat(0.035677408136300125f), f2_splat(0.7978845608028654f)));
+    const f32x2 du = f2_fma(z2, f2_splat(3.0f * 0.035677408136300125f), f2_splat(0.7978845608028654f));
+    float u0, u1;
+    f2_unpack(u, u0, u1);
+    const f32x2 t = f2_pack(tanh_approx(u0), tanh_approx(u1));
+    const f32x2 hz = f2_mul(z, f2_splat(0.5f));
+    h = f2_fma(hz, t, hz);
+    // (1 + t) / 2 + hz (1 - t^2) u' with 1 - t^2 = fma(t, -t, 1)
+    const f32x2 q = f2_fma(t, f2_mul(t, f2_splat(-1.0f)), f2_splat(1.0f));
+    dh = f2_fma(f2_mul(hz, q), du, f2_fma(t, f2_splat(0.5f), f2_splat(0.5f)));
+}
+
 // The bfloat16 network from the FP32 parameters in s.pfull (all threads; ends with a barrier).
 __device__ __forceinline__ void train_build_net(TrainSmem &s)
 {
@@ -181,10 +198,12 @@ __device__ __forceinline__ void train_tile(TrainSmem &s, int tile, float dscale,
         const int o = 8 * nt + 2 * t;
         float c[4] = {s.b1[o], s.b1[o + 1], s.b1[o], s.b1[o + 1]};
         mma_bf16(c, a, s.W1[(8 * nt + g) * 4 + t], 0u);
-        float h[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) gelu_and_grad(c[i], h[i], gz1[nt][i]);
-        const uint32_t w01 = pack_bf16x2(h[0], h[1]), w23 = pack_bf16x2(h[2], h[3]);
+        f32x2 h01, h23, d01, d23;
+        gelu_and_grad2(f2_pack(c[0], c[1]), h01, d01);
+        gelu_and_grad2(f2_pack(c[2], c[3]), h23, d23);
+        f2_unpack(d01, gz1[nt][0], gz1[nt][1]);
+        f2_unpack(d23, gz1[nt][2], gz1[nt][3]);
+        const uint32_t w01 = pack_bf16x2_f2(h01), w23 = pack_bf16x2_f2(h23);
         a2[nt >> 1][(nt & 1) * 2] = w01;
         a2[nt >> 1][(nt & 1) * 2 + 1] = w23;
         s.h1[r0 * kActWords + 4 * nt + t] = w01;
@@ -200,8 +219,13 @@ __device__ __forceinline__ void train_tile(TrainSmem &s, int tile, float dscale,
         const uint32_t *w = &s.W2[(8 * nt + g) * kW2Stride];
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma_bf16(c, a2[kt], w[8 * kt + t], w[8 * kt + t + 4]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) gelu_and_grad(c[i], h2[nt][i], gz2[nt][i]);
+        f32x2 h01, h23, d01, d23;
+        gelu_and_grad2(f2_pack(c[0], c[1]), h01, d01);
+        gelu_and_grad2(f2_pack(c[2], c[3]), h23, d23);
+        f2_unpack(h01, h2[nt][0], h2[nt][1]);
+        f2_unpack(h23, h2[nt][2], h2[nt][3]);
+        f2_unpack(d01, gz2[nt][0], gz2[nt][1]);
+        f2_unpack(d23, gz2[nt][2], gz2[nt][3]);
         p0 = fmaf(s.w3[o], h2[nt][0], p0);
         p0 = fmaf(s.w3[o + 1], h2[nt][1], p0);
         p1 = fmaf(s.w3[o], h2[nt][2], p1);
