@@ -564,14 +564,18 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         inf.train_loss = inf.var_resid / (sd[l] * sd[l]);
         const auto t_cost0 = std::chrono::steady_clock::now();
         eval_ms += std::chrono::duration<double, std::milli>(t_cost0 - t_eval0).count();
-        // 6. measured cost per sample of the plain, control-variate and mean kernels
-        // (sizes large enough that every timed launch runs for a millisecond or more: small
-        // launches would measure launch latency and idle SMs, not the cost per sample)
-        const uint64_t nt = std::max<uint64_t>(1u << 22, (uint64_t)(1u << 30) >> std::min(2 * l, 20));
-        const uint64_t nc = 1u << 24;
+        // 6. measured cost per sample of the plain, control-variate and mean kernels, each timed
+        // once after a small warm-up launch (sizes that keep every timed launch near half a
+        // millisecond or more: small launches would measure launch latency and idle SMs, not the
+        // cost per sample)
+        const uint64_t nt = std::max<uint64_t>(1u << 21, (uint64_t)(1u << 29) >> std::min(2 * l, 20));
+        const uint64_t nc = 1u << 23;
+        constexpr uint64_t kWarmSamples = 4096, kWarmReplicates = 8;
         {
-            Plan plan;
+            Plan plan, warm_plan;
             rc = plan_level(l, M, nt, MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr, &plan);
+            if (!rc) rc = plan_level(l, M, kWarmSamples, MLMC_FP32_PATH, payoff->kind, MLMC_EULER_MARUYAMA, nullptr,
+                                     &warm_plan);
             if (rc) return cleanup(rc);
             int cvb = 0;
             rc = grid_for(cv_level_kernel_for(payoff->kind), nc, &cvb);
@@ -584,30 +588,32 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
             CV_TRY(cudaMalloc(&d_out, 16 * sizeof(double)));
             double hq[2] = {0.0, 0.0};
             rc = with_workspace(wbytes, st, [&](void *ws) {
-                for (int rep = 0; rep < 2; ++rep) {  // first pass warms up, second is timed
+                for (int rep = 0; rep < 2; ++rep) {  // a small warm-up pass (lazily loaded kernels), then the timed one
+                    const Plan &pl = rep ? plan : warm_plan;
+                    const uint64_t n1 = rep ? nt : kWarmSamples, n2 = rep ? nc : kWarmSamples;
+                    const uint64_t R = rep ? kStatReplicates : kWarmReplicates;
                     LevelParams p;
-                    fill_params(p, l, M, nt, 0, model, payoff, seed, MLMC_TAG_PATHS, plan.lanes, MLMC_FP32_PATH);
+                    fill_params(p, l, M, n1, 0, model, payoff, seed, MLMC_TAG_PATHS, pl.lanes, MLMC_FP32_PATH);
                     p.out = d_out;
                     CUDA_TRY(cudaEventRecord(ev0, st));
-                    int r2 = launch_level(plan, p, ws, st);
+                    int r2 = launch_level(pl, p, ws, st);
                     if (r2) return r2;
                     CUDA_TRY(cudaEventRecord(ev1, st));
                     CUDA_TRY(cudaEventSynchronize(ev1));
-                    inf.t_plain = seconds_per_sample(ev0, ev1, nt);
+                    inf.t_plain = seconds_per_sample(ev0, ev1, n1);
                     CUDA_TRY(cudaEventRecord(ev0, st));
-                    r2 = launch_cv_level(cv, l, nc, 0, seed, d_out, nullptr, nullptr, ws, cvb, st);
+                    r2 = launch_cv_level(cv, l, n2, 0, seed, d_out, nullptr, nullptr, ws, cvb, st);
                     if (r2) return r2;
                     CUDA_TRY(cudaEventRecord(ev1, st));
                     CUDA_TRY(cudaEventSynchronize(ev1));
-                    inf.t_cv = seconds_per_sample(ev0, ev1, nc);
+                    inf.t_cv = seconds_per_sample(ev0, ev1, n2);
                     CUDA_TRY(cudaEventRecord(ev0, st));
                     // replicates far from those of any estimate (which count from 0)
-                    r2 = launch_cv_mean(cv, l, kStatReplicates, 1ull << 40, seed, d_out + 8, nullptr, ws, wbytes,
-                                        false, st);
+                    r2 = launch_cv_mean(cv, l, R, 1ull << 40, seed, d_out + 8, nullptr, ws, wbytes, false, st);
                     if (r2) return r2;
                     CUDA_TRY(cudaEventRecord(ev1, st));
                     CUDA_TRY(cudaEventSynchronize(ev1));
-                    inf.t_mean = seconds_per_sample(ev0, ev1, kStatReplicates * kLatticeN);
+                    inf.t_mean = seconds_per_sample(ev0, ev1, R * kLatticeN);
                 }
                 CUDA_TRY(cudaMemcpy(hq, d_out + 8, sizeof(hq), cudaMemcpyDeviceToHost));
                 return (int)MLMC_OK;

@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
     const TrainJob job = a.job[blockIdx.x / C];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = (kNumParams + C - 1) / C;              // parameters per owner
+    const uint32_t inv_s = (uint32_t)((0x100000000ull + (uint64_t)S - 1) / (uint64_t)S);  // ceil(2^32 / S)
     const int lo = rank * S, nown = max(0, min(S, kNumParams - lo));
     const int rows = a.B / C;                            // this CTA's rows of every batch
     const int chunks = (rows + kTrainChunk - 1) / kTrainChunk;
@@ -437,9 +438,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
             s.grad[off] = v;
         }
         __syncthreads();
-        // push the partial gradient to the owners: owner q keeps C slices, this CTA's at rank S
+        // push the partial gradient to the owners: owner q keeps C slices, this CTA's at rank S.
+        // q = i / S as a multiply-high by ceil(2^32 / S): for i < 4801 and S >= 301 the error
+        // i (ceil(2^32 / S) - 2^32 / S) / 2^32 stays below 1e-6 while i / S is at least 1 / S below
+        // the next integer, so the quotient is exact.
         for (int i = tid; i < kNumParams; i += kTrainThreads) {
-            const int q = i / S;
+            const int q = (int)__umulhi((uint32_t)i, inv_s);
             dsmem_store(dsmem_addr(&s.gin[rank * S + (i - q * S)], (uint32_t)q), s.grad[i]);
         }
         cluster_sync();
