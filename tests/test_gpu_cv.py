@@ -72,12 +72,15 @@ def test_mlp_forward_matches_oracle(mlmc):
     assert np.corrcoef(g, want)[0, 1] > 0.99999
 
 
-def test_mlp_grad_matches_oracle(mlmc):
-    """The project's forward and backward kernels against the oracle's chain rule."""
+@pytest.mark.parametrize("B", [2048, 32, 96, 65536])
+def test_mlp_grad_matches_oracle(mlmc, B):
+    """The project's forward and backward kernels (one step of the training kernel without the
+    update) against the oracle's chain rule.  B = 32 runs on a cluster of 2 CTAs with one tile
+    each, 96 on a cluster of 2 with idle tiles, 2048 on 16 CTAs of 8 tiles, 65536 on 16 CTAs of
+    16 chunks of 256 rows."""
     import torch
 
     rng = np.random.default_rng(2)
-    B = 2048
     X = rng.standard_normal((B, 8)).astype(np.float32)
     Y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + 0.1 * rng.standard_normal(B)).astype(np.float32)
     theta = _params(4)
@@ -192,3 +195,22 @@ def test_training_gains_and_estimates_stay_unbiased(mlmc):
         a = mlmc.mlmc_estimate_cv(eps, cv, seed)
         b = mlmc.mlmc_estimate(eps, p, seed)
         assert a.converged and abs(a.P - b.P) < 3 * math.sqrt(2) * eps, (a.P, b.P)
+
+
+def test_training_repeats_bit_for_bit_and_reports_its_phases(mlmc):
+    """The training launch reduces every gradient in a fixed order (rank-ordered partials over
+    distributed shared memory), so two trainings with the same seeds give identical networks;
+    mlmc_cv_train_info accounts for the call's time."""
+    p = mlmc.Problem(payoff="asian", **GBM)
+    kw = dict(seed=31, levels=2, epochs=3, n_train=100_000, batch=4096, init_seed=2)
+    a = mlmc.mlmc_cv_train(4, p, **kw)
+    b = mlmc.mlmc_cv_train(4, p, **kw)
+    for level in range(2):
+        np.testing.assert_array_equal(mlmc.mlmc_cv_get_params(a, level), mlmc.mlmc_cv_get_params(b, level))
+    info = mlmc.mlmc_cv_train_info(a)
+    assert info["levels"] == 2 and info["cluster"] in (8, 16)
+    assert info["steps"] == 3 * (90_000 // 4096)
+    assert 0 < info["train_kernel_ms"] <= info["train_ms"] * 1.05 + 0.1
+    assert info["total_ms"] >= info["data_ms"] + info["train_ms"] + info["eval_ms"] + info["cost_ms"] - 1.0
+    c = mlmc.mlmc_cv_create(4, p)
+    assert mlmc.mlmc_cv_train_info(c)["steps"] == 0
