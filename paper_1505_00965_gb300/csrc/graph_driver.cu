@@ -13,9 +13,10 @@
 // forms add the same samples in the same order; only CUDA's FP64 log and pow (against the host
 // library's) could move a decision at an exact boundary.
 //
-// Each launch of the graph replays the call's parameters (seed, model, payoff) into every node at
-// the loop's first iteration (a launch resets the device-side updates of the previous one).  The
-// loop is bounded: a driver that reaches kGdMaxIterations stops it with an error status.
+// Device-side node updates persist across launches of the graph, so each launch gives a node the
+// call's parameters (seed, model, payoff) the first time the node runs in that launch, and every
+// finished launch leaves all level nodes disabled.  The loop is bounded: a driver that reaches
+// kGdMaxIterations stops it with an error status.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -511,8 +512,14 @@ int gd_build(GdCache &c, int dev, const int key[10], int M, int Lmax, int precis
             GD_TRY(cudaFuncGetParamInfo(lk.k[v], 0, &off, &size));
             if (off != 0 || size != sizeof(LevelParams))
                 return fail(MLMC_ENOTIMPL, "device-side rounds unavailable: unexpected kernel parameter layout");
-            LevelParams p = {};
-            p.N = 0;
+            // instantiation parameters: a valid one-sample launch into this level's own slot and
+            // sums (the driver kernel gives every node the call's parameters before it first runs
+            // and disables the others; a node that ran on these would still stay in bounds)
+            LevelParams p;
+            fill_params(p, l, M, 1, 0, model, payoff, 1, MLMC_TAG_PATHS, 1, precision);
+            p.out = &c.d_state->sums[l][0];
+            p.ticket = (unsigned *)((char *)c.slots + c.slot_bytes * (size_t)l);
+            p.partials = (double *)((char *)c.slots + c.slot_bytes * (size_t)l + kTicketBytes);
             void *kargs[] = {&p};
             cudaKernelNodeParams kp = {};
             kp.func = const_cast<void *>(lk.k[v]);

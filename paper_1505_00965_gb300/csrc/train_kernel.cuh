@@ -122,21 +122,9 @@ __device__ __forceinline__ void ldsm_x2_trans(const void *p, uint32_t &r0, uint3
                  : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
 
-// GELU and its derivative from one hardware tanh: with u = sqrt(2/pi) (z + 0.044715 z^3) and
-// t = tanh(u), GELU(z) = z (1 + t) / 2 and GELU'(z) = (1 + t) / 2 + z (1 - t^2) u'(z) / 2.
-__device__ __forceinline__ void gelu_and_grad(float z, float &h, float &dh)
-{
-    const float z2 = z * z;
-    const float u = z * fmaf(0.035677408136300125f, z2, 0.7978845608028654f);
-    const float du = fmaf(3.0f * 0.035677408136300125f, z2, 0.7978845608028654f);
-    const float t = tanh_approx(u);
-    const float hz = 0.5f * z;
-    h = fmaf(hz, t, hz);
-    dh = fmaf(0.5f, t, 0.5f) + hz * fmaf(-t, t, 1.0f) * du;
-}
-
-// gelu_and_grad on both halves of a packed pair (packed FP32 arithmetic, the same operations;
-// the last line's add is a fused multiply-add here).
+// GELU and its derivative from one hardware tanh, on both halves of a packed pair (packed FP32
+// arithmetic): with u = sqrt(2/pi) (z + 0.044715 z^3) and t = tanh(u), GELU(z) = z (1 + t) / 2
+// and GELU'(z) = (1 + t) / 2 + z (1 - t^2) u'(z) / 2.
 __device__ __forceinline__ void gelu_and_grad2(f32x2 z, f32x2 &h, f32x2 &dh)
 {
     const f32x2 z2 = f2_mul(z, z);
