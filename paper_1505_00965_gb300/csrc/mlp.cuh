@@ -7,7 +7,11 @@
 // fragments (the m16n8 accumulator layout of two adjacent column tiles is the m16k16 operand
 // layout), so hidden values never leave registers.
 //
-// GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), tanh from the hardware unit.
+// GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), tanh from the hardware unit.  The
+// kernels evaluate 2 GELU(z) = z + z tanh(.) and take the factor 1/2 into the weights that
+// consume it (W2 and w3 halved when they are loaded).  Scaling by a power of two commutes with
+// every rounding involved (FP32 fma, bfloat16 conversion, the exact bfloat16 products of the
+// tensor cores) for values outside the subnormal range, so g is bit-identical to the plain form.
 #pragma once
 #include <cstdint>
 
@@ -25,17 +29,26 @@ constexpr int kOffW3 = kOffB2 + kHidden;
 constexpr int kOffB3 = kOffW3 + kHidden;
 constexpr int kNumParams = kOffB3 + 1;  // 4801
 
-// Network in shared memory: weights as packed bfloat16 pairs, the rest FP32.  A W2 row takes
-// kW2Stride = 36 words (32 used): the layer-2 operand loads of a warp read word 8 kt + t of rows
-// g = 0..7, which a stride of 32 would put in the same four banks; with 36 the 32 lanes hit 32
-// distinct banks.
+// Network in shared memory, laid out so that each lane fetches its operand fragments with
+// 16-byte loads:
+// - L1[32 nt + lane] = {W1 pair word of row 8 nt + g, columns 2t and 2t + 1 (lane = 4 g + t);
+//   b1[8 nt + 2t]; b1[8 nt + 2t + 1]; 0}: one load gives a layer-1 column tile's B fragment and
+//   bias pair.
+// - W2: row o holds the 32 bfloat16 pairs (W2[o][2j], W2[o][2j+1]) / 2 in the order a lane of
+//   quad index t reads them, words 8 kt + t and 8 kt + t + 4 for kt = 0..3 at positions
+//   8 t + 2 kt and 8 t + 2 kt + 1, so its eight words are two 16-byte loads.  A row takes
+//   kW2Stride = 36 words: a quarter warp (rows g, g + 1 at t = 0..3) then covers all 32 banks.
+// - b2w3[i] = {b2[2i], b2[2i+1], w3[2i] / 2, w3[2i+1] / 2}.
 constexpr int kW2Stride = kHidden / 2 + 4;
 struct MlpShared {
-    uint32_t W1[kHidden * kInputs / 2];   // row o: 4 words of pairs (W1[o][2t], W1[o][2t+1])
-    uint32_t W2[kHidden * kW2Stride];     // row o: 32 words of pairs (W2[o][2j], W2[o][2j+1]), then 4 unused
-    float b1[kHidden], b2[kHidden], w3[kHidden];
+    uint4 L1[8 * 32];
+    uint32_t W2[kHidden * kW2Stride];
+    float4 b2w3[kHidden / 2];
     float b3;
 };
+
+// Position within a W2 row of the pair word w = 8 kt + 4 half + t (see MlpShared).
+__host__ __device__ constexpr int w2_slot(int w) { return 8 * (w & 3) + 2 * (w >> 3) + ((w >> 2) & 1); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
@@ -49,14 +62,6 @@ __device__ __forceinline__ float tanh_approx(float x)
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-__device__ __forceinline__ float gelu(float z)
-{
-    // sqrt(2/pi) (z + 0.044715 z^3) = z (sqrt(2/pi) + 0.044715 sqrt(2/pi) z^2)
-    const float u = z * fmaf(0.035677408136300125f, z * z, 0.7978845608028654f);
-    const float hz = 0.5f * z;
-    return fmaf(hz, tanh_approx(u), hz);
 }
 
 // Two FP32 values in one 64-bit register pair, for the packed FP32 arithmetic of sm_100 and
@@ -92,15 +97,14 @@ __device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
 }
 __device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
 
-// GELU of both halves: the operations of gelu() in the same order, two values per instruction
-// (bit-identical to gelu() on each half).
-__device__ __forceinline__ f32x2 gelu2(f32x2 z)
+// 2 GELU(z) of both halves: u = z (sqrt(2/pi) + 0.044715 sqrt(2/pi) z^2), then z + z tanh(u)
+// (each half equals twice the scalar z/2 + (z/2) tanh(u) exactly).
+__device__ __forceinline__ f32x2 twice_gelu2(f32x2 z)
 {
     const f32x2 p = f2_fma(f2_mul(z, z), f2_splat(0.035677408136300125f), f2_splat(0.7978845608028654f));
     float u0, u1;
     f2_unpack(f2_mul(z, p), u0, u1);
-    const f32x2 hz = f2_mul(z, f2_splat(0.5f));
-    return f2_fma(hz, f2_pack(tanh_approx(u0), tanh_approx(u1)), hz);
+    return f2_fma(z, f2_pack(tanh_approx(u0), tanh_approx(u1)), z);
 }
 
 // The bfloat16 pair of a packed pair (low half in the low 16 bits).
@@ -124,15 +128,17 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32
 // Copy packed FP32 parameters into shared memory (all threads of the block take part).
 __device__ __forceinline__ void load_mlp(MlpShared &s, const float *__restrict__ params)
 {
-    for (int i = threadIdx.x; i < kHidden * kInputs / 2; i += blockDim.x)
-        s.W1[i] = pack_bf16x2(params[kOffW1 + 2 * i], params[kOffW1 + 2 * i + 1]);
-    for (int i = threadIdx.x; i < kHidden * kHidden / 2; i += blockDim.x)
-        s.W2[(i >> 5) * kW2Stride + (i & 31)] = pack_bf16x2(params[kOffW2 + 2 * i], params[kOffW2 + 2 * i + 1]);
-    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
-        s.b1[i] = params[kOffB1 + i];
-        s.b2[i] = params[kOffB2 + i];
-        s.w3[i] = params[kOffW3 + i];
+    for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) {
+        const int nt = i >> 5, g = (i & 31) >> 2, t = i & 3, row = 8 * nt + g, o = 8 * nt + 2 * t;
+        s.L1[i] = make_uint4(pack_bf16x2(params[kOffW1 + row * kInputs + 2 * t], params[kOffW1 + row * kInputs + 2 * t + 1]),
+                             __float_as_uint(params[kOffB1 + o]), __float_as_uint(params[kOffB1 + o + 1]), 0u);
     }
+    for (int i = threadIdx.x; i < kHidden * kHidden / 2; i += blockDim.x)
+        s.W2[(i >> 5) * kW2Stride + w2_slot(i & 31)] =
+            pack_bf16x2(0.5f * params[kOffW2 + 2 * i], 0.5f * params[kOffW2 + 2 * i + 1]);
+    for (int i = threadIdx.x; i < kHidden / 2; i += blockDim.x)
+        s.b2w3[i] = make_float4(params[kOffB2 + 2 * i], params[kOffB2 + 2 * i + 1], 0.5f * params[kOffW3 + 2 * i],
+                                0.5f * params[kOffW3 + 2 * i + 1]);
     if (threadIdx.x == 0) s.b3 = params[kOffB3];
 }
 
@@ -144,30 +150,34 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // layer 1: A = x (16 x 16, columns 8..15 zero), B[k][n] = W1[n][k]
     uint32_t a[4] = {xw[g * 4 + t], xw[(g + 8) * 4 + t], 0u, 0u};
-    // layer 1, then A = GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1); GELU on the
+    // layer 1, then A = 2 GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1); GELU on the
     // accumulator pairs (columns 2t, 2t + 1 of rows g and g + 8) with packed FP32 arithmetic
     uint32_t a2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        const int o = 8 * nt + 2 * t;
-        float c[4] = {s.b1[o], s.b1[o + 1], s.b1[o], s.b1[o + 1]};
-        mma_bf16(c, a, s.W1[(8 * nt + g) * 4 + t], 0u);
-        a2[nt >> 1][(nt & 1) * 2] = pack_bf16x2_f2(gelu2(f2_pack(c[0], c[1])));
-        a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2_f2(gelu2(f2_pack(c[2], c[3])));
+        const uint4 l1 = s.L1[32 * nt + lane];
+        const float b1a = __uint_as_float(l1.y), b1b = __uint_as_float(l1.z);
+        float c[4] = {b1a, b1b, b1a, b1b};
+        mma_bf16(c, a, l1.x, 0u);
+        a2[nt >> 1][(nt & 1) * 2] = pack_bf16x2_f2(twice_gelu2(f2_pack(c[0], c[1])));
+        a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2_f2(twice_gelu2(f2_pack(c[2], c[3])));
     }
-    // layer 2, B[k][n] = W2[n][k]; layer 3: the dot product with w3 over this lane's units, rows g
-    // and g + 8, in packed pairs (units o and o + 1 summed at the end)
+    // layer 2, B[k][n] = W2[n][k] / 2; layer 3: the dot product with w3 / 2 over this lane's
+    // units, rows g and g + 8, in packed pairs (units o and o + 1 summed at the end)
     f32x2 q0 = f2_splat(0.f), q1 = f2_splat(0.f);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        const int o = 8 * nt + 2 * t;
-        float c[4] = {s.b2[o], s.b2[o + 1], s.b2[o], s.b2[o + 1]};
-        const uint32_t *w = &s.W2[(8 * nt + g) * kW2Stride];
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) mma_bf16(c, a2[kt], w[8 * kt + t], w[8 * kt + t + 4]);
-        const f32x2 w3 = f2_pack(s.w3[o], s.w3[o + 1]);
-        q0 = f2_fma(w3, gelu2(f2_pack(c[0], c[1])), q0);
-        q1 = f2_fma(w3, gelu2(f2_pack(c[2], c[3])), q1);
+        const float4 bw = s.b2w3[4 * nt + t];
+        float c[4] = {bw.x, bw.y, bw.x, bw.y};
+        const uint4 *w = reinterpret_cast<const uint4 *>(&s.W2[(8 * nt + g) * kW2Stride + 8 * t]);
+        const uint4 w01 = w[0], w23 = w[1];
+        mma_bf16(c, a2[0], w01.x, w01.y);
+        mma_bf16(c, a2[1], w01.z, w01.w);
+        mma_bf16(c, a2[2], w23.x, w23.y);
+        mma_bf16(c, a2[3], w23.z, w23.w);
+        const f32x2 w3 = f2_pack(bw.z, bw.w);
+        q0 = f2_fma(w3, twice_gelu2(f2_pack(c[0], c[1])), q0);
+        q1 = f2_fma(w3, twice_gelu2(f2_pack(c[2], c[3])), q1);
     }
     float p0, p1, e0, e1;
     f2_unpack(q0, p0, e0);

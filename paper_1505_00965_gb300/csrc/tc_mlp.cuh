@@ -8,7 +8,8 @@
 // The epilogues read the accumulator with tcgen05.ld (thread t of the CTA owns row t, i.e. one
 // sample), add the bias and apply GELU in FP32 with the hardware tanh; layer 1's result is
 // rounded to bfloat16 and written back to shared memory as layer 2's A operand.  The numerics
-// are those of the mma.sync form (bfloat16 x, W1, W2, GELU(z1); FP32 accumulation and epilogue).
+// are those of the mma.sync form (bfloat16 x, W1, W2, GELU(z1); FP32 accumulation and epilogue),
+// including its exact folding of GELU's factor 1/2 into W2 and w3.
 //
 // Operand layout (no swizzle, K-major): 8 x 8 bfloat16 "core matrices" of 128 contiguous bytes
 // (row r at byte 16 r); the two core matrices of one MMA's K = 16 sit LBO = 128 bytes apart and
@@ -27,10 +28,10 @@ constexpr uint32_t kTcWaitLimit = 1u << 22;  // mbarrier polls before a tile is 
 
 struct TcShared {
     alignas(1024) uint8_t a1[kTcRows * 16 * 2];      // x: 128 x 16 bfloat16 (k = 8..15 zero), SBO 256
-    alignas(1024) uint8_t a2[kTcRows * 64 * 2];      // GELU(z1): 128 x 64 bfloat16, SBO 1024
+    alignas(1024) uint8_t a2[kTcRows * 64 * 2];      // 2 GELU(z1): 128 x 64 bfloat16, SBO 1024
     alignas(1024) uint8_t w1[kHidden * 16 * 2];      // W1: 64 x 16 bfloat16 (k = 8..15 zero), SBO 256
-    alignas(1024) uint8_t w2[kHidden * 64 * 2];      // W2: 64 x 64 bfloat16, SBO 1024
-    float b1[kHidden], b2[kHidden], w3[kHidden];
+    alignas(1024) uint8_t w2[kHidden * 64 * 2];      // W2 / 2: 64 x 64 bfloat16, SBO 1024
+    float b1[kHidden], b2[kHidden], w3[kHidden];     // w3 halved
     float b3;
     alignas(8) uint64_t mbar;
     uint32_t tmem_base;
@@ -129,15 +130,15 @@ __device__ __forceinline__ uint32_t tc_setup(TcShared &s, const float *__restric
         const float hi = k < kInputs ? params[kOffW1 + n * kInputs + k + 1] : 0.f;
         *reinterpret_cast<uint32_t *>(s.w1 + cm_byte(n, k, 256)) = pack_bf16x2(lo, hi);
     }
-    for (int i = tid; i < kHidden * 32; i += blockDim.x) {  // W2 pairs
+    for (int i = tid; i < kHidden * 32; i += blockDim.x) {  // W2 / 2 pairs (the epilogues form 2 GELU)
         const int n = i >> 5, k = 2 * (i & 31);
         *reinterpret_cast<uint32_t *>(s.w2 + cm_byte(n, k, 1024)) =
-            pack_bf16x2(params[kOffW2 + n * kHidden + k], params[kOffW2 + n * kHidden + k + 1]);
+            pack_bf16x2(0.5f * params[kOffW2 + n * kHidden + k], 0.5f * params[kOffW2 + n * kHidden + k + 1]);
     }
     for (int i = tid; i < kHidden; i += blockDim.x) {
         s.b1[i] = params[kOffB1 + i];
         s.b2[i] = params[kOffB2 + i];
-        s.w3[i] = params[kOffW3 + i];
+        s.w3[i] = 0.5f * params[kOffW3 + i];
     }
     if (tid == 0) {
         s.b3 = params[kOffB3];
@@ -188,8 +189,8 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
     ok = mbar_wait(&s.mbar, phase) && ok;
     phase ^= 1u;
     tc_fence_after();
-    // epilogue 1: GELU(z1 + b1) as bfloat16 into the layer-2 A operand, 16 columns at a time, in
-    // packed FP32 pairs
+    // epilogue 1: 2 GELU(z1 + b1) as bfloat16 into the layer-2 A operand (the layer-2 weights are
+    // halved), 16 columns at a time, in packed FP32 pairs
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float z[16];
@@ -197,7 +198,7 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
         uint32_t h[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            h[j] = pack_bf16x2_f2(gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]),
+            h[j] = pack_bf16x2_f2(twice_gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]),
                                                f2_pack(s.b1[16 * c + 2 * j], s.b1[16 * c + 2 * j + 1]))));
         *reinterpret_cast<uint4 *>(s.a2 + cm_byte(tid, 16 * c, 1024)) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(s.a2 + cm_byte(tid, 16 * c + 8, 1024)) = make_uint4(h[4], h[5], h[6], h[7]);
@@ -216,8 +217,8 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
     ok = mbar_wait(&s.mbar, phase) && ok;
     phase ^= 1u;
     tc_fence_after();
-    // epilogue 2: g = b3 + sum_o w3_o GELU(z2_o + b2_o), in packed FP32 pairs (even and odd units
-    // summed apart, then together)
+    // epilogue 2: g = b3 + sum_o (w3_o / 2) 2 GELU(z2_o + b2_o), in packed FP32 pairs (even and odd
+    // units summed apart, then together)
     f32x2 q = f2_splat(0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -226,7 +227,7 @@ __device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const f
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int o = 16 * c + 2 * j;
-            const f32x2 h = gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]), f2_pack(s.b2[o], s.b2[o + 1])));
+            const f32x2 h = twice_gelu2(f2_add(f2_pack(z[2 * j], z[2 * j + 1]), f2_pack(s.b2[o], s.b2[o + 1])));
             q = f2_fma(f2_pack(s.w3[o], s.w3[o + 1]), h, q);
         }
     }
