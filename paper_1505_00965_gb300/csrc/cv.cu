@@ -37,12 +37,12 @@ constexpr double kMinKappa = 1.0 / 64.0, kMaxKappa = 4096.0;  // mean points per
 const void *cv_level_kernel_for(int payoff)
 {
     switch (payoff) {
-    case kEuropean: return (const void *)cv_level_kernel<kEuropean>;
-    case kAsian: return (const void *)cv_level_kernel<kAsian>;
-    case kLookback: return (const void *)cv_level_kernel<kLookback>;
-    case kDigital: return (const void *)cv_level_kernel<kDigital>;
-    case kLinear: return (const void *)cv_level_kernel<kLinear>;
-    case kGeoAsian: return (const void *)cv_level_kernel<kGeoAsian>;
+    case kEuropean: return (const void *)cv_level_tc_kernel<kEuropean>;
+    case kAsian: return (const void *)cv_level_tc_kernel<kAsian>;
+    case kLookback: return (const void *)cv_level_tc_kernel<kLookback>;
+    case kDigital: return (const void *)cv_level_tc_kernel<kDigital>;
+    case kLinear: return (const void *)cv_level_tc_kernel<kLinear>;
+    case kGeoAsian: return (const void *)cv_level_tc_kernel<kGeoAsian>;
     default: return nullptr;
     }
 }
@@ -67,6 +67,39 @@ int grid_for(const void *kernel, uint64_t items, int *blocks)
     if (rc) return rc;
     const double need = std::ceil((double)std::max<uint64_t>(items, 1) / kCvThreads);
     *blocks = (int)std::max(1.0, std::min<double>(need, resident));
+    return MLMC_OK;
+}
+
+// Grid of the tcgen05 level kernel, in waves of the blocks an SM holds by shared memory,
+// registers, threads and tensor memory (64 columns of 512 per block).  The occupancy query reports
+// one block per SM for this kernel although six run at once (a launch of six blocks per SM runs
+// 2.2 times faster than one of one block per SM), so the count comes from the kernel's attributes.
+// Up to four waves when every block still gets at least eight tiles (the blocks of an SM then fall
+// out of step: 5% faster than one wave at 4e7 samples); one wave otherwise, since each block pays
+// for loading the network and for its share of the final reduction.
+int cv_level_grid(int payoff, uint64_t items, int *blocks)
+{
+    const void *k = cv_level_kernel_for(payoff);
+    if (!k) return fail(MLMC_EINVAL, "payoff %d has no control-variate kernel", payoff);
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserved = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const int warps = kCvTcThreads / 32;
+    const int regs_block = warps * ((fa.numRegs * 32 + 255) / 256) * 256;  // 256-register warp granules
+    int per_sm = std::min({smem_sm / std::max(1, (int)fa.sharedSizeBytes + reserved), regs_sm / std::max(1, regs_block),
+                           thr_sm / kCvTcThreads, 512 / (int)kTcCols});
+    per_sm = std::max(per_sm, 1);
+    const double need = std::ceil((double)std::max<uint64_t>(items, 1) / kCvTcThreads);
+    const double slots = (double)per_sm * sms;
+    const double waves = std::min(4.0, std::max(1.0, std::floor(need / (8.0 * slots))));
+    *blocks = (int)std::max(1.0, std::min(need, waves * slots));
     return MLMC_OK;
 }
 
@@ -100,7 +133,7 @@ int launch_cv_level(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, ui
     p.partials = (double *)((char *)ws + kTicketBytes);
     const float *params = cv->d_params[level];
     void *args[] = {&p, (void *)&params, &d_sums8, &d_r, &d_g};
-    CUDA_TRY(cudaLaunchKernel(cv_level_kernel_for(cv->payoff.kind), dim3(blocks), dim3(kCvThreads), args, 0, st));
+    CUDA_TRY(cudaLaunchKernel(cv_level_kernel_for(cv->payoff.kind), dim3(blocks), dim3(kCvTcThreads), args, 0, st));
     return MLMC_OK;
 }
 
@@ -332,7 +365,7 @@ int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first,
         return MLMC_OK;
     }
     int blocks = 0;
-    rc = grid_for(cv_level_kernel_for(cv->payoff.kind), N, &blocks);
+    rc = cv_level_grid(cv->payoff.kind, N, &blocks);
     if (rc) return rc;
     return with_workspace(sums_workspace(blocks, 8), st, [&](void *ws) {
         return launch_cv_level(cv, level, N, first, seed, d_sums8, d_r, d_g, ws, blocks, st);
@@ -578,7 +611,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
                                      &warm_plan);
             if (rc) return cleanup(rc);
             int cvb = 0;
-            rc = grid_for(cv_level_kernel_for(payoff->kind), nc, &cvb);
+            rc = cv_level_grid(payoff->kind, nc, &cvb);
             if (rc) return cleanup(rc);
             // the lattice statistics use kStatReplicates replicates (2^23 points)
             constexpr uint64_t kStatReplicates = 128;
@@ -732,7 +765,7 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
             if (uses(l)) {
                 drep[l] = mean_replicates(cv->info[l].kappa, dN[l], nrep[l]);
                 int cb = 0;
-                rc = grid_for(cv_level_kernel_for(payoff->kind), dN[l], &cb);
+                rc = cv_level_grid(payoff->kind, dN[l], &cb);
                 if (!rc)
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
                                          nullptr, ws, std::min(cb, ws_blocks), sk);

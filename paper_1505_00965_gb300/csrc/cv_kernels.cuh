@@ -138,13 +138,14 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, uint64_t s, floa
 }
 
 // Sum NV doubles over the grid: block partials into `partials`, the last block to finish adds
-// them in block order into out.  The ticket is zero between launches.
+// them into out (every thread a fixed stride of blocks in block order, then the threads in a fixed
+// tree), so the sums repeat bit for bit for a given grid.  The ticket is zero between launches.
 template <int NV>
 __device__ __forceinline__ void finish_sums_n(double m[NV], double *partials, unsigned *ticket, double *out)
 {
     __shared__ double sm[32][NV];
     __shared__ bool is_last;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) m[k] = warp_sum(m[k]);
     if (lane == 0) {
@@ -153,7 +154,6 @@ __device__ __forceinline__ void finish_sums_n(double m[NV], double *partials, un
     }
     __syncthreads();
     if (warp == 0) {
-        const int nw = blockDim.x >> 5;
 #pragma unroll
         for (int k = 0; k < NV; ++k) m[k] = warp_sum(lane < nw ? sm[lane][k] : 0.0);
         if (lane == 0) {
@@ -166,52 +166,65 @@ __device__ __forceinline__ void finish_sums_n(double m[NV], double *partials, un
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (warp == 0) {
-        double acc[NV];
+    double acc[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) {
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+#pragma unroll 4
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
 #pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + NV * b + k);
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + NV * b + k);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[warp][k] = acc[k];  // sm's earlier values were read before the barrier above
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sm[w][k];
+            out[k] = t;
         }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) out[k] = acc[k];
-            *ticket = 0u;
-        }
+        *ticket = 0u;
     }
 }
 
 // Control-variate level estimator: per sample r = Y - g(x); sums
-// [r, r^2, r^3, r^4, Y, Y^2, g, g^2] (FP64).  One thread per sample, whole warps evaluate g.
-// Each thread adds batches of kCvBatch samples in FP32 and folds every batch into its FP64 sums
-// (relative error of a batch sum at most (kCvBatch - 1) u of its sum of magnitudes, 4.2e-7): the
-// eight FP64 updates per sample kept GB300's FP64 pipe (2 operations per SM per clock) 47% busy.
+// [r, r^2, r^3, r^4, Y, Y^2, g, g^2] (FP64).  Each thread adds batches of kCvBatch samples in FP32
+// and folds every batch into its FP64 sums (relative error of a batch sum at most
+// (kCvBatch - 1) u of its sum of magnitudes, 4.2e-7): eight FP64 updates per sample kept GB300's
+// FP64 pipe (2 operations per SM per clock) 47% busy.
 constexpr int kCvBatch = 8;
+
+// The network runs on the tcgen05 tensor cores (tc_mlp.cuh), the function the lattice mean kernel
+// evaluates, so that the samples of Y - g and the estimate of E[g] use one g.
+// 128 threads, one sample per thread and tile; each block strides over tiles of 128 samples (the
+// stride is uniform over the block, so all its threads reach the tile's barriers; the lanes past
+// N compute copies of sample N - 1 and add nothing).  A tile whose tensor-core wait ran out
+// makes the sums NaN (the driver then stops on non-finite sums).
+constexpr int kCvTcThreads = kTcRows;
 template <int PAY>
-__global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, const float *__restrict__ params,
-                                                       double *out8, float *r_out, float *g_out)
+__global__ void __launch_bounds__(kCvTcThreads) cv_level_tc_kernel(const LevelParams p, const float *__restrict__ params,
+                                                                   double *out8, float *r_out, float *g_out)
 {
-    __shared__ MlpShared net;
-    __shared__ __align__(16) uint32_t xw_all[8][128];  // 16-byte rows: warp_mlp stores uint4
-    load_mlp(net, params);
-    __syncthreads();
-    uint32_t *xw = xw_all[threadIdx.x >> 5];
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t warp_first = tid & ~uint64_t(31);
+    __shared__ TcShared ts;
+    const uint32_t tmem = tc_setup(ts, params);
     double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float b[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int nb = 0;
-    for (uint64_t base = 0; base + warp_first < p.N; base += stride) {
-        const uint64_t idx = base + tid;
+    uint32_t phase = 0;
+    bool ok = true;
+    const uint64_t tile_stride = (uint64_t)gridDim.x * kCvTcThreads;
+#pragma unroll 1
+    for (uint64_t base = (uint64_t)blockIdx.x * kCvTcThreads; base < p.N; base += tile_stride) {
+        const uint64_t idx = base + threadIdx.x;
         const bool valid = idx < p.N;
-        const uint64_t s = p.first + (valid ? idx : p.N - 1);
         float Y, x[8];
-        cv_sample<PAY>(p, s, Y, x);
-        const float gv = warp_mlp(net, xw, x);
+        cv_sample<PAY>(p, p.first + (valid ? idx : p.N - 1), Y, x);
+        const float gv = tc_mlp_tile(ts, tmem, x, phase, ok);
         if (valid) {
             const float r = Y - gv, r2 = r * r;
             b[0] += r;
@@ -234,8 +247,9 @@ __global__ void __launch_bounds__(256) cv_level_kernel(const LevelParams p, cons
             if (g_out) g_out[idx] = gv;
         }
     }
+    tc_teardown(ts, tmem);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) m[k] += (double)b[k];
+    for (int k = 0; k < 8; ++k) m[k] = ok ? m[k] + (double)b[k] : __longlong_as_double(0x7FF8000000000000LL);
     finish_sums_n<8>(m, p.partials, p.ticket, out8);
 }
 
