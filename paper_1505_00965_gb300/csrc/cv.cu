@@ -74,9 +74,10 @@ int grid_for(const void *kernel, uint64_t items, int *blocks)
 // registers, threads and tensor memory (64 columns of 512 per block).  The occupancy query reports
 // one block per SM for this kernel although six run at once (a launch of six blocks per SM runs
 // 2.2 times faster than one of one block per SM), so the count comes from the kernel's attributes.
-// Up to four waves when every block still gets at least eight tiles (the blocks of an SM then fall
+// Up to four waves when every block still gets at least 32 tiles (the blocks of an SM then fall
 // out of step: 5% faster than one wave at 4e7 samples); one wave otherwise, since each block pays
-// for loading the network and for its share of the final reduction.
+// for loading the network and for the FP64 warp reductions of its eight sums (with 8.6 tiles per
+// block these kept the FP64 pipe 20% busy).
 int cv_level_grid(int payoff, uint64_t items, int *blocks)
 {
     const void *k = cv_level_kernel_for(payoff);
@@ -98,7 +99,7 @@ int cv_level_grid(int payoff, uint64_t items, int *blocks)
     per_sm = std::max(per_sm, 1);
     const double need = std::ceil((double)std::max<uint64_t>(items, 1) / kCvTcThreads);
     const double slots = (double)per_sm * sms;
-    const double waves = std::min(4.0, std::max(1.0, std::floor(need / (8.0 * slots))));
+    const double waves = std::min(4.0, std::max(1.0, std::floor(need / (32.0 * slots))));
     *blocks = (int)std::max(1.0, std::min(need, waves * slots));
     return MLMC_OK;
 }

@@ -18,12 +18,26 @@
 
 namespace mlmcgb {
 
+// The FP32 constants of a level's paths and payoff, converted once from the FP64 parameters (a
+// conversion from FP64 runs on the FP64 pipe, 2 per SM per clock on GB300; kernels keep these in
+// shared memory so the compiler reloads them instead of converting again in every sample).
+// scale = sqrt_h / sqrt_t8 and inv_t8 = 1 / sqrt_t8 are the FP32 quotients of the converted values.
+struct CvConsts {
+    float a, rh, S0, sqrt_h, sqrt_t8, inv_nf, inv_nc, K, disc, Q, scale, inv_t8;
+};
+__device__ __forceinline__ CvConsts cv_consts(const LevelParams &p)
+{
+    const float sqrt_h = (float)p.sqrt_h, sqrt_t8 = (float)p.sqrt_t8;
+    return {(float)p.a, (float)p.rh, (float)p.S0, sqrt_h, sqrt_t8, (float)p.inv_nf, (float)p.inv_nc,
+            (float)p.K, (float)p.disc, (float)p.Q, sqrt_h / sqrt_t8, 1.0f / sqrt_t8};
+}
+
 template <int PAY>
-__device__ __forceinline__ void cv_sample(const LevelParams &p, uint64_t s, float &Y, float x[8])
+__device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &k, uint64_t s, float &Y, float x[8])
 {
     const int nf = p.nf, M = p.M;
-    const float a = (float)p.a, rh = (float)p.rh, S0 = (float)p.S0;
-    const float sqrt_h = (float)p.sqrt_h, sqrt_t8 = (float)p.sqrt_t8;
+    const float a = k.a, rh = k.rh, S0 = k.S0;
+    const float sqrt_h = k.sqrt_h, sqrt_t8 = k.sqrt_t8;
     float fS = 1.f, fsum = 0.f, fhi = 1.f, flo = 1.f, fls = 0.f;
     float cS = 1.f, csum = 0.f, chi = 1.f, clo = 1.f, cls = 0.f;
     float dc = 0.f;
@@ -67,7 +81,7 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, uint64_t s, floa
     } else {
         const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
         const int per8 = nf >= 8 ? nf / 8 : 0;
-        const float scale = sqrt_h / sqrt_t8;
+        const float scale = k.scale;
         float acc = 0.f, W = 0.f;
         int f = 0, cnt = 0;
         grid[0] = 0.f;
@@ -121,18 +135,18 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, uint64_t s, floa
                 grid[mid] = 0.5f * (grid[left] + grid[left + width]) + sd * zb[next++];
             }
         }
-        const float inv = 1.0f / sqrt_t8;
+        const float inv = k.inv_t8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] = (grid[k + 1] - grid[k]) * inv;
     }
     const float logS0 = PAY == kGeoAsian ? logf(S0) : 0.f;
-    const float Pf = payoff_value<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, (float)nf * logS0 + fls,
-                                              (float)p.inv_nf, p);
+    const float Pf = payoff_from<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, (float)nf * logS0 + fls, k.inv_nf, k.K,
+                                             k.disc, S0, k.Q);
     if (p.level == 0) {
         Y = Pf;
     } else {
-        const float Pc = payoff_value<float, PAY>(S0 * cS, S0 * csum, S0 * chi, (float)(nf / M) * logS0 + cls,
-                                                  (float)p.inv_nc, p);
+        const float Pc = payoff_from<float, PAY>(S0 * cS, S0 * csum, S0 * chi, (float)(nf / M) * logS0 + cls,
+                                                 k.inv_nc, k.K, k.disc, S0, k.Q);
         Y = Pf - Pc;
     }
 }
@@ -211,45 +225,46 @@ __global__ void __launch_bounds__(kCvTcThreads) cv_level_tc_kernel(const LevelPa
                                                                    double *out8, float *r_out, float *g_out)
 {
     __shared__ TcShared ts;
-    const uint32_t tmem = tc_setup(ts, params);
+    __shared__ CvConsts kc;
+    if (threadIdx.x == 0) kc = cv_consts(p);
+    const uint32_t tmem = tc_setup(ts, params);  // ends with a block barrier
     double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float b[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int nb = 0;
     uint32_t phase = 0;
     bool ok = true;
     const uint64_t tile_stride = (uint64_t)gridDim.x * kCvTcThreads;
+    uint64_t base = (uint64_t)blockIdx.x * kCvTcThreads;
+    // batches of kCvBatch tiles, each folded into the FP64 sums after its loop (a fold inside the
+    // tile loop was compiled as predicated FP64 work on every tile: FP64 pipe 42% busy)
 #pragma unroll 1
-    for (uint64_t base = (uint64_t)blockIdx.x * kCvTcThreads; base < p.N; base += tile_stride) {
-        const uint64_t idx = base + threadIdx.x;
-        const bool valid = idx < p.N;
-        float Y, x[8];
-        cv_sample<PAY>(p, p.first + (valid ? idx : p.N - 1), Y, x);
-        const float gv = tc_mlp_tile(ts, tmem, x, phase, ok);
-        if (valid) {
-            const float r = Y - gv, r2 = r * r;
-            b[0] += r;
-            b[1] += r2;
-            b[2] = fmaf(r2, r, b[2]);
-            b[3] = fmaf(r2, r2, b[3]);
-            b[4] += Y;
-            b[5] = fmaf(Y, Y, b[5]);
-            b[6] += gv;
-            b[7] = fmaf(gv, gv, b[7]);
-            if (++nb == kCvBatch) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    m[k] += (double)b[k];
-                    b[k] = 0.f;
-                }
-                nb = 0;
+    while (base < p.N) {
+        float b[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int j = 0; j < kCvBatch && base < p.N; ++j, base += tile_stride) {
+            const uint64_t idx = base + threadIdx.x;
+            const bool valid = idx < p.N;
+            float Y, x[8];
+            cv_sample<PAY>(p, kc, p.first + (valid ? idx : p.N - 1), Y, x);
+            const float gv = tc_mlp_tile(ts, tmem, x, phase, ok);
+            if (valid) {
+                const float r = Y - gv, r2 = r * r;
+                b[0] += r;
+                b[1] += r2;
+                b[2] = fmaf(r2, r, b[2]);
+                b[3] = fmaf(r2, r2, b[3]);
+                b[4] += Y;
+                b[5] = fmaf(Y, Y, b[5]);
+                b[6] += gv;
+                b[7] = fmaf(gv, gv, b[7]);
+                if (r_out) r_out[idx] = r;
+                if (g_out) g_out[idx] = gv;
             }
-            if (r_out) r_out[idx] = r;
-            if (g_out) g_out[idx] = gv;
         }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m[k] += (double)b[k];
     }
     tc_teardown(ts, tmem);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) m[k] = ok ? m[k] + (double)b[k] : __longlong_as_double(0x7FF8000000000000LL);
+    for (int k = 0; k < 8; ++k) m[k] = ok ? m[k] : __longlong_as_double(0x7FF8000000000000LL);
     finish_sums_n<8>(m, p.partials, p.ticket, out8);
 }
 
@@ -372,9 +387,10 @@ __global__ void __launch_bounds__(256) cv_data_kernel(const LevelParams p, float
 {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const CvConsts kc = cv_consts(p);
     for (uint64_t idx = tid; idx < p.N; idx += stride) {
         float Y, x[8];
-        cv_sample<PAY>(p, p.first + idx, Y, x);
+        cv_sample<PAY>(p, kc, p.first + idx, Y, x);
         Yout[idx] = Y;
 #pragma unroll
         for (int k = 0; k < 8; ++k) X[8 * idx + k] = x[k];

@@ -76,12 +76,11 @@ __device__ __forceinline__ void em_step(R &S, R &sum, R &hi, R &lo, R &lsum, R d
 }
 
 // Discounted payoff of a path from its totals: final value Sn, sum of post-step values
-// `post` (i = 1..n), maximum over S_0..S_n, sum of log post-step values; n = steps.
+// `post` (i = 1..n), maximum over S_0..S_n, sum of log post-step values; n = steps.  K, disc, S0
+// and Q are the strike, discount factor, initial value and digital cash in the path's precision.
 template <typename R, int PAY>
-__device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
-                                          const LevelParams &p)
+__device__ __forceinline__ R payoff_from(R Sn, R post, R hi, R lpost, R inv_n, R K, R disc, R S0, R Q)
 {
-    const R K = R(p.K), disc = R(p.disc), S0 = R(p.S0);
     if constexpr (PAY == kEuropean) {
         return disc * fmax(Sn - K, R(0));
     } else if constexpr (PAY == kAsian) {
@@ -91,7 +90,6 @@ __device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
     } else if constexpr (PAY == kLookback) {
         return disc * fmax(hi - K, R(0));
     } else if constexpr (PAY == kDigital) {
-        const R Q = R(p.Q);
         return Sn > K ? disc * Q : (Sn == K ? R(0.5) * disc * Q : R(0));
     } else if constexpr (PAY == kLinear) {
         return Sn;
@@ -101,6 +99,12 @@ __device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n,
         const R G = sizeof(R) == 4 ? R(expf(float(lg))) : R(exp(double(lg)));
         return disc * fmax(G - K, R(0));
     }
+}
+
+template <typename R, int PAY>
+__device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n, const LevelParams &p)
+{
+    return payoff_from<R, PAY>(Sn, post, hi, lpost, inv_n, R(p.K), R(p.disc), R(p.S0), R(p.Q));
 }
 
 // Philox block of counter c under the parameters' key: from the precomputed round keys (RK, the
