@@ -159,6 +159,40 @@ def test_cv_level_and_mean_sums_match_oracle(mlmc, level):
     np.testing.assert_allclose(d_m.cpu().numpy(), [Q.sum(), (Q ** 2).sum()], rtol=1e-9)
 
 
+def test_cv_level_sums_with_many_tiles_per_block(mlmc):
+    """N = 2^21 + 77 on level 1: each block of the tensor-core level kernel runs several batches
+    of tiles (folds of FP32 batch sums into FP64) and the last tile is ragged.  The eight sums
+    match the device's own per-sample values; g and Y of samples at the start, the middle and
+    the end match the oracle."""
+    import torch
+
+    p = mlmc.Problem(payoff="asian", **GBM)
+    op = oracle_problem(oracle, p)
+    cv = mlmc.mlmc_cv_create(4, p)
+    theta = _params(31)
+    level = 1
+    mlmc.mlmc_cv_set_params(cv, level, theta, kappa=2.0)
+    N, first, seed = (1 << 21) + 77, 5, 19
+    d_s = torch.zeros(8, dtype=torch.float64, device="cuda")
+    d_r = torch.zeros(N, dtype=torch.float32, device="cuda")
+    d_g = torch.zeros(N, dtype=torch.float32, device="cuda")
+    mlmc.mlmc_cv_level_sums(cv, level, N, first, seed, d_s, d_r, d_g)
+    r, g = d_r.cpu().numpy().astype(np.float64), d_g.cpu().numpy().astype(np.float64)
+    Yg = r + g
+    own = [r.sum(), (r ** 2).sum(), (r ** 3).sum(), (r ** 4).sum(), Yg.sum(), (Yg ** 2).sum(), g.sum(), (g ** 2).sum()]
+    scales = [np.abs(r).sum(), (r ** 2).sum(), (np.abs(r) ** 3).sum(), (r ** 4).sum(), np.abs(Yg).sum(),
+              (Yg ** 2).sum(), np.abs(g).sum(), (g ** 2).sum()]
+    sums = d_s.cpu().numpy()
+    for k in range(8):
+        assert abs(sums[k] - own[k]) <= 1e-6 * scales[k] + 1e-9, k
+    idx = np.concatenate([np.arange(40), N // 2 + np.arange(40), N - 40 + np.arange(40)])
+    Yo = np.array([oracle.level_samples(level, 4, 1, op, seed=seed, first=first + int(i), stream="fp32")[0] for i in idx])
+    Xo = np.array([omlp.features(level, 4, first + int(i), 1.0, seed=seed, stream="fp32") for i in idx])
+    go, _ = omlp.forward(theta.astype(np.float64), Xo, quantize=True)
+    assert np.all(np.abs(g[idx] - go) <= _g_bound(theta, Xo))
+    assert np.max(np.abs(Yg[idx] - Yo)) <= _y_bound(level, 4) + 1e-5 * np.max(np.abs(Yo))
+
+
 def test_zero_network_reduces_to_plain(mlmc):
     """g = 0 (all parameters zero): r is the plain sample Y, sample for sample."""
     import torch
