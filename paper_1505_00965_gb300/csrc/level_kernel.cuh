@@ -171,12 +171,14 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             R dk;
+            // with M = 4 a call starts a coarse step: its sum starts from d[0] itself (the same
+            // value as 0 + d[0] up to the sign of a zero, which no step can see)
             if constexpr (MIL) {
-                dc += d[k];  // the coarse increment's sum of normals
+                dc = (MT == 4 && k == 0) ? d[k] : dc + d[k];  // the coarse increment's sum of normals
                 dk = fma(fma(c2, d[k], a), d[k], rhm);
             } else {
                 dk = d[k];
-                dc += dk;
+                dc = (MT == 4 && k == 0) ? dk : dc + dk;
             }
             em_step<R, PAY, SPLIT && !POS>(fS, fsum, fhi, flo, fls, dk);
             bool coarse_now;
@@ -298,12 +300,13 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
                 R dk;
+                // M = 4: a call starts a coarse step, whose sum starts from d[i][0] (as in simulate_steps)
                 if constexpr (MIL) {
-                    dc[i] += d[i][k];
+                    dc[i] = (MT == 4 && k == 0) ? d[i][k] : dc[i] + d[i][k];
                     dk = fma(fma(c2, d[i][k], a), d[i][k], rhm);
                 } else {
                     dk = d[i][k];
-                    dc[i] += dk;
+                    dc[i] = (MT == 4 && k == 0) ? dk : dc[i] + dk;
                 }
                 em_step<R, PAY, false>(fS[i], fsum[i], fhi[i], flo[i], fls[i], dk);
                 if constexpr (ANTI) {
