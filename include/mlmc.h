@@ -356,25 +356,28 @@ int mlmc_level_sums_batch(int n, const mlmc_level_task *tasks, int M, int precis
 /*
  * ---------------------------------------------------------------- learned control variate
  * A control variate replaces E[Y_l] by E[Y_l - g] + E[g] (Sec. 5 "Exploiting Structure":
- * compute E[X - Y] and add E[Y]).  Here g is a network 8 -> 64 -> 64 -> 1 of the sample's
+ * compute E[X - Y] and add E[Y]).  Here g is a network 16 -> 64 -> 64 -> 1 of the sample's
  * Brownian path, trained per level on (inputs, Y_l) pairs the method itself generates:
- *   x_k = (W(k T/8) - W((k-1) T/8)) / sqrt(T/8), k = 1..8 (iid N(0,1)); on levels with
- *   M^l < 8 the T/8 grid is refined from the path's grid by Brownian-bridge midpoints taken from
- *   Philox blocks 1 and 2 of the sample's counter;
+ *   x = the Brownian-bridge (Levy) coordinates of the path on the T/16 grid (iid N(0,1)):
+ *   x_0 = W(T) / sqrt(T), then stage by stage (intervals of 16, 8, 4, 2 grid steps) and left to
+ *   right (W(m) - (W(l) + W(r)) / 2) / sqrt((r - l) / 4), m the midpoint of [l, r]; on levels with
+ *   M^l < 16 the T/16 grid is refined from the path's grid by Brownian-bridge midpoints (stage by
+ *   stage, left to right) taken from the Philox blocks of the sample's counter that its path does
+ *   not read, from block max(1, M^l / 4) on;
  *   g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3, GELU(z) = z/2 (1 + tanh(sqrt(2/pi)
  *   (z + 0.044715 z^3))); products on the tensor cores with bfloat16 operands and FP32
  *   accumulation (rounded: x, W1, W2, GELU(z1)); everything else FP32;
- *   packed parameters (MLMC_CV_PARAMS floats): W1 [64][8] (row = output unit), b1 [64],
+ *   packed parameters (MLMC_CV_PARAMS floats): W1 [64][16] (row = output unit), b1 [64],
  *   W2 [64][64], b2 [64], w3 [64], b3.
  * The level estimator with the control variate is mean over N samples of (Y - g(x)) plus an
  * independent estimate of E[g]: the average of R replicate means Q_r of a randomly shifted
  * rank-1 lattice rule (Sloan and Joe 1994; random shift after Cranley and Patterson 1976).
- * Replicate r has the n = MLMC_CV_LATTICE_POINTS points i = 0 .. n-1 with coordinates, k = 0..7,
+ * Replicate r has the n = MLMC_CV_LATTICE_POINTS points i = 0 .. n-1 with coordinates, k = 0..15,
  *   v_k = ((i z_k mod n) 2^16 + D_k) mod 2^32,  z_k = a^k mod n (a = MLMC_CV_LATTICE_A),
  *   w_k = 2 v_k if v_k < 2^31, else 2 (2^32 - 1 - v_k)  (the baker's, or tent, transform
  *         u -> 1 - |2u - 1|, which keeps points uniform and suits non-periodic integrands),
  *   u_k = (floor(w_k / 2^9) + 1/2) 2^-23,  x_k = Phi^{-1}(u_k),
- * where D_0..D_7 are the words of Philox blocks 0 and 1 of counter r under tag
+ * where D_0..D_15 are the words of Philox blocks 0..3 of counter r under tag
  * MLMC_TAG_CV_MEAN (the random shift, as 32-bit fractions).  Every point is uniform whatever
  * the shift, so Q_r is unbiased for E[g] for any g, and replicates are independent; the lattice
  * makes Var(Q_r) far smaller than Var(g) / n for a smooth g.  kappa is the number of lattice
@@ -383,9 +386,10 @@ int mlmc_level_sums_batch(int n, const mlmc_level_task *tasks, int M, int precis
  * (Var(Y - g) + var_lattice / kappa) (t_cv + kappa t_mean) stays below Var(Y) t_plain, with
  * var_lattice = n Var(Q_r); otherwise the plain estimator runs.  FP32 paths only.
  */
-#define MLMC_CV_PARAMS 4801
+#define MLMC_CV_PARAMS 5313
+#define MLMC_CV_INPUTS 16              /* network inputs: the Levy coordinates of the T/16 grid */
 #define MLMC_CV_LATTICE_POINTS 65536   /* points n of one mean-sample replicate */
-#define MLMC_CV_LATTICE_A 21553        /* Korobov multiplier a of the mean-sample lattice */
+#define MLMC_CV_LATTICE_A 43833        /* Korobov multiplier a of the mean-sample lattice */
 #define MLMC_CV_MAX_LEVELS 8
 typedef struct mlmc_cv mlmc_cv;   /* opaque; owns device memory */
 
@@ -470,12 +474,12 @@ int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first,
 int mlmc_cv_mean_sums(const mlmc_cv *cv, int level, uint64_t R, uint64_t first, uint64_t seed,
                       double *d_sums2, float *d_g, void *stream);
 
-/* Training data of `level`: d_X device [N][8] network inputs, d_Y device [N] Y values, for
+/* Training data of `level`: d_X device [N][16] network inputs, d_Y device [N] Y values, for
  * samples [first, first + N) under tag MLMC_TAG_CV_TRAIN.  Synchronises `stream`. */
 int mlmc_cv_training_data(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, uint64_t seed,
                           float *d_X, float *d_Y, void *stream);
 
-/* The network on given inputs: params host [MLMC_CV_PARAMS]; d_X device [N][8]; d_G device [N].
+/* The network on given inputs: params host [MLMC_CV_PARAMS]; d_X device [N][16]; d_G device [N].
  * mlmc_mlp_grad: loss (1/N) sum (g - Y)^2 and its gradient (host outputs) for rows d_X, d_Y
  * (device); N a multiple of 32, at most 65536.  The gradient comes from the training kernel's
  * own forward and backward code (one step, no update).  Both synchronise `stream`. */

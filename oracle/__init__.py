@@ -166,7 +166,7 @@ def sample_paths(level: int, M: int, s: int, p: Problem, seed: int, stream: str 
 
 
 def grid_brownian(level: int, M: int, s: int, T: float, seed: int, stream: str = "fp64", tag: int = TAG_PATHS) -> np.ndarray:
-    W = np.empty(8, dtype=np.float64)
+    W = np.empty(16, dtype=np.float64)
     _load().oracle_grid_brownian(level, M, s, tag, T, seed, STREAMS[stream], _dp(W))
     return W
 

@@ -33,11 +33,12 @@
  *     M^l < 4 (level 0, and level 1 for M = 2), G = 4 / M^l consecutive samples share one
  *     block: sample s takes normals (s mod G) M^l .. (s mod G) M^l + M^l - 1 of block j = 0 of
  *     counter index floor(s / G) (in place of s).
- *   - The Brownian path on the T/8 grid (the learned control variate's inputs) is the running
- *     sum of the fine increments when M^l >= 8.  On coarser levels it is refined from the
+ *   - The Brownian path on the T/16 grid (the learned control variate's inputs) is the running
+ *     sum of the fine increments when M^l >= 16.  On coarser levels it is refined from the
  *     fine-grid values by Brownian-bridge midpoints, stage by stage and left to right; the
- *     midpoints take the normals of blocks j = 1, 2 of the sample's own counter.  The fine path
- *     never depends on whether the grid is built.
+ *     midpoints take the normals of the sample's own counter from block b0 = max(1, M^l / 4)
+ *     on, the first block its fine path does not read.  The fine path never depends on whether
+ *     the grid is built.
  *   - Arithmetic Asian: trapezoid average (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 on each path's own
  *     grid.  Lookback: fixed strike, max over the grid points S_0..S_n.  Both discounted.
  *   - Cost of one level-l sample: C_0 = 1, C_l = M^l + M^{l-1} Euler--Maruyama steps.
@@ -242,44 +243,48 @@ int oracle_sample_paths(int level, int M, uint64_t s, int tag, const oracle_prob
     return (int)nf;
 }
 
-/* Brownian values W(k T / 8), k = 1..8, of one sample (the T/8 grid of the stream). */
+/* Brownian values W(k T / 16), k = 1..16, of one sample (the T/16 grid of the stream). */
 void oracle_grid_brownian(int level, int M, uint64_t s, int tag, double T, uint64_t seed,
-                          int stream, double W8[8])
+                          int stream, double W16[16])
 {
     long nf = ipow(M, level);
-    double *z = (double *)malloc(sizeof(double) * (size_t)(nf > 8 ? nf : 8));
+    double *z = (double *)malloc(sizeof(double) * (size_t)(nf > 16 ? nf : 16));
     oracle_sample_normals(seed, level, M, tag, s, stream, z);
     double sqrt_h = sqrt(T / (double)nf);
-    if (nf >= 8) {
-        long per8 = nf / 8;
+    if (nf >= 16) {
+        long per16 = nf / 16;
         double W = 0.0;
-        for (int k = 0; k < 8; ++k) {
-            for (long q = 0; q < per8; ++q)
-                W += sqrt_h * z[k * per8 + q];
-            W8[k] = W;
+        for (int k = 0; k < 16; ++k) {
+            for (long q = 0; q < per16; ++q)
+                W += sqrt_h * z[k * per16 + q];
+            W16[k] = W;
         }
     } else {
-        /* grid[i] = W(i T / 8), i = 0..8; known at multiples of 8 / nf, then bridged */
-        double grid[9], zb[12];
-        oracle_normals(seed, level, tag, s, stream, 12, zb);  /* blocks 0..2 of the sample */
-        long step = 8 / nf;
+        /* grid[i] = W(i T / 16), i = 0..16; known at multiples of 16 / nf, then bridged.  The
+         * midpoints take the normals of the sample's own blocks from b0 on: the first block
+         * after the path's own (b0 = M^l / 4 when M^l >= 4; b0 = 1 on packed levels, whose path
+         * reads block 0 of another counter). */
+        long b0 = nf >= 4 ? nf / 4 : 1;
+        double grid[17], zb[24];
+        oracle_normals(seed, level, tag, s, stream, (int)(4 * b0 + 16), zb);
+        long step = 16 / nf;
         double W = 0.0;
         grid[0] = 0.0;
         for (long k = 0; k < nf; ++k) {
             W += sqrt_h * z[k];
             grid[(k + 1) * step] = W;
         }
-        long next = 4;  /* first normal of block 1 */
+        long next = 4 * b0;
         for (long width = step; width > 1; width /= 2) {
-            double dt_half = T / 8.0 * (double)(width / 2);
-            for (long left = 0; left < 8; left += width) {
+            double dt_half = T / 16.0 * (double)(width / 2);
+            for (long left = 0; left < 16; left += width) {
                 long mid = left + width / 2;
                 grid[mid] = 0.5 * (grid[left] + grid[left + width]) +
                             sqrt(dt_half / 2.0) * zb[next++];
             }
         }
-        for (int k = 0; k < 8; ++k)
-            W8[k] = grid[k + 1];
+        for (int k = 0; k < 16; ++k)
+            W16[k] = grid[k + 1];
     }
     free(z);
 }

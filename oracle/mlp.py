@@ -3,12 +3,17 @@
 A control variate replaces E[Y] by E[Y - g] + E[g] (the control-variate remark of Sec. 5:
 compute E[X - Y] and add E[Y]).  Here g is a small network of the sample's Brownian path:
 
-* inputs x_k = (W(k T / 8) - W((k - 1) T / 8)) / sqrt(T / 8), k = 1..8, the standardised
-  increments of the path on the T/8 grid (iid N(0, 1) whatever the level);
-* g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3, widths 8 -> 64 -> 64 -> 1, with
+* inputs: the Brownian-bridge (Levy) coordinates of the path on the T/16 grid, iid N(0, 1)
+  whatever the level: x_0 = W(T) / sqrt(T), then stage by stage (intervals of 16, 8, 4, 2 grid
+  steps) and left to right the standardised midpoint deviations
+  (W(m) - (W(l) + W(r)) / 2) / sqrt((r - l) / 4), m the midpoint of [l, r] (the construction of
+  Caflisch, Morokoff and Owen, J. Comput. Finance 1, 1997, which puts the directions a path
+  functional depends on most first: it suits the lattice rule below, whose weights decay along
+  the coordinates);
+* g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3, widths 16 -> 64 -> 64 -> 1, with
   GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
-* parameters packed as W1 [64][8] (row = output unit), b1 [64], W2 [64][64], b2 [64],
-  w3 [64], b3 [1]: 4801 numbers;
+* parameters packed as W1 [64][16] (row = output unit), b1 [64], W2 [64][64], b2 [64],
+  w3 [64], b3 [1]: 5313 numbers;
 * training loss: the mean of (g(x) - Y)^2 over a batch.
 
 `quantize=True` rounds to bfloat16 (round to nearest, ties to even) the operands of the
@@ -26,7 +31,7 @@ from scipy.special import ndtri
 from . import TAG_CV_MEAN, grid_brownian, philox
 
 H = 64
-D = 8
+D = 16
 N_PARAMS = H * D + H + H * H + H + H + 1
 SQRT_2_OVER_PI = math.sqrt(2.0 / math.pi)
 GELU_C = 0.044715
@@ -68,7 +73,7 @@ def gelu_grad(z):
 
 
 def forward(theta, X, quantize: bool = False):
-    """g(x) for the rows of X [B, 8], and the layer values (z1, h1, z2, h2)."""
+    """g(x) for the rows of X [B, 16], and the layer values (z1, h1, z2, h2)."""
     W1, b1, W2, b2, w3, b3 = unpack(theta)
     X = np.asarray(X, dtype=np.float64)
     if quantize:
@@ -112,38 +117,49 @@ def init_params(seed: int) -> np.ndarray:
     return pack(W1, np.zeros(H), W2, np.zeros(H), w3, 0.0)
 
 
+def levy_coordinates(W, T: float) -> np.ndarray:
+    """The Brownian-bridge coordinates of grid values W = (W(T/16), ..., W(T)) (module docstring)."""
+    grid = np.concatenate([[0.0], np.asarray(W, dtype=np.float64)])
+    x = [grid[D] / math.sqrt(T)]
+    width = D
+    while width > 1:
+        sd = math.sqrt(T / D * width / 4.0)
+        for left in range(0, D, width):
+            x.append((grid[left + width // 2] - 0.5 * (grid[left] + grid[left + width])) / sd)
+        width //= 2
+    return np.array(x)
+
+
 def features(level: int, M: int, s: int, T: float, seed: int, stream: str = "fp64", tag: int = 0) -> np.ndarray:
-    """The 8 standardised T/8-grid increments of sample s (from the oracle's Brownian grid)."""
-    W = grid_brownian(level, M, s, T, seed, stream=stream, tag=tag)
-    inc = np.diff(np.concatenate([[0.0], W]))
-    return inc / math.sqrt(T / 8.0)
+    """The 16 network inputs of sample s: the Levy coordinates of its T/16 Brownian grid."""
+    return levy_coordinates(grid_brownian(level, M, s, T, seed, stream=stream, tag=tag), T)
 
 
 # The independent sample that estimates E[g] is a randomly shifted rank-1 lattice rule
 # (Sloan and Joe, "Lattice Methods for Multiple Integration", 1994; random shifts after
 # Cranley and Patterson, SIAM J. Numer. Anal. 13, 1976): replicate r is the point set
 # {frac(i z / n + Delta_r) : i = 0 .. n - 1} with the Korobov generating vector
-# z = (1, a, a^2, ..., a^7) mod n, mapped to N(0, I_8) coordinate by coordinate with the inverse
+# z = (1, a, a^2, ..., a^15) mod n, mapped to N(0, I_16) coordinate by coordinate with the inverse
 # normal distribution function, after the baker's (tent) transform u -> 1 - |2u - 1| of every
 # coordinate (Hickernell, "Obtaining O(N^-2+eps) convergence for lattice quadrature rules",
 # 2002), which suits integrands that are not periodic.  Each point of a replicate is uniform on
-# [0, 1)^8 whatever Delta_r, and the tent transform keeps it uniform, so the replicate's mean of
+# [0, 1)^16 whatever Delta_r, and the tent transform keeps it uniform, so the replicate's mean of
 # g is an unbiased estimate of E[g]; replicates with independent shifts are independent.  The
 # library fixes n, a and the shift bits:
 LATTICE_N = 65536
-LATTICE_A = 21553
+LATTICE_A = 43833
 
 
 def lattice_generator() -> list[int]:
-    """z_k = a^k mod n, k = 0..7."""
+    """z_k = a^k mod n, k = 0..15."""
     return [pow(LATTICE_A, k, LATTICE_N) for k in range(D)]
 
 
 def lattice_shift(r: int, seed: int, level: int) -> list[int]:
-    """The shift of replicate r as eight 32-bit fractions: the words of Philox blocks 0 and 1 of
+    """The shift of replicate r as sixteen 32-bit fractions: the words of Philox blocks 0..3 of
     counter r under the control-variate-mean tag."""
     words = []
-    for j in (0, 1):
+    for j in range(D // 4):
         words += list(philox((j, r & 0xFFFFFFFF, r >> 32, (TAG_CV_MEAN << 16) | level),
                              (seed & 0xFFFFFFFF, seed >> 32)))
     return words
@@ -167,14 +183,14 @@ def tent32(v: np.ndarray) -> np.ndarray:
 
 
 def lattice_uniforms(r: int, i, seed: int, level: int) -> np.ndarray:
-    """Points i (array) of replicate r in (0, 1)^8: the tent transform of the shifted lattice point,
+    """Points i (array) of replicate r in (0, 1)^16: the tent transform of the shifted lattice point,
     keeping its top 23 bits, centred: u = (floor(tent(v) / 2^9) + 1/2) 2^-23."""
     v = tent32(lattice_points32(r, i, seed, level))
     return ((v >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
 
 
 def mean_sample_features(r: int, i, seed: int, level: int) -> np.ndarray:
-    """Network inputs of points i of replicate r: x_k = Phi^{-1}(u_k), shape (len(i), 8)."""
+    """Network inputs of points i of replicate r: x_k = Phi^{-1}(u_k), shape (len(i), 16)."""
     return ndtri(lattice_uniforms(r, i, seed, level))
 
 

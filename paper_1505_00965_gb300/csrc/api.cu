@@ -338,7 +338,7 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.small = nf < 4 ? 1 : 0;
     p.a = m->sigma * std::sqrt(h);
     p.sqrt_h = std::sqrt(h);
-    p.sqrt_t8 = std::sqrt(m->T / 8.0);
+    p.sqrt_tg = std::sqrt(m->T / 16.0);
     p.rh = m->r * h;
     p.h = h;
     p.inv_nf = 1.0 / (double)nf;

@@ -31,6 +31,7 @@ struct mlmc_cv {
 
 namespace {
 
+static_assert(kNumParams == MLMC_CV_PARAMS && kInputs == MLMC_CV_INPUTS, "network shape of the C ABI");
 constexpr int kCvThreads = 256;
 constexpr double kMinKappa = 1.0 / 64.0, kMaxKappa = 4096.0;  // mean points per path sample
 
@@ -527,7 +528,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         cudaError_t e_ = (expr);                                                                    \
         if (e_ != cudaSuccess) return cleanup(fail(MLMC_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_))); \
     } while (0)
-    CV_TRY(cudaMalloc(&d_X, sizeof(float) * 8 * n_train * levels));
+    CV_TRY(cudaMalloc(&d_X, sizeof(float) * kInputs * n_train * levels));
     CV_TRY(cudaMalloc(&d_Y, sizeof(float) * n_train * levels));
     CV_TRY(cudaMalloc(&d_Gv, sizeof(float) * n_train));
     CV_TRY(cudaMalloc(&d_P, sizeof(float) * kNumParams * levels));
@@ -539,7 +540,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
     // standardisation, initial weights
     TrainArgs targs = {};
     for (int l = 0; l < levels; ++l) {
-        float *X = d_X + 8 * n_train * l, *Yd = d_Y + n_train * l;
+        float *X = d_X + kInputs * n_train * l, *Yd = d_Y + n_train * l;
         rc = mlmc_cv_training_data(cv, l, n_train, 0, seed, X, Yd, st);
         if (rc) return cleanup(rc);
         const float *hy = hY.data() + n_train * l;
@@ -579,10 +580,10 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
         w[kOffB3] = (float)(w[kOffB3] * sd[l] + mu[l]);
         rc = mlmc_cv_set_params(cv, l, w, 1.0);
         if (rc) return cleanup(rc);
-        const float *d_Xl = d_X + 8 * n_train * l;
+        const float *d_Xl = d_X + kInputs * n_train * l;
         const float *hYl = hY.data() + n_train * l;
         // 5. held-out variance ratio
-        rc = mlmc_mlp_forward(w, d_Xl + 8 * n_fit, n_val, d_Gv, st);
+        rc = mlmc_mlp_forward(w, d_Xl + kInputs * n_fit, n_val, d_Gv, st);
         if (rc) return cleanup(rc);
         CV_TRY(cudaMemcpy(hG.data(), d_Gv, sizeof(float) * n_val, cudaMemcpyDeviceToHost));
         double sy = 0, syy = 0, sr = 0, srr = 0, sg = 0, sgg = 0;

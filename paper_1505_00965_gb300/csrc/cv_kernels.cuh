@@ -1,11 +1,14 @@
 // cv_kernels.cuh -- device code of the learned control variate (FP32 paths).
 //
 // For a level-l sample the control variate needs Y = P_l - P_{l-1} (Sec. 5, Eq. Yldef) and the
-// network inputs x_k = (W(k T/8) - W((k-1) T/8)) / sqrt(T/8), k = 1..8.  On levels with
-// M^l >= 8 the grid increments are sums of M^l / 8 consecutive fine increments of the path;
-// on coarser levels the grid is refined from the path's own grid by Brownian-bridge midpoints
-// whose normals come from Philox blocks 1 and 2 of the sample's counter (stage by stage, left
-// to right), so the path itself is the one the plain estimator draws.
+// network inputs: the Brownian-bridge (Levy) coordinates of the path on the T/16 grid,
+// x_0 = W(T) / sqrt(T), then stage by stage (intervals of 16, 8, 4, 2 grid steps) and left to
+// right the standardised midpoint deviations (W(m) - (W(l) + W(r)) / 2) / sqrt((r - l) / 4).
+// On levels with M^l >= 16 the grid values are running sums of the path's fine increments; on
+// coarser levels the grid is refined from the path's own grid by Brownian-bridge midpoints whose
+// normals come from the Philox blocks of the sample's counter after the path's own (from block
+// max(1, M^l / 4) on; stage by stage, left to right), so the path itself is the one the plain
+// estimator draws.
 #pragma once
 #include <cstdint>
 
@@ -21,28 +24,45 @@ namespace mlmcgb {
 // The FP32 constants of a level's paths and payoff, converted once from the FP64 parameters (a
 // conversion from FP64 runs on the FP64 pipe, 2 per SM per clock on GB300; kernels keep these in
 // shared memory so the compiler reloads them instead of converting again in every sample).
-// scale = sqrt_h / sqrt_t8 and inv_t8 = 1 / sqrt_t8 are the FP32 quotients of the converted values.
+// inv_tg = 1 / sqrt_tg is the FP32 quotient of the converted value (sqrt_tg = sqrt(T / 16), the
+// scale of a grid increment).
 struct CvConsts {
-    float a, rh, S0, sqrt_h, sqrt_t8, inv_nf, inv_nc, K, disc, Q, scale, inv_t8;
+    float a, rh, S0, sqrt_h, sqrt_tg, inv_nf, inv_nc, K, disc, Q, inv_tg;
 };
 __device__ __forceinline__ CvConsts cv_consts(const LevelParams &p)
 {
-    const float sqrt_h = (float)p.sqrt_h, sqrt_t8 = (float)p.sqrt_t8;
-    return {(float)p.a, (float)p.rh, (float)p.S0, sqrt_h, sqrt_t8, (float)p.inv_nf, (float)p.inv_nc,
-            (float)p.K, (float)p.disc, (float)p.Q, sqrt_h / sqrt_t8, 1.0f / sqrt_t8};
+    const float sqrt_tg = (float)p.sqrt_tg;
+    return {(float)p.a, (float)p.rh, (float)p.S0, (float)p.sqrt_h, sqrt_tg, (float)p.inv_nf, (float)p.inv_nc,
+            (float)p.K, (float)p.disc, (float)p.Q, 1.0f / sqrt_tg};
+}
+
+// The Levy coordinates of grid[i] = W(i T / 16), i = 0..16 (grid[0] = 0); inv_tg = 1 / sqrt(T / 16).
+// The midpoint of an interval of w grid steps has bridge standard deviation sqrt(T / 16) sqrt(w) / 2.
+__device__ __forceinline__ void levy_coordinates(const float grid[17], float inv_tg, float x[kInputs])
+{
+    static_assert(kInputs == 16, "the coordinates of a 16-step grid");
+    x[0] = 0.25f * inv_tg * grid[16];
+    int idx = 1;
+#pragma unroll
+    for (int w = 16; w > 1; w /= 2) {
+        const float s = inv_tg * (w == 16 ? 0.5f : w == 8 ? 0.70710678118654752f : w == 4 ? 1.0f : 1.41421356237309505f);
+#pragma unroll
+        for (int left = 0; left < 16; left += w) x[idx++] = (grid[left + w / 2] - 0.5f * (grid[left] + grid[left + w])) * s;
+    }
 }
 
 template <int PAY>
-__device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &k, uint64_t s, float &Y, float x[8])
+__device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &k, uint64_t s, float &Y,
+                                          float x[kInputs])
 {
     const int nf = p.nf, M = p.M;
     const float a = k.a, rh = k.rh, S0 = k.S0;
-    const float sqrt_h = k.sqrt_h, sqrt_t8 = k.sqrt_t8;
+    const float sqrt_h = k.sqrt_h, sqrt_tg = k.sqrt_tg;
     float fS = 1.f, fsum = 0.f, fhi = 1.f, flo = 1.f, fls = 0.f;
     float cS = 1.f, csum = 0.f, chi = 1.f, clo = 1.f, cls = 0.f;
     float dc = 0.f;
     int q = 0;
-    float grid[9];  // W at i T / 8 (coarse levels only)
+    float grid[17];  // W at i T / 16
     auto fine_step = [&](float z) {
         const float d = fmaf(a, z, rh);
         em_step<float, PAY, false>(fS, fsum, fhi, flo, fls, d);
@@ -76,12 +96,11 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
                 em_step<float, PAY, false>(fS, fsum, fhi, flo, fls, fmaf(a, zk, rh));
             }
             W = fmaf(sqrt_h, zk, W);
-            grid[(k + 1) * (8 / nf)] = W;
+            grid[(k + 1) * (16 / nf)] = W;
         }
     } else {
         const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
-        const int per8 = nf >= 8 ? nf / 8 : 0;
-        const float scale = k.scale;
+        const int per16 = nf >= 16 ? nf / 16 : 0, gstep = nf < 16 ? 16 / nf : 0;
         float acc = 0.f, W = 0.f;
         int f = 0, cnt = 0;
         grid[0] = 0.f;
@@ -97,48 +116,51 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 fine_step(z[k]);
-                if (per8) {
+                if (per16) {
                     acc += z[k];
-                    if (++cnt == per8) {
-                        x[f++] = acc * scale;
+                    if (++cnt == per16) {
+                        W = fmaf(sqrt_h, acc, W);
+                        grid[++f] = W;
                         acc = 0.f;
                         cnt = 0;
                     }
-                } else {  // nf == 4: the path's grid points T/4, T/2, 3T/4, T
+                } else {  // nf = 4 or 8: the path's own grid points
                     W = fmaf(sqrt_h, z[k], W);
-                    grid[(4 * j + k + 1) * 2] = W;
+                    grid[(4 * j + k + 1) * gstep] = W;
                 }
             }
         }
     }
-    if (nf < 8) {
-        // Brownian-bridge midpoints from blocks 1 and 2 of the sample's own counter
+    if (nf < 16) {
+        // Brownian-bridge midpoints: 16 - M^l normals from blocks b0, b0 + 1, ... of the sample's
+        // own counter, b0 = max(1, M^l / 4) the first block its path does not read
         const uint32_t slo = (uint32_t)s, shi = (uint32_t)(s >> 32);
-        float zb[8];
+        const int b0 = nf >= 4 ? nf / 4 : 1, nblk = (19 - nf) / 4;
+        float zb[16];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const uint4 xb = philox4x32_10(make_uint4((uint32_t)(j + 1), slo, shi, p.ctr3), p.key0, p.key1);
-            float rho, c, sn;
-            BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
-            zb[4 * j + 0] = rho * c;
-            zb[4 * j + 1] = rho * sn;
-            BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
-            zb[4 * j + 2] = rho * c;
-            zb[4 * j + 3] = rho * sn;
+        for (int j = 0; j < 4; ++j) {
+            if (j < nblk) {
+                const uint4 xb = philox4x32_10(make_uint4((uint32_t)(b0 + j), slo, shi, p.ctr3), p.key0, p.key1);
+                float rho, c, sn;
+                BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
+                zb[4 * j + 0] = rho * c;
+                zb[4 * j + 1] = rho * sn;
+                BoxMuller<float>::pair(xb.z, xb.w, rho, c, sn);
+                zb[4 * j + 2] = rho * c;
+                zb[4 * j + 3] = rho * sn;
+            }
         }
         int next = 0;
-        for (int width = 8 / nf; width > 1; width /= 2) {
-            // midpoint variance: (width / 4) T / 8
-            const float sd = sqrt_t8 * sqrtf(0.25f * (float)width);
-            for (int left = 0; left < 8; left += width) {
+        for (int width = 16 / nf; width > 1; width /= 2) {
+            // midpoint variance: (width / 4) T / 16
+            const float sd = sqrt_tg * sqrtf(0.25f * (float)width);
+            for (int left = 0; left < 16; left += width) {
                 const int mid = left + width / 2;
                 grid[mid] = 0.5f * (grid[left] + grid[left + width]) + sd * zb[next++];
             }
         }
-        const float inv = k.inv_t8;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = (grid[k + 1] - grid[k]) * inv;
     }
+    levy_coordinates(grid, k.inv_tg, x);
     const float logS0 = PAY == kGeoAsian ? logf(S0) : 0.f;
     const float Pf = payoff_from<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, (float)nf * logS0 + fls, k.inv_nf, k.K,
                                              k.disc, S0, k.Q);
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(kCvTcThreads) cv_level_tc_kernel(const LevelPa
         for (int j = 0; j < kCvBatch && base < p.N; ++j, base += tile_stride) {
             const uint64_t idx = base + threadIdx.x;
             const bool valid = idx < p.N;
-            float Y, x[8];
+            float Y, x[kInputs];
             cv_sample<PAY>(p, kc, p.first + (valid ? idx : p.N - 1), Y, x);
             const float gv = tc_mlp_tile(ts, tmem, x, phase, ok);
             if (valid) {
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(kCvTcThreads) cv_level_tc_kernel(const LevelPa
 // Independent sample that estimates E[g]: replicates of a randomly shifted rank-1 lattice rule
 // (Sloan and Joe 1994; random shift after Cranley and Patterson 1976).  Replicate r is
 // {frac(i z / n + Delta_r)}, i < n = MLMC_CV_LATTICE_POINTS, z_k = a^k mod n with the Korobov
-// multiplier a = MLMC_CV_LATTICE_A, and Delta_r the eight words of Philox blocks 0 and 1 of
+// multiplier a = MLMC_CV_LATTICE_A, and Delta_r the sixteen words of Philox blocks 0..3 of
 // counter r under the control-variate-mean tag, read as 32-bit fractions.  In fixed point a
 // coordinate is v = (i z_k mod n) 2^16 + D_k mod 2^32, exact; the point keeps its top 23 bits,
 // the baker's (tent) transform w = 2 v below one half, 2 (2^32 - 1 - v) above (Hickernell 2002;
@@ -310,9 +332,9 @@ __global__ void __launch_bounds__(kMeanTcThreads) cv_mean_tc_kernel(const LevelP
     const uint64_t rep = blockIdx.x / kChunksPerReplicate;
     const uint32_t chunk = blockIdx.x % kChunksPerReplicate;
     const uint64_t r = p.first + rep;
-    uint32_t D[8];
+    uint32_t D[kInputs];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kInputs / 4; ++j) {
         const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)r, (uint32_t)(r >> 32), p.ctr3),
                                        p.key0, p.key1);
         D[4 * j + 0] = xb.x;
@@ -326,9 +348,9 @@ __global__ void __launch_bounds__(kMeanTcThreads) cv_mean_tc_kernel(const LevelP
 #pragma unroll 1
     for (uint32_t tile = 0; tile < kLatticeChunk / kMeanTcThreads; ++tile) {
         const uint32_t i = chunk * kLatticeChunk + tile * kMeanTcThreads + threadIdx.x;
-        float x[8];
+        float x[kInputs];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kInputs; ++k) {
             const uint32_t v = (((i * lattice_z(k)) & (kLatticeN - 1)) << 16) + D[k];
             const uint32_t w = v < 0x80000000u ? v << 1 : (~v) << 1;  // tent: 2v, or 2 (2^32 - 1 - v)
             x[k] = normcdfinvf(((float)(w >> 9) + 0.5f) * 0x1p-23f);
@@ -389,20 +411,20 @@ __global__ void __launch_bounds__(256) cv_data_kernel(const LevelParams p, float
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const CvConsts kc = cv_consts(p);
     for (uint64_t idx = tid; idx < p.N; idx += stride) {
-        float Y, x[8];
+        float Y, x[kInputs];
         cv_sample<PAY>(p, kc, p.first + idx, Y, x);
         Yout[idx] = Y;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) X[8 * idx + k] = x[k];
+        for (int k = 0; k < kInputs; ++k) X[kInputs * idx + k] = x[k];
     }
 }
 
-// g(x) for rows of X [N][8] (standalone forward, used for validation and tests).
+// g(x) for rows of X [N][16] (standalone forward, used for validation and tests).
 __global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restrict__ params, const float *X,
                                                           uint64_t N, float *G)
 {
     __shared__ MlpShared net;
-    __shared__ __align__(16) uint32_t xw_all[8][128];  // 16-byte rows: warp_mlp stores uint4
+    __shared__ __align__(16) uint32_t xw_all[8][32 * kXStride];  // 16-byte aligned rows: warp_mlp stores uint4
     load_mlp(net, params);
     __syncthreads();
     uint32_t *xw = xw_all[threadIdx.x >> 5];
@@ -413,9 +435,9 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restric
         const uint64_t idx = base + tid;
         const bool valid = idx < N;
         const uint64_t row = valid ? idx : N - 1;
-        float x[8];
+        float x[kInputs];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = X[8 * row + k];
+        for (int k = 0; k < kInputs; ++k) x[k] = X[kInputs * row + k];
         const float gv = warp_mlp(net, xw, x);
         if (valid) G[idx] = gv;
     }

@@ -18,7 +18,7 @@ struct LevelParams {
     double inv_nf;    // 1 / M^l
     double inv_nc;    // 1 / M^(l-1)
     double sqrt_h;    // sqrt(h): Brownian increment scale of one fine step
-    double sqrt_t8;   // sqrt(T / 8): scale of the control variate's grid increments
+    double sqrt_tg;   // sqrt(T / 16): scale of the control variate's grid increments
     double h;         // fine step T / M^l
     uint64_t first;   // first sample index
     uint64_t N;       // number of samples

@@ -1,5 +1,5 @@
 // mlp.cuh -- the control-variate network g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3 on the
-// tensor cores (8 -> 64 -> 64 -> 1), evaluated by whole warps on 32 samples at a time.
+// tensor cores (16 -> 64 -> 64 -> 1), evaluated by whole warps on 32 samples at a time.
 //
 // The two matrix products run as mma.sync m16n8k16 with bfloat16 operands and FP32
 // accumulation; biases, GELU and the last layer (a 64-term dot product) are FP32.  Layer-1
@@ -18,8 +18,8 @@
 namespace mlmcgb {
 
 constexpr int kHidden = 64;
-constexpr int kInputs = 8;
-// Packed FP32 parameters: W1 [64][8] (row = output unit), b1 [64], W2 [64][64], b2 [64],
+constexpr int kInputs = 16;
+// Packed FP32 parameters: W1 [64][16] (row = output unit), b1 [64], W2 [64][64], b2 [64],
 // w3 [64], b3.
 constexpr int kOffW1 = 0;
 constexpr int kOffB1 = kOffW1 + kHidden * kInputs;
@@ -27,13 +27,17 @@ constexpr int kOffW2 = kOffB1 + kHidden;
 constexpr int kOffB2 = kOffW2 + kHidden * kHidden;
 constexpr int kOffW3 = kOffB2 + kHidden;
 constexpr int kOffB3 = kOffW3 + kHidden;
-constexpr int kNumParams = kOffB3 + 1;  // 4801
+constexpr int kNumParams = kOffB3 + 1;  // 5313
+// A staged row of 16 bfloat16 inputs (8 words) takes kXStride = 12 words: the rows g = 0..7 that
+// one operand fetch (word t or t + 4 of each) or one ldmatrix (16 bytes of each) reads then fall in
+// distinct banks.
+constexpr int kXStride = 12;
 
 // Network in shared memory, laid out so that each lane fetches its operand fragments with
 // 16-byte loads:
-// - L1[32 nt + lane] = {W1 pair word of row 8 nt + g, columns 2t and 2t + 1 (lane = 4 g + t);
-//   b1[8 nt + 2t]; b1[8 nt + 2t + 1]; 0}: one load gives a layer-1 column tile's B fragment and
-//   bias pair.
+// - L1[32 nt + lane] = {W1 pairs of row 8 nt + g at columns (2t, 2t + 1) and (8 + 2t, 9 + 2t)
+//   (lane = 4 g + t); b1[8 nt + 2t]; b1[8 nt + 2t + 1]}: one load gives a layer-1 column tile's B
+//   fragment and bias pair.
 // - W2: row o holds the 32 bfloat16 pairs (W2[o][2j], W2[o][2j+1]) / 2 in the order a lane of
 //   quad index t reads them, words 8 kt + t and 8 kt + t + 4 for kt = 0..3 at positions
 //   8 t + 2 kt and 8 t + 2 kt + 1, so its eight words are two 16-byte loads.  A row takes
@@ -130,8 +134,9 @@ __device__ __forceinline__ void load_mlp(MlpShared &s, const float *__restrict__
 {
     for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) {
         const int nt = i >> 5, g = (i & 31) >> 2, t = i & 3, row = 8 * nt + g, o = 8 * nt + 2 * t;
-        s.L1[i] = make_uint4(pack_bf16x2(params[kOffW1 + row * kInputs + 2 * t], params[kOffW1 + row * kInputs + 2 * t + 1]),
-                             __float_as_uint(params[kOffB1 + o]), __float_as_uint(params[kOffB1 + o + 1]), 0u);
+        const float *w = params + kOffW1 + row * kInputs;
+        s.L1[i] = make_uint4(pack_bf16x2(w[2 * t], w[2 * t + 1]), pack_bf16x2(w[8 + 2 * t], w[9 + 2 * t]),
+                             __float_as_uint(params[kOffB1 + o]), __float_as_uint(params[kOffB1 + o + 1]));
     }
     for (int i = threadIdx.x; i < kHidden * kHidden / 2; i += blockDim.x)
         s.W2[(i >> 5) * kW2Stride + w2_slot(i & 31)] =
@@ -142,23 +147,24 @@ __device__ __forceinline__ void load_mlp(MlpShared &s, const float *__restrict__
     if (threadIdx.x == 0) s.b3 = params[kOffB3];
 }
 
-// g for the 16 samples of one tile.  xw: the warp's staging area, xw[row * 4 + t] holds the
-// bfloat16 pair (x[2t], x[2t+1]) of tile row `row`.  Returns g for rows g and g + 8 of this
+// g for the 16 samples of one tile.  xw: the warp's staging area, xw[row * kXStride + j] holds the
+// bfloat16 pair (x[2j], x[2j+1]) of tile row `row`, j < 8.  Returns g for rows g and g + 8 of this
 // lane's group (every lane of the group gets both).
 __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw, float &out0, float &out1)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    // layer 1: A = x (16 x 16, columns 8..15 zero), B[k][n] = W1[n][k]
-    uint32_t a[4] = {xw[g * 4 + t], xw[(g + 8) * 4 + t], 0u, 0u};
+    // layer 1: A = x (16 x 16), B[k][n] = W1[n][k]
+    const uint32_t a[4] = {xw[g * kXStride + t], xw[(g + 8) * kXStride + t], xw[g * kXStride + t + 4],
+                           xw[(g + 8) * kXStride + t + 4]};
     // layer 1, then A = 2 GELU(z1) as bfloat16 (k-tile kt = n-tiles 2kt and 2kt + 1); GELU on the
     // accumulator pairs (columns 2t, 2t + 1 of rows g and g + 8) with packed FP32 arithmetic
     uint32_t a2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const uint4 l1 = s.L1[32 * nt + lane];
-        const float b1a = __uint_as_float(l1.y), b1b = __uint_as_float(l1.z);
+        const float b1a = __uint_as_float(l1.z), b1b = __uint_as_float(l1.w);
         float c[4] = {b1a, b1b, b1a, b1b};
-        mma_bf16(c, a, l1.x, 0u);
+        mma_bf16(c, a, l1.x, l1.y);
         a2[nt >> 1][(nt & 1) * 2] = pack_bf16x2_f2(twice_gelu2(f2_pack(c[0], c[1])));
         a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2_f2(twice_gelu2(f2_pack(c[2], c[3])));
     }
@@ -192,20 +198,22 @@ __device__ __forceinline__ void mlp_tile(const MlpShared &s, const uint32_t *xw,
     out1 = p1 + s.b3;
 }
 
-// g(x) for the 32 samples of a warp, one per lane (all 32 lanes must call).  xw: 128 words of
-// warp-private shared memory.
-__device__ __forceinline__ float warp_mlp(const MlpShared &s, uint32_t *xw, const float x[8])
+// g(x) for the 32 samples of a warp, one per lane (all 32 lanes must call).  xw: 32 kXStride
+// words of warp-private shared memory, 16-byte aligned.
+__device__ __forceinline__ float warp_mlp(const MlpShared &s, uint32_t *xw, const float x[kInputs])
 {
     const int lane = threadIdx.x & 31;
-    // one 16-byte store per lane (four 4-byte stores at a stride of 4 words conflicted 4 ways)
-    *reinterpret_cast<uint4 *>(&xw[lane * 4]) = make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]),
-                                                           pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+    // two 16-byte stores per lane
+    uint4 *row = reinterpret_cast<uint4 *>(&xw[lane * kXStride]);
+    row[0] = make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]), pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+    row[1] = make_uint4(pack_bf16x2(x[8], x[9]), pack_bf16x2(x[10], x[11]), pack_bf16x2(x[12], x[13]),
+                        pack_bf16x2(x[14], x[15]));
     __syncwarp();
     float mine = 0.f;
 #pragma unroll 1
     for (int tile = 0; tile < 2; ++tile) {
         float r0, r1;
-        mlp_tile(s, xw + tile * 64, r0, r1);
+        mlp_tile(s, xw + tile * 16 * kXStride, r0, r1);
         // sample (tile * 16 + row) is lane tile * 16 + row; row < 8 holds r0 of group row
         const int row = lane & 15;
         const float v0 = __shfl_sync(0xffffffffu, r0, (row & 7) * 4);

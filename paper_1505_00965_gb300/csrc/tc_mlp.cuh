@@ -2,8 +2,8 @@
 // g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3 for a tile of 128 samples per CTA.
 //
 // Both products are tcgen05.mma kind::f16 with bfloat16 operands in shared memory and an FP32
-// accumulator of 128 x 64 in tensor memory (TMEM): layer 1 is one MMA (K = 16, the 8 inputs
-// padded with zeros), layer 2 four (K = 64).  One thread issues the MMAs; their completion is
+// accumulator of 128 x 64 in tensor memory (TMEM): layer 1 is one MMA (K = 16, the 16 inputs),
+// layer 2 four (K = 64).  One thread issues the MMAs; their completion is
 // signalled through an mbarrier (tcgen05.commit), which the CTA waits on with a bounded spin.
 // The epilogues read the accumulator with tcgen05.ld (thread t of the CTA owns row t, i.e. one
 // sample), add the bias and apply GELU in FP32 with the hardware tanh; layer 1's result is
@@ -27,9 +27,9 @@ constexpr uint32_t kTcCols = 64;   // TMEM columns: one FP32 128 x 64 accumulato
 constexpr uint32_t kTcWaitLimit = 1u << 22;  // mbarrier polls before a tile is declared failed
 
 struct TcShared {
-    alignas(1024) uint8_t a1[kTcRows * 16 * 2];      // x: 128 x 16 bfloat16 (k = 8..15 zero), SBO 256
+    alignas(1024) uint8_t a1[kTcRows * 16 * 2];      // x: 128 x 16 bfloat16, SBO 256
     alignas(1024) uint8_t a2[kTcRows * 64 * 2];      // 2 GELU(z1): 128 x 64 bfloat16, SBO 1024
-    alignas(1024) uint8_t w1[kHidden * 16 * 2];      // W1: 64 x 16 bfloat16 (k = 8..15 zero), SBO 256
+    alignas(1024) uint8_t w1[kHidden * 16 * 2];      // W1: 64 x 16 bfloat16, SBO 256
     alignas(1024) uint8_t w2[kHidden * 64 * 2];      // W2 / 2: 64 x 64 bfloat16, SBO 1024
     float b1[kHidden], b2[kHidden], w3[kHidden];     // w3 halved
     float b3;
@@ -118,17 +118,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// One CTA of 128 threads.  Prologue: the network's weights into the operand layout, the zero
-// half of the layer-1 A operand, the mbarrier and 64 TMEM columns (warp 0).  Returns the TMEM
-// base address.
+// One CTA of 128 threads.  Prologue: the network's weights into the operand layout, the mbarrier
+// and 64 TMEM columns (warp 0).  Returns the TMEM base address.
 __device__ __forceinline__ uint32_t tc_setup(TcShared &s, const float *__restrict__ params)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
+    static_assert(kInputs == 16, "layer 1 is one MMA of K = 16");
     for (int i = tid; i < kHidden * 8; i += blockDim.x) {  // W1 pairs (n, k..k+1), k < 16
         const int n = i >> 3, k = 2 * (i & 7);
-        const float lo = k < kInputs ? params[kOffW1 + n * kInputs + k] : 0.f;
-        const float hi = k < kInputs ? params[kOffW1 + n * kInputs + k + 1] : 0.f;
-        *reinterpret_cast<uint32_t *>(s.w1 + cm_byte(n, k, 256)) = pack_bf16x2(lo, hi);
+        *reinterpret_cast<uint32_t *>(s.w1 + cm_byte(n, k, 256)) =
+            pack_bf16x2(params[kOffW1 + n * kInputs + k], params[kOffW1 + n * kInputs + k + 1]);
     }
     for (int i = tid; i < kHidden * 32; i += blockDim.x) {  // W2 / 2 pairs (the epilogues form 2 GELU)
         const int n = i >> 5, k = 2 * (i & 31);
@@ -144,8 +143,6 @@ __device__ __forceinline__ uint32_t tc_setup(TcShared &s, const float *__restric
         s.b3 = params[kOffB3];
         mbar_init(&s.mbar, 1);
     }
-    // k = 8..15 of this thread's layer-1 row: zero for good
-    *reinterpret_cast<uint4 *>(s.a1 + cm_byte(tid, 8, 256)) = make_uint4(0u, 0u, 0u, 0u);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&s.tmem_base)), "r"(kTcCols) : "memory");
@@ -168,16 +165,19 @@ __device__ __forceinline__ void tc_teardown(TcShared &s, uint32_t tmem)
     }
 }
 
-// g for the sample of this thread (row threadIdx.x of the tile) from its inputs x[8].  All 128
+// g for the sample of this thread (row threadIdx.x of the tile) from its inputs x[16].  All 128
 // threads of the CTA call it together.  `phase` is the mbarrier parity to wait for next; `ok`
 // turns false if a wait ran out (the result is then meaningless and the caller reports it).
-__device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const float x[8], uint32_t &phase, bool &ok)
+__device__ __forceinline__ float tc_mlp_tile(TcShared &s, uint32_t tmem, const float x[kInputs], uint32_t &phase,
+                                             bool &ok)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-    // layer-1 A operand: this thread's row, k = 0..7
+    // layer-1 A operand: this thread's row, k = 0..7 and 8..15 (two core matrices)
     *reinterpret_cast<uint4 *>(s.a1 + cm_byte(tid, 0, 256)) =
         make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]), pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+    *reinterpret_cast<uint4 *>(s.a1 + cm_byte(tid, 8, 256)) = make_uint4(
+        pack_bf16x2(x[8], x[9]), pack_bf16x2(x[10], x[11]), pack_bf16x2(x[12], x[13]), pack_bf16x2(x[14], x[15]));
     fence_async_smem();
     tc_fence_before();
     __syncthreads();

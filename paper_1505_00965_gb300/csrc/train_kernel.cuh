@@ -1,7 +1,7 @@
 // train_kernel.cuh -- training of the control-variate network on the GPU: every mini-batch step
 // (forward, backward, parameter gradient, Adam) of every epoch in one persistent launch.
 //
-// The network is g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3 (8 -> 64 -> 64 -> 1) with the
+// The network is g(x) = w3 . GELU(W2 GELU(W1 x + b1) + b2) + b3 (16 -> 64 -> 64 -> 1) with the
 // numerics of the estimator's kernels: bfloat16 operands x, W1, W2 and GELU(z1), FP32 accumulation.
 // The loss is the mean of (g - t)^2 over the B rows of a batch, t = (Y - mu) / sd the
 // standardised target.  Its gradient by the chain rule (d = dL/dg = 2 (g - t) / B):
@@ -41,7 +41,7 @@ constexpr int kTrainMaxSlice = (kNumParams + kTrainMinClusterAdam - 1) / kTrainM
 constexpr int kTrainPartCols = 3 * kHidden + 1;  // per-warp sums: db1, db2, dw3, db3
 
 struct TrainJob {
-    const float *X;   // [n][8] network inputs of the job's rows
+    const float *X;   // [n][16] network inputs of the job's rows
     const float *Y;   // [n] targets (before standardisation)
     float *params;    // [kNumParams] in: initial values; out: trained values
     float mu, inv_sd; // target standardisation t = (Y - mu) inv_sd
@@ -58,7 +58,7 @@ struct TrainArgs {
 };
 
 struct TrainSmem {
-    uint32_t W1[kHidden * kInputs / 2];      // bfloat16 pairs, row o: (W1[o][2t], W1[o][2t+1])
+    uint32_t W1[kHidden * kXStride];         // bfloat16 pairs, row o: (W1[o][2j], W1[o][2j+1]), j < 8, padded
     uint32_t W2[kHidden * kW2Stride];        // row o: (W2[o][2j], W2[o][2j+1]), j < 32
     uint32_t W2T[kHidden * kW2Stride];       // row i: (W2[2j][i], W2[2j+1][i]), j < 32
     float b1[kHidden], b2[kHidden], w3[kHidden];
@@ -69,7 +69,7 @@ struct TrainSmem {
     float grad[kNumParams + 3];              // this CTA's partial gradient
     float part[kTrainWarps][kTrainPartCols + 3];
     // ldmatrix reads rows of 16 bytes: the staged operands start on 16-byte boundaries
-    alignas(16) uint32_t x[kTrainChunk * 4];             // staged rows: 8 bfloat16 inputs (16 bytes) each
+    alignas(16) uint32_t x[kTrainChunk * kXStride];      // staged rows: 16 bfloat16 inputs (32 bytes), padded
     float y[kTrainChunk];
     alignas(16) uint32_t h1[kTrainChunk * kActWords];    // bfloat16 GELU(z1) of the staged rows
     alignas(16) uint32_t dz2[kTrainChunk * kActWords];   // bfloat16 dL/dz2
@@ -115,13 +115,6 @@ __device__ __forceinline__ void ldsm_x4_trans(const void *p, uint32_t &r0, uint3
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
-__device__ __forceinline__ void ldsm_x2_trans(const void *p, uint32_t &r0, uint32_t &r1)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
-}
-
 // GELU and its derivative from one hardware tanh, on both halves of a packed pair (packed FP32
 // arithmetic): with u = sqrt(2/pi) (z + 0.044715 z^3) and t = tanh(u), GELU(z) = z (1 + t) / 2
 // and GELU'(z) = (1 + t) / 2 + z (1 - t^2) u'(z) / 2.
@@ -144,7 +137,7 @@ __device__ __forceinline__ void gelu_and_grad2(f32x2 z, f32x2 &h, f32x2 &dh)
 __device__ __forceinline__ void train_build_net(TrainSmem &s)
 {
     for (int i = threadIdx.x; i < kHidden * kInputs / 2; i += kTrainThreads)
-        s.W1[i] = pack_bf16x2(s.pfull[kOffW1 + 2 * i], s.pfull[kOffW1 + 2 * i + 1]);
+        s.W1[(i >> 3) * kXStride + (i & 7)] = pack_bf16x2(s.pfull[kOffW1 + 2 * i], s.pfull[kOffW1 + 2 * i + 1]);
     for (int i = threadIdx.x; i < kHidden * kHidden / 2; i += kTrainThreads) {
         const int o = i >> 5, c = i & 31;
         s.W2[o * kW2Stride + c] = pack_bf16x2(s.pfull[kOffW2 + o * kHidden + 2 * c], s.pfull[kOffW2 + o * kHidden + 2 * c + 1]);
@@ -177,15 +170,16 @@ __device__ __forceinline__ void train_tile(TrainSmem &s, int tile, float dscale,
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int r0 = 16 * tile + g, r1 = r0 + 8;
-    // layer 1: A = x (k = 8..15 zero), B[k][n] = W1[n][k]
-    const uint32_t a[4] = {s.x[r0 * 4 + t], s.x[r1 * 4 + t], 0u, 0u};
+    // layer 1: A = x (16 x 16), B[k][n] = W1[n][k]
+    const uint32_t a[4] = {s.x[r0 * kXStride + t], s.x[r1 * kXStride + t], s.x[r0 * kXStride + t + 4],
+                           s.x[r1 * kXStride + t + 4]};
     float gz1[8][4];
     uint32_t a2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int o = 8 * nt + 2 * t;
         float c[4] = {s.b1[o], s.b1[o + 1], s.b1[o], s.b1[o + 1]};
-        mma_bf16(c, a, s.W1[(8 * nt + g) * 4 + t], 0u);
+        mma_bf16(c, a, s.W1[(8 * nt + g) * kXStride + t], s.W1[(8 * nt + g) * kXStride + t + 4]);
         f32x2 h01, h23, d01, d23;
         gelu_and_grad2(f2_pack(c[0], c[1]), h01, d01);
         gelu_and_grad2(f2_pack(c[2], c[3]), h23, d23);
@@ -265,10 +259,10 @@ __device__ __forceinline__ void train_tile(TrainSmem &s, int tile, float dscale,
 
 // Batch contractions over the `nrows` staged rows (a multiple of 16), added into this warp's
 // accumulators: warp w takes dW2 rows o in [16 (w / 2), +16) and columns u in [32 (w % 2), +32)
-// (four n-tiles), warps 0..3 also dW1 rows u in [16 w, +16) (all 8 columns).  Operands are read
+// (four n-tiles), warps 0..3 also dW1 rows u in [16 w, +16) (all 16 columns, two n-tiles).  Operands are read
 // with ldmatrix.trans: the staged activations are row-major in the batch index r, which is the
 // products' k.
-__device__ __forceinline__ void train_contract(const TrainSmem &s, int nrows, float gw2[4][4], float gw1[4])
+__device__ __forceinline__ void train_contract(const TrainSmem &s, int nrows, float gw2[4][4], float gw1[2][4])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mi = lane >> 3, rr = lane & 7;
@@ -292,11 +286,13 @@ __device__ __forceinline__ void train_contract(const TrainSmem &s, int nrows, fl
         if (warp < 4) {
             uint32_t a1[4];
             ldsm_x4_trans(&s.dz1[ar * kActWords + 8 * warp + ((mi & 1) ? 4 : 0)], a1[0], a1[1], a1[2], a1[3]);
-            // B = x: 8 columns, rows r = kk + rr (+ 8 for odd mi; lanes 16..31 repeat 0..15)
+            // B = x for n-tiles 0 and 1: matrix mi holds rows r = kk + rr (+ 8 for odd mi), columns
+            // 0..7 (8..15 for mi >= 2)
             const int xr = kk + rr + ((mi & 1) ? 8 : 0);
-            uint32_t b0, b1;
-            ldsm_x2_trans(&s.x[xr * 4], b0, b1);
-            mma_bf16(gw1, a1, b0, b1);
+            uint32_t b[4];
+            ldsm_x4_trans(&s.x[xr * kXStride + ((mi & 2) ? 4 : 0)], b[0], b[1], b[2], b[3]);
+            mma_bf16(gw1[0], a1, b[0], b[1]);
+            mma_bf16(gw1[1], a1, b[2], b[3]);
         }
     }
 }
@@ -326,17 +322,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
     cluster_sync();  // every CTA of the cluster is running before any distributed store
 
     // rows of (step, chunk) are prefetched into registers one chunk ahead
-    float px[8], py = 0.f;
+    float px[kInputs], py = 0.f;
     auto fetch = [&](int step, int chunk) {
         const int local = chunk * kTrainChunk + tid;
         if (local < rows) {
             const size_t row = (size_t)step * a.B + (size_t)rank * rows + local;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) px[k] = __ldg(job.X + 8 * row + k);
+            for (int k = 0; k < kInputs; ++k) px[k] = __ldg(job.X + kInputs * row + k);
             py = __ldg(job.Y + row);
         } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) px[k] = 0.f;
+            for (int k = 0; k < kInputs; ++k) px[k] = 0.f;
             py = 0.f;
         }
     };
@@ -352,15 +348,16 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
             for (int e = 0; e < 2; ++e) acc.db1[nt][e] = acc.db2[nt][e] = acc.dw3[nt][e] = 0.f;
         }
         acc.db3 = 0.f;
-        float gw2[4][4], gw1[4] = {0.f, 0.f, 0.f, 0.f};
+        float gw2[4][4], gw1[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
         for (int j = 0; j < 4; ++j) gw2[j][0] = gw2[j][1] = gw2[j][2] = gw2[j][3] = 0.f;
         for (int ch = 0; ch < chunks; ++ch) {
             const int nrows = min(kTrainChunk, rows - ch * kTrainChunk);
-            s.x[tid * 4 + 0] = pack_bf16x2(px[0], px[1]);
-            s.x[tid * 4 + 1] = pack_bf16x2(px[2], px[3]);
-            s.x[tid * 4 + 2] = pack_bf16x2(px[4], px[5]);
-            s.x[tid * 4 + 3] = pack_bf16x2(px[6], px[7]);
+            uint4 *xrow = reinterpret_cast<uint4 *>(&s.x[tid * kXStride]);
+            xrow[0] = make_uint4(pack_bf16x2(px[0], px[1]), pack_bf16x2(px[2], px[3]), pack_bf16x2(px[4], px[5]),
+                                 pack_bf16x2(px[6], px[7]));
+            xrow[1] = make_uint4(pack_bf16x2(px[8], px[9]), pack_bf16x2(px[10], px[11]), pack_bf16x2(px[12], px[13]),
+                                 pack_bf16x2(px[14], px[15]));
             s.y[tid] = py;
             if (ch + 1 < chunks) fetch(step, ch + 1);
             else if (it + 1 < total) fetch((it + 1) % a.steps, 0);
@@ -385,11 +382,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
                 s.grad[kOffW2 + (o + 8) * kHidden + u + 1] = gw2[j][3];
             }
             if (warp < 4) {
-                const int u = 16 * warp + g, k = 2 * t;
-                s.grad[kOffW1 + u * kInputs + k] = gw1[0];
-                s.grad[kOffW1 + u * kInputs + k + 1] = gw1[1];
-                s.grad[kOffW1 + (u + 8) * kInputs + k] = gw1[2];
-                s.grad[kOffW1 + (u + 8) * kInputs + k + 1] = gw1[3];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int u = 16 * warp + g, k = 8 * j + 2 * t;
+                    s.grad[kOffW1 + u * kInputs + k] = gw1[j][0];
+                    s.grad[kOffW1 + u * kInputs + k + 1] = gw1[j][1];
+                    s.grad[kOffW1 + (u + 8) * kInputs + k] = gw1[j][2];
+                    s.grad[kOffW1 + (u + 8) * kInputs + k + 1] = gw1[j][3];
+                }
             }
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt) {

@@ -82,7 +82,8 @@ _u64, _i32, _dbl, _vp, _sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, cty
 _dptr = ctypes.POINTER(ctypes.c_double)
 _pm, _pp, _pl = ctypes.POINTER(mlmc_model), ctypes.POINTER(mlmc_payoff), ctypes.POINTER(mlmc_launch)
 
-MLMC_CV_PARAMS = 4801
+MLMC_CV_PARAMS = 5313
+MLMC_CV_INPUTS = 16
 MLMC_CV_LATTICE_POINTS = 65536
 MLMC_CV_MAX_LEVELS = 8
 
@@ -458,7 +459,7 @@ def mlmc_mlp_forward(params, d_X, N: int, d_G, stream=None) -> None:
 
 
 def mlmc_mlp_grad(params, d_X, d_Y, N: int, stream=None):
-    """(loss, gradient) of the mean squared error on device rows d_X [N][8], d_Y [N]."""
+    """(loss, gradient) of the mean squared error on device rows d_X [N][16], d_Y [N]."""
     import numpy as np
 
     arr, ptr = _floats(params)

@@ -61,7 +61,7 @@ def test_mlp_forward_matches_oracle(mlmc):
     import torch
 
     rng = np.random.default_rng(1)
-    X = rng.standard_normal((4096 + 17, 8)).astype(np.float32)
+    X = rng.standard_normal((4096 + 17, omlp.D)).astype(np.float32)
     theta = _params(3)
     d_X = torch.tensor(X, device="cuda")
     d_G = torch.zeros(len(X), dtype=torch.float32, device="cuda")
@@ -81,7 +81,7 @@ def test_mlp_grad_matches_oracle(mlmc, B):
     import torch
 
     rng = np.random.default_rng(2)
-    X = rng.standard_normal((B, 8)).astype(np.float32)
+    X = rng.standard_normal((B, omlp.D)).astype(np.float32)
     Y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + 0.1 * rng.standard_normal(B)).astype(np.float32)
     theta = _params(4)
     loss, grad = mlmc.mlmc_mlp_grad(theta, torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"), B)
@@ -91,21 +91,23 @@ def test_mlp_grad_matches_oracle(mlmc, B):
     grad = grad.astype(np.float64)
     assert np.linalg.norm(grad - want) <= 2e-2 * np.linalg.norm(want)
     # every parameter block separately
-    bounds = [0, 512, 576, 4672, 4736, 4800, 4801]
+    nw1 = 64 * omlp.D
+    bounds = [0, nw1, nw1 + 64, nw1 + 64 + 4096, nw1 + 128 + 4096, nw1 + 192 + 4096, omlp.N_PARAMS]
     for a, b in zip(bounds[:-1], bounds[1:]):
         assert np.linalg.norm(grad[a:b] - want[a:b]) <= 5e-2 * np.linalg.norm(want[a:b]) + 1e-7, (a, b)
 
 
-@pytest.mark.parametrize("M,level", [(4, 0), (4, 1), (4, 2), (4, 3), (2, 1), (2, 2), (8, 0), (8, 1)])
+@pytest.mark.parametrize("M,level", [(4, 0), (4, 1), (4, 2), (4, 3), (2, 1), (2, 2), (2, 3), (2, 4), (8, 0), (8, 1)])
 def test_training_data_matches_oracle(mlmc, M, level):
-    """(x, Y) pairs under the training tag: inputs from the Brownian grid (bridged below eight fine
-    steps), Y = P_l - P_{l-1} on the same path."""
+    """(x, Y) pairs under the training tag: inputs from the Brownian grid (bridged below sixteen
+    fine steps, from the first Philox block the path does not read: block 1 on levels of 1, 2 and 4
+    steps, block 2 on levels of 8), Y = P_l - P_{l-1} on the same path."""
     import torch
 
     p = mlmc.Problem(payoff="asian", **GBM)
     cv = mlmc.mlmc_cv_create(M, p)
     N, first = 600, 5
-    d_X = torch.zeros((N, 8), dtype=torch.float32, device="cuda")
+    d_X = torch.zeros((N, omlp.D), dtype=torch.float32, device="cuda")
     d_Y = torch.zeros(N, dtype=torch.float32, device="cuda")
     mlmc.mlmc_cv_training_data(cv, level, N, first, 9, d_X, d_Y)
     X, Y = d_X.cpu().numpy().astype(np.float64), d_Y.cpu().numpy().astype(np.float64)

@@ -84,15 +84,16 @@ def test_fine_increments_are_stream_normals():
         np.testing.assert_array_equal(dW, math.sqrt(p.T / n) * z)
 
 
-@pytest.mark.parametrize("M,level", [(4, 0), (4, 1), (4, 2), (4, 3), (2, 1), (2, 2), (8, 1)])
+@pytest.mark.parametrize("M,level", [(4, 0), (4, 1), (4, 2), (4, 3), (2, 1), (2, 2), (2, 3), (2, 4), (8, 1)])
 def test_grid_brownian_law(M, level):
-    """The T/8 grid values are a Brownian path: Cov(W(s), W(t)) = min(s, t), on the levels whose
-    grid is the fine path and on those refined by Brownian-bridge midpoints; W(T) and the grid
-    points the level's own grid contains equal the running sums of its fine increments."""
+    """The T/16 grid values are a Brownian path: Cov(W(s), W(t)) = min(s, t), on the levels whose
+    grid is the fine path and on those refined by Brownian-bridge midpoints (a midpoint normal that
+    reused one of the path's own would break the covariance); W(T) and the grid points the level's
+    own grid contains equal the running sums of its fine increments."""
     T = 1.0
     n = 20000
     W = np.array([oracle.grid_brownian(level, M, s, T, seed=13) for s in range(n)])
-    t = (np.arange(8) + 1) * T / 8
+    t = (np.arange(16) + 1) * T / 16
     cov = np.cov(W.T, bias=True)
     want = np.minimum.outer(t, t)
     assert np.max(np.abs(cov - want)) < 5 * math.sqrt(2.0 / n) * T
@@ -104,10 +105,10 @@ def test_grid_brownian_law(M, level):
         Wg = oracle.grid_brownian(level, M, s, T, seed=13)
         cum = np.cumsum(dW)
         for k in range(nf):
-            idx = (k + 1) * 8 // nf - 1 if nf <= 8 else None
+            idx = (k + 1) * 16 // nf - 1 if nf <= 16 else None
             if idx is not None:
                 assert Wg[idx] == pytest.approx(cum[k], rel=1e-13, abs=1e-14)
-        assert Wg[7] == pytest.approx(cum[-1], rel=1e-12, abs=1e-14)
+        assert Wg[15] == pytest.approx(cum[-1], rel=1e-12, abs=1e-14)
 
 
 def test_payoffs_hand_evaluated():
