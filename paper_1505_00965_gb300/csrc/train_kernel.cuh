@@ -427,8 +427,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_cluster_kernel(const T
         }
         __syncthreads();
         // push the partial gradient to the owners: owner q keeps C slices, this CTA's at rank S.
-        // q = i / S as a multiply-high by ceil(2^32 / S): for i < 4801 and S >= 301 the error
-        // i (ceil(2^32 / S) - 2^32 / S) / 2^32 stays below 1e-6 while i / S is at least 1 / S below
+        // q = i / S as a multiply-high by ceil(2^32 / S): for i < 5313 and S >= 333 the error
+        // i (ceil(2^32 / S) - 2^32 / S) / 2^32 stays below 2e-6 while i / S is at least 1 / S below
         // the next integer, so the quotient is exact.
         for (int i = tid; i < kNumParams; i += kTrainThreads) {
             const int q = (int)__umulhi((uint32_t)i, inv_s);
