@@ -328,6 +328,11 @@ def side_workloads(mlmc, stream) -> dict:
         "estimate_median": {"fp32_cv": statistics.median(r.P for r in a),
                             "fp32_plain": statistics.median(r.P for r in b),
                             "fp64_plain": statistics.median(r.P for r in c)}}
+    # the same trained networks at the benchmark's eps (the plain FP32 time there is the line's
+    # time_to_eps_ms.asian)
+    out["learned_cv"]["time_to_eps_ms_at_bench_eps"] = {
+        "eps": EPS, "fp32_cv": statistics.median(
+            mlmc.mlmc_estimate_cv(EPS, cv, s, Lmin=LMIN, Lmax=LMAX, N0=N0, stream=stream).wall_ms for s in seeds)}
     mlmc.mlmc_cv_free(cv)
     return out
 
