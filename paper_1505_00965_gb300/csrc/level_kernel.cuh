@@ -666,6 +666,27 @@ __device__ __forceinline__ void block_increments(const LevelParams &p, uint64_t 
     }
 }
 
+// Level 0 of the FP32 path, one Euler step S_1 = S_0 (1 + d), for the payoffs whose value is
+// affine in d up to a max: the discounted payoff in two or three operations, its constants
+// formed in FP64 (disc S_0, disc S_0 / 2, disc (S_0 - K)).  The same value as payoff_value on the
+// one-step path in exact arithmetic: European disc (S_1 - K)^+; arithmetic Asian (trapezoid,
+// n = 1) A = (S_0 + S_1) / 2 = S_0 (1 + d / 2); lookback max(S_0, S_1) = S_0 (1 + max(d, 0)).
+template <int PAY> constexpr bool kLevel0Affine = PAY == kEuropean || PAY == kAsian || PAY == kLookback;
+struct Level0Consts {
+    float dS0, half_dS0, dS0mK;
+};
+__device__ __forceinline__ Level0Consts level0_consts(const LevelParams &p)
+{
+    return {(float)(p.disc * p.S0), (float)(0.5 * p.disc * p.S0), (float)(p.disc * (p.S0 - p.K))};
+}
+template <int PAY>
+__device__ __forceinline__ float level0_payoff(float d, const Level0Consts &c)
+{
+    if constexpr (PAY == kEuropean) return fmaxf(fmaf(d, c.dS0, c.dS0mK), 0.f);
+    else if constexpr (PAY == kAsian) return fmaxf(fmaf(d, c.half_dS0, c.dS0mK), 0.f);
+    else return fmaxf(fmaf(fmaxf(d, 0.f), c.dS0, c.dS0mK), 0.f);
+}
+
 // The samples of Philox block q (slots r = 0 .. G - 1, sample q G + r) that lie in
 // [first, end), from the block's normals z and increments d.
 template <typename R, int PAY, bool MIL>
@@ -683,9 +704,13 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
         R Y[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
-            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-            Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
+                Y[r] = level0_payoff<PAY>(d[r], level0_consts(p));
+            } else {
+                R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            }
             if (y_out) y_out[q * 4 + r - first] = (double)Y[r];
         }
         add_moments4(Y, m, b1, b2, b3, b4, nb);
@@ -700,8 +725,12 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
         R cS = R(1), csum = R(0), chi = R(1), clo = R(1), cls = R(0);
         R Y;
         if (nf == 1) {
-            em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-            Y = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
+                Y = level0_payoff<PAY>(d[r], level0_consts(p));
+            } else {
+                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                Y = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+            }
         } else {  // nf == 2, level 1 with M = 2: two fine steps, one coarse step
             const R d0 = d[2 * (r & 1)], d1 = d[2 * (r & 1) + 1];
             em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d0);
@@ -762,6 +791,7 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const uint64_t qa = first / 4 + ((first & 3) != 0), qb = end / 4;
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf);
     const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
+    const Level0Consts c0 = level0_consts(p);
     // two copies of the loop, with and without per-sample output, keep the output test out of it
     auto whole_blocks = [&](auto with_output) {
         for (uint64_t q = qa + t; q < qb; q += T) {
@@ -769,9 +799,13 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
             block_increments<R, MIL, RK>(p, q, z, d);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
-                em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-                Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+                if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
+                    Y[r] = level0_payoff<PAY>(d[r], c0);
+                } else {
+                    R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+                    em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                    Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+                }
                 if constexpr (decltype(with_output)::value) y_out[q * 4 + r - first] = (double)Y[r];
             }
             add_moments4(Y, m, b1, b2, b3, b4, nb);
