@@ -22,7 +22,7 @@
  *   - All floating-point arguments are FP64; the path arithmetic precision is chosen by an
  *     mlmc_precision argument.
  *   - Random numbers: sample s of level l draws Philox4x32-10 blocks with key = (seed low,
- *     seed high) and counter = (j, s low, s high, (tag << 16) | l), j = 0, 1, ...  Block j
+ *     seed high) and counter = ((tag << 16) | l, j, s high, s low), j = 0, 1, ...  Block j
  *     gives normals 4j..4j+3 by two Box--Muller pairs; fine step k takes normal k,
  *     dW_k = sqrt(T / M^l) z_k.  Every level and every sample index therefore has its own,
  *     independent numbers (Sec. 5: fresh random numbers on every level), and a sample range

@@ -21,7 +21,7 @@
  * Readings where the paper is silent (the Asian and lookback payoffs are only named in Sec. 7;
  * the random stream is not specified at all):
  *   - Random stream: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Key = (seed low 32
- *     bits, seed high 32 bits).  Counter = (j, s low, s high, (tag << 16) | level) where j is
+ *     bits, seed high 32 bits).  Counter = ((tag << 16) | level, j, s high, s low) where j is
  *     the call index inside one sample and s the sample index inside the level.  Call j gives
  *     four words x0..x3; the pairs (x0,x1) and (x2,x3) each give two normals by Box--Muller.
  *   - Uniforms from a 32-bit word x: FP64 stream u = (x + 1) 2^-32; FP32 stream
@@ -99,8 +99,8 @@ void oracle_normals(uint64_t seed, int level, int tag, uint64_t s, int stream, i
 {
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     for (int j = 0; 4 * j < n; ++j) {
-        uint32_t ctr[4] = { (uint32_t)j, (uint32_t)s, (uint32_t)(s >> 32),
-                            ((uint32_t)tag << 16) | (uint32_t)level };
+        uint32_t ctr[4] = { ((uint32_t)tag << 16) | (uint32_t)level, (uint32_t)j, (uint32_t)(s >> 32),
+                            (uint32_t)s };
         uint32_t x[4];
         oracle_philox4x32_10(ctr, key, x);
         for (int pair = 0; pair < 2; ++pair) {

@@ -78,7 +78,7 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
         const uint32_t G = 4u / (uint32_t)nf;
         const uint64_t qb = s / G;
         const uint32_t slot = (uint32_t)(s % G);
-        const uint4 xb = philox4x32_10(make_uint4(0u, (uint32_t)qb, (uint32_t)(qb >> 32), p.ctr3), p.key0, p.key1);
+        const uint4 xb = philox4x32_10(make_uint4(p.ctr3, 0u, (uint32_t)(qb >> 32), (uint32_t)qb), p.key0, p.key1);
         float rho, c, sn, z[4];
         BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
         z[0] = rho * c;
@@ -105,7 +105,7 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
         int f = 0, cnt = 0;
         grid[0] = 0.f;
         for (int j = 0; j < nf / 4; ++j) {
-            const uint4 xb = philox4x32_10(make_uint4((uint32_t)j, slo, shi, p.ctr3), p.key0, p.key1);
+            const uint4 xb = philox4x32_10(make_uint4(p.ctr3, (uint32_t)j, shi, slo), p.key0, p.key1);
             float rho, c, sn, z[4];
             BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
             z[0] = rho * c;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (j < nblk) {
-                const uint4 xb = philox4x32_10(make_uint4((uint32_t)(b0 + j), slo, shi, p.ctr3), p.key0, p.key1);
+                const uint4 xb = philox4x32_10(make_uint4(p.ctr3, (uint32_t)(b0 + j), shi, slo), p.key0, p.key1);
                 float rho, c, sn;
                 BoxMuller<float>::pair(xb.x, xb.y, rho, c, sn);
                 zb[4 * j + 0] = rho * c;
@@ -162,12 +162,12 @@ __device__ __forceinline__ void cv_sample(const LevelParams &p, const CvConsts &
     }
     levy_coordinates(grid, k.inv_tg, x);
     const float logS0 = PAY == kGeoAsian ? logf(S0) : 0.f;
-    const float Pf = payoff_from<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, (float)nf * logS0 + fls, k.inv_nf, k.K,
+    const float Pf = payoff_from<float, PAY>(S0 * fS, S0 * fsum, S0 * fhi, lpost_of((float)nf, logS0, fls), k.inv_nf, k.K,
                                              k.disc, S0, k.Q);
     if (p.level == 0) {
         Y = Pf;
     } else {
-        const float Pc = payoff_from<float, PAY>(S0 * cS, S0 * csum, S0 * chi, (float)(nf / M) * logS0 + cls,
+        const float Pc = payoff_from<float, PAY>(S0 * cS, S0 * csum, S0 * chi, lpost_of((float)(nf / M), logS0, cls),
                                                  k.inv_nc, k.K, k.disc, S0, k.Q);
         Y = Pf - Pc;
     }

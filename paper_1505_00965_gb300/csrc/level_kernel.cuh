@@ -75,6 +75,32 @@ __device__ __forceinline__ void em_step(R &S, R &sum, R &hi, R &lo, R &lsum, R d
     if constexpr (PAY == kGeoAsian) lsum += log(S);
 }
 
+// Separately rounded multiply, add and subtract, which the compiler may not fuse with a
+// neighbouring operation.  The sample loops exist in several copies (with and without per-sample
+// output, straight-line and looped), and floating-point contraction is decided per copy: the
+// payoff, the quantities passed to it and the moment sums use these so that a sample's value
+// and a launch's sums do not depend on the copy that computes them.
+template <typename R> __device__ __forceinline__ R mul_rn(R a, R b)
+{
+    if constexpr (sizeof(R) == 4) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+template <typename R> __device__ __forceinline__ R add_rn(R a, R b)
+{
+    if constexpr (sizeof(R) == 4) return __fadd_rn(a, b);
+    else return __dadd_rn(a, b);
+}
+template <typename R> __device__ __forceinline__ R sub_rn(R a, R b)
+{
+    if constexpr (sizeof(R) == 4) return __fsub_rn(a, b);
+    else return __dsub_rn(a, b);
+}
+// The geometric Asian's log-sum argument n log S_0 + sum log(S_i / S_0).
+template <typename R> __device__ __forceinline__ R lpost_of(R n, R logS0, R lsum)
+{
+    return add_rn(mul_rn(n, logS0), lsum);
+}
+
 // Discounted payoff of a path from its totals: final value Sn, sum of post-step values
 // `post` (i = 1..n), maximum over S_0..S_n, sum of log post-step values; n = steps.  K, disc, S0
 // and Q are the strike, discount factor, initial value and digital cash in the path's precision.
@@ -82,22 +108,23 @@ template <typename R, int PAY>
 __device__ __forceinline__ R payoff_from(R Sn, R post, R hi, R lpost, R inv_n, R K, R disc, R S0, R Q)
 {
     if constexpr (PAY == kEuropean) {
-        return disc * fmax(Sn - K, R(0));
+        return mul_rn(disc, fmax(sub_rn(Sn, K), R(0)));
     } else if constexpr (PAY == kAsian) {
         // (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 = (1/n) (sum_{i=1..n} S_i + (S_0 - S_n) / 2)
-        const R A = (post + R(0.5) * (S0 - Sn)) * inv_n;
-        return disc * fmax(A - K, R(0));
+        const R A = mul_rn(add_rn(post, mul_rn(R(0.5), sub_rn(S0, Sn))), inv_n);
+        return mul_rn(disc, fmax(sub_rn(A, K), R(0)));
     } else if constexpr (PAY == kLookback) {
-        return disc * fmax(hi - K, R(0));
+        return mul_rn(disc, fmax(sub_rn(hi, K), R(0)));
     } else if constexpr (PAY == kDigital) {
-        return Sn > K ? disc * Q : (Sn == K ? R(0.5) * disc * Q : R(0));
+        return Sn > K ? mul_rn(disc, Q) : (Sn == K ? mul_rn(mul_rn(R(0.5), disc), Q) : R(0));
     } else if constexpr (PAY == kLinear) {
         return Sn;
     } else {  // kGeoAsian
-        const R lg = (lpost + R(0.5) * (PathAcc<R, PAY, false>::log_r(S0) -
-                                        PathAcc<R, PAY, false>::log_r(Sn))) * inv_n;
+        const R lg = mul_rn(add_rn(lpost, mul_rn(R(0.5), sub_rn(PathAcc<R, PAY, false>::log_r(S0),
+                                                                PathAcc<R, PAY, false>::log_r(Sn)))),
+                            inv_n);
         const R G = sizeof(R) == 4 ? R(expf(float(lg))) : R(exp(double(lg)));
-        return disc * fmax(G - K, R(0));
+        return mul_rn(disc, fmax(sub_rn(G, K), R(0)));
     }
 }
 
@@ -139,7 +166,7 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
     const R a_s = R(p.a) * R(kSqrt2Ln2);  // FP32: sigma sqrt(h) sqrt(2 ln 2), for box_muller_lg2
     // one Philox call: four fine steps and the coarse steps they complete
     auto call = [&](int j) {
-        const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, slo, shi, p.ctr3));
+        const uint4 x = philox_of<RK>(p, make_uint4(p.ctr3, (uint32_t)j, shi, slo));
         R rho, c, s;
         R d[4];
         if constexpr (!MIL && sizeof(R) == 4) {
@@ -224,7 +251,7 @@ __device__ __forceinline__ void simulate_steps(const LevelParams &p, uint32_t sl
 // (M = 4: a Philox block is one coarse step, read backwards; M = 2: its two pairs swapped).
 template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false,
           bool LONG = false>
-__device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint64_t s[NS], R fS[NS],
+__device__ __forceinline__ void simulate_multi(const LevelParams &p, uint32_t s_hi, const uint32_t s_lo[NS], R fS[NS],
                                                R fsum[NS], R fhi[NS], R fls[NS], R cS[NS], R csum[NS],
                                                R chi[NS], R cls[NS], R aS[NS], R asum[NS], R ahi[NS],
                                                R als[NS])
@@ -256,7 +283,7 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, const uint6
         R d[NS][4];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-            const uint4 x = philox_of<RK>(p, make_uint4((uint32_t)j, (uint32_t)s[i], (uint32_t)(s[i] >> 32), p.ctr3));
+            const uint4 x = philox_of<RK>(p, make_uint4(p.ctr3, (uint32_t)j, s_hi, s_lo[i]));
             R rho, c, sn;
             if constexpr (!MIL && sizeof(R) == 4) {
                 box_muller_lg2(x.x, x.y, rho, c, sn);
@@ -423,9 +450,9 @@ __device__ __forceinline__ void finish_sums(double m[4], const LevelParams &p)
 // batch into m, which keeps FP64 off the per-sample path.
 __device__ __forceinline__ void batch_add(float Y, float &b1, float &b2, float &b3, float &b4)
 {
-    const float y2 = Y * Y;
-    b1 += Y;
-    b2 += y2;
+    const float y2 = __fmul_rn(Y, Y);
+    b1 = __fadd_rn(b1, Y);
+    b2 = __fadd_rn(b2, y2);
     b3 = fmaf(y2, Y, b3);
     b4 = fmaf(y2, y2, b4);
 }
@@ -453,9 +480,9 @@ __device__ __forceinline__ void add_moments4(const float Y[4], double m[4], floa
 __device__ __forceinline__ void add_moments(double Y, double m[4], float &, float &, float &,
                                             float &, int &)
 {
-    const double y2 = Y * Y;
-    m[0] += Y;
-    m[1] += y2;
+    const double y2 = __dmul_rn(Y, Y);
+    m[0] = __dadd_rn(m[0], Y);
+    m[1] = __dadd_rn(m[1], y2);
     m[2] = fma(y2, Y, m[2]);
     m[3] = fma(y2, y2, m[3]);
 }
@@ -519,10 +546,10 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
         simulate_steps<R, MT, PAY, false, MIL, RK, LONG>(p, slo, shi, 0, p.nf >> 2, fa, ca);
         const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
         const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
-                                          R(p.nf) * logS0 + fa.lsum, inv_nf, p);
+                                          lpost_of(R(p.nf), logS0, fa.lsum), inv_nf, p);
         if (p.fine_only) return Pf;
         const R Pc = payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
-                                          R(p.nf / p.M) * logS0 + ca.lsum, inv_nc, p);
+                                          lpost_of(R(p.nf / p.M), logS0, ca.lsum), inv_nc, p);
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
@@ -548,37 +575,43 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
 {
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
     const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
-    // The range in spans of at most 2^31 samples, each walked with 32-bit offsets (threads leave
-    // the loop independently: nothing in it synchronises the warp).  With 64-bit offsets and a
-    // warp-uniform exit the loop control took about 25 of the 126 instructions of a sample on
-    // levels with M^l = 4.
+    // The range in spans of at most 2^31 samples that stay inside one 2^32-aligned block of sample
+    // indices, each walked with 32-bit offsets (threads leave the loop independently: nothing in it
+    // synchronises the warp).  The sample index's high word is then the same for the whole span,
+    // so the Philox products of that counter word are formed once per span, not once per sample.
+    // With 64-bit offsets and a warp-uniform exit the loop control took about 25 of the 126
+    // instructions of a sample on levels with M^l = 4.
     const uint32_t t32 = (uint32_t)t, T32 = (uint32_t)T;
     for (uint64_t c0 = 0; c0 < N;) {
-        const uint32_t n = (uint32_t)(N - c0 < kSpan32 ? N - c0 : kSpan32);  // c0 + n <= N: no wrap
+        const uint64_t start = first + c0;
+        const uint64_t room = (uint64_t(1) << 32) - (uint32_t)start;  // samples left below the next 2^32 boundary
+        const uint64_t left = N - c0 < kSpan32 ? N - c0 : kSpan32;
+        const uint32_t n = (uint32_t)(left < room ? left : room);  // c0 + n <= N
+        const uint32_t s_hi = (uint32_t)(start >> 32), lo0 = (uint32_t)start;
         for (uint32_t i0 = t32; i0 < n; i0 += NS * T32) {
-            uint64_t s[NS];
+            uint32_t s_lo[NS];
             bool valid[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
                 const uint32_t j = i0 + (uint32_t)i * T32;
                 valid[i] = i == 0 || j < n;
-                s[i] = first + c0 + (valid[i] ? j : i0);
+                s_lo[i] = lo0 + (valid[i] ? j : i0);  // below 2^32: the span stops at the boundary
             }
             R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
             R aS[NS], asum[NS], ahi[NS], als[NS];
-            simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s, fS, fsum, fhi, fls, cS, csum, chi, cls,
+            simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s_hi, s_lo, fS, fsum, fhi, fls, cS, csum, chi, cls,
                                                                        aS, asum, ahi, als);
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
                 R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
-                                            R(p.nf) * logS0 + fls[i], inv_nf, p);
+                                            lpost_of(R(p.nf), logS0, fls[i]), inv_nf, p);
                 if constexpr (ANTI)
-                    Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
-                                                             R(p.nf) * logS0 + als[i], inv_nf, p));
+                    Pf = mul_rn(R(0.5), add_rn(Pf, payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
+                                                                        lpost_of(R(p.nf), logS0, als[i]), inv_nf, p)));
                 R Y = Pf;
                 if (!p.fine_only)
                     Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
-                                              R(p.nf / p.M) * logS0 + cls[i], inv_nc, p);
+                                              lpost_of(R(p.nf / p.M), logS0, cls[i]), inv_nc, p);
                 if (valid[i]) {
                     if (y_out) y_out[c0 + i0 + (uint32_t)i * T32] = (double)Y;
                     add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -632,13 +665,14 @@ __device__ __forceinline__ void regular_range(const LevelParams &p, uint64_t fir
     }
 }
 
-// The four normals z of Philox block q of a level with M^l < 4 and their step increments d.
+// The four normals z of Philox block q = (q_hi, q_lo) of a level with M^l < 4 and their step
+// increments d.
 template <typename R, bool MIL, bool RK = true>
-__device__ __forceinline__ void block_increments(const LevelParams &p, uint64_t q, R z[4], R d[4])
+__device__ __forceinline__ void block_increments(const LevelParams &p, uint32_t q_hi, uint32_t q_lo, R z[4], R d[4])
 {
     const R a = R(p.a), rh = R(p.rh), c2 = R(p.c2), rhm = R(p.rh - p.c2);
     const bool u23 = p.u23 != 0;
-    const uint4 x = philox_of<RK>(p, make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3));
+    const uint4 x = philox_of<RK>(p, make_uint4(p.ctr3, 0u, q_hi, q_lo));
     R rho, c, s;
     if constexpr (!MIL && sizeof(R) == 4) {
         // FP32 Euler--Maruyama needs the increments only (z is left unset)
@@ -699,8 +733,9 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
     const R a = R(p.a), S0 = R(p.S0), c2 = R(p.c2), rhm = R(p.rh - p.c2);
     const R inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
     const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
-    if (nf == 1 && q * 4 >= first && q * 4 + 4 <= end) {
-        // four whole level-0 samples: no per-sample range checks, moments added together
+    if (nf == 1 && q * 4 >= first && end - q * 4 >= 4) {
+        // four whole level-0 samples: no per-sample range checks, moments added together (the
+        // test avoids q * 4 + 4, which wraps to 0 for the last block below 2^64)
         R Y[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -743,14 +778,14 @@ __device__ __forceinline__ void small_block(const LevelParams &p, uint64_t q, ui
                 dcs = d0 + d1;
             }
             em_step<R, PAY, false>(cS, csum, chi, clo, cls, dcs);
-            R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, R(2) * logS0 + fls, inv_nf, p);
+            R Pf = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, lpost_of(R(2), logS0, fls), inv_nf, p);
             if (p.antithetic) {
                 // the antithetic fine path: the coarse step's two increments swapped
                 R aS = R(1), asum = R(0), ahi = R(1), alo = R(1), als = R(0);
                 em_step<R, PAY, false>(aS, asum, ahi, alo, als, d1);
                 em_step<R, PAY, false>(aS, asum, ahi, alo, als, d0);
-                Pf = R(0.5) * (Pf + payoff_value<R, PAY>(S0 * aS, S0 * asum, S0 * ahi, R(2) * logS0 + als,
-                                                         inv_nf, p));
+                Pf = mul_rn(R(0.5), add_rn(Pf, payoff_value<R, PAY>(S0 * aS, S0 * asum, S0 * ahi, lpost_of(R(2), logS0, als),
+                                                         inv_nf, p)));
             }
             if (p.fine_only) {
                 Y = Pf;
@@ -780,7 +815,8 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     if (p.nf != 1) {
         for (uint64_t u = t; u < nq; u += T) {
             R z[4], d[4];
-            block_increments<R, MIL, RK>(p, q0 + u, z, d);
+            const uint64_t q = q0 + u;
+            block_increments<R, MIL, RK>(p, (uint32_t)(q >> 32), (uint32_t)q, z, d);
             small_block<R, PAY, MIL>(p, q0 + u, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
         }
         return;
@@ -792,23 +828,33 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf);
     const R logS0 = PAY == kGeoAsian ? log(S0) : R(0);
     const Level0Consts c0 = level0_consts(p);
-    // two copies of the loop, with and without per-sample output, keep the output test out of it
+    // two copies of the loop, with and without per-sample output, keep the output test out of it;
+    // the blocks go in spans inside one 2^32-aligned run of block indices, so the counter's high
+    // word and its Philox products stay fixed over a span
     auto whole_blocks = [&](auto with_output) {
-        for (uint64_t q = qa + t; q < qb; q += T) {
-            R z[4], d[4], Y[4];
-            block_increments<R, MIL, RK>(p, q, z, d);
+        for (uint64_t qs = qa; qs < qb;) {
+            const uint64_t room = (uint64_t(1) << 32) - (uint32_t)qs;
+            const uint64_t len = qb - qs < room ? qb - qs : room;
+            const uint32_t q_hi = (uint32_t)(qs >> 32), lo0 = (uint32_t)qs;
+            for (uint64_t u = t; u < len; u += T) {
+                const uint32_t q_lo = lo0 + (uint32_t)u;  // below 2^32: the span stops at the boundary
+                R z[4], d[4], Y[4];
+                block_increments<R, MIL, RK>(p, q_hi, q_lo, z, d);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
-                    Y[r] = level0_payoff<PAY>(d[r], c0);
-                } else {
-                    R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
-                    em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
-                    Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+                for (int r = 0; r < 4; ++r) {
+                    if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
+                        Y[r] = level0_payoff<PAY>(d[r], c0);
+                    } else {
+                        R fS = R(1), fsum = R(0), fhi = R(1), flo = R(1), fls = R(0);
+                        em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
+                        Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
+                    }
+                    if constexpr (decltype(with_output)::value)
+                        y_out[(qs + u) * 4 + r - first] = (double)Y[r];
                 }
-                if constexpr (decltype(with_output)::value) y_out[q * 4 + r - first] = (double)Y[r];
+                add_moments4(Y, m, b1, b2, b3, b4, nb);
             }
-            add_moments4(Y, m, b1, b2, b3, b4, nb);
+            qs += len;
         }
     };
     if (y_out) whole_blocks(std::true_type{});
@@ -819,7 +865,7 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     if ((t == 0 && first_partial) || (t == 1 && last_partial)) {
         const uint64_t q = t == 0 ? q0 : qlast;
         R z[4], d[4];
-        block_increments<R, MIL, RK>(p, q, z, d);
+        block_increments<R, MIL, RK>(p, (uint32_t)(q >> 32), (uint32_t)q, z, d);
         small_block<R, PAY, MIL>(p, q, first, end, z, d, m, b1, b2, b3, b4, nb, y_out);
     }
 }

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) quintic_level_kernel(const LevelParams p)
     const bool u23 = p.u23 != 0;
     for (uint64_t u = t; u < nq; u += T) {
         const uint64_t q = q0 + u;
-        const uint4 w = philox4x32_10(make_uint4(0u, (uint32_t)q, (uint32_t)(q >> 32), p.ctr3), p.rkey);
+        const uint4 w = philox4x32_10(make_uint4(p.ctr3, 0u, (uint32_t)(q >> 32), (uint32_t)q), p.rkey);
         R rho, c, s, x0[4];
         BoxMuller<R>::pair(w.x, w.y, rho, c, s, u23);
         x0[0] = rho * c;

@@ -74,9 +74,23 @@ def test_explicit_level0_matches_oracle(mlmc, precision):
     assert np.all(np.abs(y - yo) <= tol)
 
 
+def _amplification(x0, h, n):
+    """Upper bound on how much the explicit map x -> x - h x^5 enlarges a perturbation over n
+    steps from x0: the product of max(1, |1 - 5 h x_k^4|) along the path (first order)."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    a = np.ones_like(x)
+    with np.errstate(over="ignore", invalid="ignore"):
+        for _ in range(n):
+            a *= np.maximum(1.0, np.abs(1.0 - 5.0 * h * x ** 4))
+            x = x - h * x ** 5
+    return a
+
+
 def test_explicit_deep_paths_match_or_blow_up_together(mlmc):
     """FP64, level 2 (16 steps): samples whose oracle path stays below 10 in size match to the
-    tamed-style bound; the others are above 1e3 or non-finite on both sides."""
+    tamed-style bound times the explicit map's amplification of a rounding difference along the
+    path (near the blow-up threshold one step multiplies it by up to |1 - 5 h x^4|); the others
+    are above 1e3 or non-finite on both sides."""
     seed, N = 23, 40000
     p = _problem(mlmc, "em")
     _, y = run_level(mlmc, 2, 4, N, 0, p, seed, "fp64")
@@ -88,8 +102,9 @@ def test_explicit_deep_paths_match_or_blow_up_together(mlmc):
     calm = np.isfinite(xf) & np.isfinite(xc) & (np.abs(xf) < 10) & (np.abs(xc) < 10)
     wild = ~np.isfinite(yo) | (np.abs(yo) > 1e3)
     assert calm.sum() > 0.9 * N and wild.sum() > 50
-    tol = 8.0 * (1.0 + x0 ** 2) * (EZ["fp64"] + 4 * U["fp64"] * math.sqrt(17))
-    assert np.all(np.abs(y[calm] - yo[calm]) <= tol[calm] * 1e3)
+    amp = np.maximum(_amplification(x0, T / 16, 16), _amplification(x0, T / 4, 4))
+    tol = 8.0 * (1.0 + x0 ** 2) * (EZ["fp64"] + 4 * U["fp64"] * math.sqrt(17)) * amp
+    assert np.all(np.abs(y[calm] - yo[calm]) <= 4.0 * tol[calm])
     assert np.all(~np.isfinite(y[wild]) | (np.abs(y[wild]) > 1e2))
 
 
