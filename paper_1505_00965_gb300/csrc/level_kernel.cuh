@@ -354,10 +354,12 @@ __device__ __forceinline__ void simulate_multi(const LevelParams &p, uint32_t s_
         }
     };
     if constexpr (!(LONG && kBlockedSum<R, PAY>)) {
-        if constexpr (PAY == kAsian && CALLS == 0) {
+        if constexpr (CALLS == 0) {
             // two calls per iteration: the arithmetic-Asian kernel otherwise waited on its MUFU
-            // results (short-scoreboard stalls 0.21 per issue against 0.04 in the split form)
-            // and ran 5 % slower than its split form; unrolled it matches it
+            // results (short-scoreboard stalls 0.21 per issue against 0.04 in the split form) and
+            // ran 5 % slower than its split form.  The lookback kernel ran slower unrolled until
+            // the counter layout left 16 loop-variant multiplies per block; with it, unrolled
+            // runs 4 % faster (1.229 -> 1.280e12 steps/s at level 6 over whole waves)
 #pragma unroll 2
             for (int j = 0; j < calls; ++j) call(j);
         } else {
