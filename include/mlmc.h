@@ -123,7 +123,8 @@ enum { MLMC_TAG_PATHS = 0, MLMC_TAG_CV_MEAN = 1, MLMC_TAG_CV_TRAIN = 2 };
  *                      them by a product scan (GBM's step is multiplicative); requires
  *                      M^l / lanes_per_path to be a multiple of max(M, 4); GBM only (QUINTIC_ODE
  *                      paths are nonlinear and run one thread per sample)
- *   blocks             grid size; the kernel strides over the samples */
+ *   blocks             grid size, blocks x threads_per_block below 2^31; the kernel strides
+ *                      over the samples */
 typedef struct mlmc_launch {
     int32_t threads_per_block;
     int32_t lanes_per_path;
@@ -132,8 +133,12 @@ typedef struct mlmc_launch {
                               per-sample launch steps two samples' paths in lockstep (two
                               independent Philox and step chains for the scheduler to interleave);
                               FP32 Euler--Maruyama paths of the coupled or single-level estimator
-                              with M^l >= 4 and lanes_per_path = 1 only.  The samples and their Y
-                              are the same; the FP32 moment sums add them in another order. */
+                              with M^l >= 4 and lanes_per_path = 1 only.  Thread t of a grid of
+                              T threads takes samples t, t + T, ... as with 1, in pairs, and runs
+                              an unpaired last sample alone; the automatic grid is the same.  The
+                              samples and their Y are the same; the FP32 moment sums add them in
+                              another order.  Automatic: 2 for FP32 Euler--Maruyama whole paths
+                              with M = 4 and M^l >= 16, else 1 (or the autotuner's choice). */
 } mlmc_launch;
 
 /* Message describing the last failure on this host thread ("" if none). */

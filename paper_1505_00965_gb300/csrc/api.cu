@@ -195,7 +195,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     // samples per thread: the two-sample kernel exists for FP32 Euler--Maruyama whole paths
     const bool ns2_ok = !split && !small && precision == MLMC_FP32_PATH && scheme == MLMC_EULER_MARUYAMA &&
                         threads <= kNs2MaxThreads;
-    int ns = ns_req ? ns_req : (have_tuned && tuned.ns ? tuned.ns : kDefaultSamplesPerThread);
+    const int auto_ns = ns2_ok && M == 4 && nf >= kNs2MinSteps ? 2 : kDefaultSamplesPerThread;
+    int ns = ns_req ? ns_req : (have_tuned && tuned.ns ? tuned.ns : auto_ns);
     if (ns == 2 && !ns2_ok) {
         if (ns_req == 2)
             return fail(MLMC_EINVAL, "samples_per_thread 2 needs FP32 Euler--Maruyama paths with M^l >= 4, "
@@ -211,10 +212,14 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     if (rc) return rc;
     int blocks = launch && launch->blocks ? launch->blocks : 0;
     if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
+    // the sample loops stride by the grid's thread count in 32-bit offsets below 2^31
+    if ((uint64_t)blocks * (uint64_t)threads >= (uint64_t(1) << 31))
+        return fail(MLMC_EINVAL, "blocks x threads_per_block must be below 2^31");
     if (!blocks) {
-        // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels
+        // work items: samples x lanes, or Philox blocks of 4 / M^l samples on small levels (the
+        // two-sample kernel runs on the one-sample kernel's grid)
         const double items = small ? std::ceil((double)std::max<uint64_t>(N, 1) * nf / 4.0) + 1.0
-                                   : std::ceil((double)std::max<uint64_t>(N, 1) * lanes / ns);
+                                   : (double)std::max<uint64_t>(N, 1) * lanes;
         const double need = std::ceil(items / threads);
         const int oversub = have_tuned ? std::max(1, tuned.oversub) : 1;
         blocks = (int)std::min<double>(need, (double)max_blocks * oversub);
@@ -250,6 +255,9 @@ static int plan_ode(int level, int M, uint64_t N, int precision, int scheme, con
     if (rc) return rc;
     int blocks = launch && launch->blocks ? launch->blocks : 0;
     if (blocks < 0) return fail(MLMC_EINVAL, "blocks must be >= 0");
+    // the sample loops stride by the grid's thread count in 32-bit offsets below 2^31
+    if ((uint64_t)blocks * (uint64_t)threads >= (uint64_t(1) << 31))
+        return fail(MLMC_EINVAL, "blocks x threads_per_block must be below 2^31");
     if (!blocks) {
         const double items = std::ceil((double)std::max<uint64_t>(N, 1) / 4.0) + 1.0;
         blocks = (int)std::min<double>(std::ceil(items / threads), (double)max_blocks);

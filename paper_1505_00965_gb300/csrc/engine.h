@@ -68,6 +68,14 @@ const void *level_anti_kernel_fp64(int payoff, int mt, int scheme, bool long_lan
 // mt = 4 or 0; at most 512 threads per block.
 const void *level_ns2_kernel_fp32(int payoff, int mt, bool long_lanes);
 constexpr int kNs2MaxThreads = 512;
+// The planners' default of two samples per thread: FP32 Euler--Maruyama whole paths with M = 4
+// and at least 16 fine steps.  The two-sample kernel takes the same samples per thread on the
+// same grid (a thread's unpaired last sample runs alone).  Timed against one sample per thread on
+// the lookback and arithmetic Asian calls at levels 2-7 and 0.3-6.4 waves of resident threads, it
+// was 0.6 % slower in one case of 84 and faster in the rest: about 3 % on the lookback and 3-8 %
+// on the Asian, 4.5 % over the whole set.  On the straight-line sample of M^l = 4 two samples per
+// thread were slower.
+constexpr long kNs2MinSteps = 16;
 // Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
 const void *ode_level_kernel(int precision, int scheme);
 const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive = false);

@@ -418,7 +418,11 @@ int level_kernels(int l, int M, int precision, const mlmc_model *model, const ml
         return max_resident_blocks(out->k[kVarWhole], kGdThreads, &out->resident[kVarWhole]);
     }
     const int mt = M == 4 ? 4 : 0;
-    const void *whole = pick(mt, false, nf > kLongLaneSteps, false);
+    // whole paths: the two-sample kernel where plan_level takes it by default (same grid rule)
+    const bool ns2 = !anti && precision == MLMC_FP32_PATH && scheme == MLMC_EULER_MARUYAMA && M == 4 &&
+                     nf >= kNs2MinSteps && kGdThreads <= kNs2MaxThreads;
+    const void *whole = ns2 ? level_ns2_kernel_fp32(pay, mt, nf > kLongLaneSteps)
+                            : pick(mt, false, nf > kLongLaneSteps, false);
     if (!whole) return fail(MLMC_EINVAL, "no kernel for payoff %d", pay);
     rc = max_resident_blocks(whole, kGdThreads, &out->resident[kVarWhole]);
     if (rc) return rc;

@@ -567,14 +567,55 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     }
 }
 
-// One thread per sample, NS samples per thread and iteration (i, i + T, ...) of each span, over
-// the samples [first, first + N) (the arguments as for regular_range below).
+// NS samples of one span run in lockstep: offsets i0, i0 + T, ... below n (the first always is),
+// sample indices (s_hi, lo0 + offset); moments go into m / b1..b4 / nb and Y into y_out[c0 + offset].
+template <typename R, int MT, int PAY, bool MIL, int NS, bool RK, int CALLS, bool ANTI, bool LONG>
+__device__ __forceinline__ void multi_samples(const LevelParams &p, uint32_t s_hi, uint32_t lo0, uint32_t i0,
+                                              uint32_t T32, uint32_t n, uint64_t c0, R S0, R inv_nf, R inv_nc,
+                                              R logS0, double m[4], float &b1, float &b2, float &b3, float &b4,
+                                              int &nb, double *y_out)
+{
+    uint32_t s_lo[NS];
+    bool valid[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const uint32_t j = i0 + (uint32_t)i * T32;
+        valid[i] = i == 0 || j < n;
+        s_lo[i] = lo0 + (valid[i] ? j : i0);  // below 2^32: the span stops at the boundary
+    }
+    R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
+    R aS[NS], asum[NS], ahi[NS], als[NS];
+    simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s_hi, s_lo, fS, fsum, fhi, fls, cS, csum, chi, cls,
+                                                               aS, asum, ahi, als);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
+                                    lpost_of(R(p.nf), logS0, fls[i]), inv_nf, p);
+        if constexpr (ANTI)
+            Pf = mul_rn(R(0.5), add_rn(Pf, payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
+                                                                lpost_of(R(p.nf), logS0, als[i]), inv_nf, p)));
+        R Y = Pf;
+        if (!p.fine_only)
+            Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
+                                      lpost_of(R(p.nf / p.M), logS0, cls[i]), inv_nc, p);
+        if (valid[i]) {
+            if (y_out) y_out[c0 + i0 + (uint32_t)i * T32] = (double)Y;
+            add_moments(Y, m, b1, b2, b3, b4, nb);
+        }
+    }
+}
+
+// One thread per sample over the samples [first, first + N) (the arguments as for regular_range
+// below): thread t takes the offsets t, t + T, t + 2T, ... of each span, NS of them per iteration.
+// With NS = 2 a thread whose last offset has no partner runs it alone, so every thread takes the
+// same samples as with NS = 1 and the grid is the same; only the pairing differs.
 template <typename R, int MT, int PAY, bool MIL, int NS, bool RK = true, int CALLS = 0, bool ANTI = false,
           bool LONG = false>
 __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first, uint64_t N, uint64_t t,
                                             uint64_t T, double m[4], float &b1, float &b2, float &b3,
                                             float &b4, int &nb, double *y_out)
 {
+    static_assert(NS == 1 || NS == 2, "one or two samples per thread");
     const R S0 = R(p.S0), inv_nf = R(p.inv_nf), inv_nc = R(p.inv_nc);
     const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
     // The range in spans of at most 2^31 samples that stay inside one 2^32-aligned block of sample
@@ -590,35 +631,19 @@ __device__ __forceinline__ void multi_range(const LevelParams &p, uint64_t first
         const uint64_t left = N - c0 < kSpan32 ? N - c0 : kSpan32;
         const uint32_t n = (uint32_t)(left < room ? left : room);  // c0 + n <= N
         const uint32_t s_hi = (uint32_t)(start >> 32), lo0 = (uint32_t)start;
-        for (uint32_t i0 = t32; i0 < n; i0 += NS * T32) {
-            uint32_t s_lo[NS];
-            bool valid[NS];
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                const uint32_t j = i0 + (uint32_t)i * T32;
-                valid[i] = i == 0 || j < n;
-                s_lo[i] = lo0 + (valid[i] ? j : i0);  // below 2^32: the span stops at the boundary
-            }
-            R fS[NS], fsum[NS], fhi[NS], fls[NS], cS[NS], csum[NS], chi[NS], cls[NS];
-            R aS[NS], asum[NS], ahi[NS], als[NS];
-            simulate_multi<R, MT, PAY, MIL, NS, RK, CALLS, ANTI, LONG>(p, s_hi, s_lo, fS, fsum, fhi, fls, cS, csum, chi, cls,
-                                                                       aS, asum, ahi, als);
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
-                                            lpost_of(R(p.nf), logS0, fls[i]), inv_nf, p);
-                if constexpr (ANTI)
-                    Pf = mul_rn(R(0.5), add_rn(Pf, payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
-                                                                        lpost_of(R(p.nf), logS0, als[i]), inv_nf, p)));
-                R Y = Pf;
-                if (!p.fine_only)
-                    Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
-                                              lpost_of(R(p.nf / p.M), logS0, cls[i]), inv_nc, p);
-                if (valid[i]) {
-                    if (y_out) y_out[c0 + i0 + (uint32_t)i * T32] = (double)Y;
-                    add_moments(Y, m, b1, b2, b3, b4, nb);
-                }
-            }
+        uint32_t i0 = t32;
+        if constexpr (NS == 2) {
+            // i0 < n <= 2^31 and T32 < 2^31, so i0 + T32 does not wrap
+            for (; i0 < n && n - i0 > T32; i0 += 2 * T32)
+                multi_samples<R, MT, PAY, MIL, 2, RK, CALLS, ANTI, LONG>(p, s_hi, lo0, i0, T32, n, c0, S0, inv_nf,
+                                                                         inv_nc, logS0, m, b1, b2, b3, b4, nb, y_out);
+            if (i0 < n)
+                multi_samples<R, MT, PAY, MIL, 1, RK, CALLS, ANTI, LONG>(p, s_hi, lo0, i0, T32, n, c0, S0, inv_nf,
+                                                                         inv_nc, logS0, m, b1, b2, b3, b4, nb, y_out);
+        } else {
+            for (; i0 < n; i0 += T32)
+                multi_samples<R, MT, PAY, MIL, 1, RK, CALLS, ANTI, LONG>(p, s_hi, lo0, i0, T32, n, c0, S0, inv_nf,
+                                                                         inv_nc, logS0, m, b1, b2, b3, b4, nb, y_out);
         }
         c0 += n;
     }
@@ -899,7 +924,7 @@ __global__ void __launch_bounds__(1024) level_kernel(const LevelParams p)
 
 // Two samples per thread and iteration, one thread per sample (no split, no antithetic path): the
 // two samples' Philox and step chains are independent, so each scheduler has twice the
-// instruction-level parallelism per warp, at about 1.5 times the registers.  A kernel of its own
+// instruction-level parallelism per warp, at more registers (64 against 54).  A kernel of its own
 // (not a runtime branch of level_kernel) so that the one-sample kernels keep their register count;
 // at most 512 threads per block, which lets it hold up to 128 registers.
 template <typename R, int MT, int PAY, bool LONG = false>

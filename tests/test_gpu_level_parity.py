@@ -127,16 +127,18 @@ def test_other_refinement_factors(mlmc, M, level, N, lanes, payoff, precision):
     _check_level(mlmc, level, M, N, 3, payoff, precision, launch={"lanes_per_path": lanes})
 
 
+@pytest.mark.parametrize("blocks", [0, 2])
 @pytest.mark.parametrize("payoff", PAYOFFS)
 @pytest.mark.parametrize("M,level,N,first", [(4, 1, 20011, 977), (4, 2, 8191, 5), (4, 3, 4001, 123456789),
                                              (4, 5, 1201, 2 ** 33 + 3), (4, 6, 601, 11), (4, 7, 257, 0),
                                              (2, 2, 5001, 3), (2, 5, 2001, 3), (8, 2, 2001, 3)])
-def test_two_samples_per_thread_match_oracle(mlmc, M, level, N, first, payoff):
+def test_two_samples_per_thread_match_oracle(mlmc, M, level, N, first, payoff, blocks):
     """The two-samples-per-thread kernels (FP32 Euler--Maruyama, one thread per sample) step two
-    samples in lockstep: every sample against the oracle, ragged tails (odd N, so a thread's
-    second sample runs past the range and is dropped) included."""
+    samples in lockstep: every sample against the oracle.  On a grid of 2 blocks (512 threads) a
+    thread runs pairs and then, where its last sample has no partner (N not a multiple of 1024),
+    that sample alone; on the planner's grid most threads hold one sample and run it alone."""
     _check_level(mlmc, level, M, N, first, payoff, "fp32",
-                 launch={"lanes_per_path": 1, "samples_per_thread": 2, "threads_per_block": 256})
+                 launch={"lanes_per_path": 1, "samples_per_thread": 2, "threads_per_block": 256, "blocks": blocks})
 
 
 @pytest.mark.parametrize("threads,blocks,spt", [(32, 1, 2), (64, 3, 2), (512, 0, 2), (96, 5, 2)])
