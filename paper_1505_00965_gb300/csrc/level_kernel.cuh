@@ -857,16 +857,20 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     const Level0Consts c0 = level0_consts(p);
     // two copies of the loop, with and without per-sample output, keep the output test out of it;
     // the blocks go in spans inside one 2^32-aligned run of block indices, so the counter's high
-    // word and its Philox products stay fixed over a span
+    // word and its Philox products stay fixed over a span.  Thread t takes blocks t, t + T, ... of
+    // a span; on the FP32 one-step payoffs two at a time (two independent Philox chains for the
+    // scheduler: 8.9 -> 9.4e11 samples/s on the lookback, +8 % on the Asian, +5 % on the
+    // European at 4e8 samples), and an unpaired last block alone.
+    constexpr bool kPairBlocks = sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL;
     auto whole_blocks = [&](auto with_output) {
         for (uint64_t qs = qa; qs < qb;) {
             const uint64_t room = (uint64_t(1) << 32) - (uint32_t)qs;
             const uint64_t len = qb - qs < room ? qb - qs : room;
             const uint32_t q_hi = (uint32_t)(qs >> 32), lo0 = (uint32_t)qs;
-            for (uint64_t u = t; u < len; u += T) {
-                const uint32_t q_lo = lo0 + (uint32_t)u;  // below 2^32: the span stops at the boundary
-                R z[4], d[4], Y[4];
-                block_increments<R, MIL, RK>(p, q_hi, q_lo, z, d);
+            // the four samples of block lo0 + u (below 2^32: the span stops at the boundary)
+            auto block_Y = [&](uint64_t u, R Y[4]) {
+                R z[4], d[4];
+                block_increments<R, MIL, RK>(p, q_hi, lo0 + (uint32_t)u, z, d);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     if constexpr (sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL) {
@@ -876,10 +880,29 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
                         em_step<R, PAY, false>(fS, fsum, fhi, flo, fls, d[r]);
                         Y[r] = payoff_value<R, PAY>(S0 * fS, S0 * fsum, S0 * fhi, logS0 + fls, inv_nf, p);
                     }
-                    if constexpr (decltype(with_output)::value)
-                        y_out[(qs + u) * 4 + r - first] = (double)Y[r];
+                }
+            };
+            auto emit = [&](uint64_t u, const R Y[4]) {
+                if constexpr (decltype(with_output)::value) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) y_out[(qs + u) * 4 + r - first] = (double)Y[r];
                 }
                 add_moments4(Y, m, b1, b2, b3, b4, nb);
+            };
+            uint64_t u = t;
+            if constexpr (kPairBlocks) {
+                for (; u + T < len; u += 2 * T) {  // len <= 2^32 and T < 2^31: no wrap
+                    R Ya[4], Yb[4];
+                    block_Y(u, Ya);
+                    block_Y(u + T, Yb);
+                    emit(u, Ya);
+                    emit(u + T, Yb);
+                }
+            }
+            for (; u < len; u += T) {
+                R Y[4];
+                block_Y(u, Y);
+                emit(u, Y);
             }
             qs += len;
         }
