@@ -351,6 +351,13 @@ void fill_params(LevelParams &p, int level, int M, uint64_t N, uint64_t first,
     p.h = h;
     p.inv_nf = 1.0 / (double)nf;
     p.inv_nc = level > 0 ? (double)M / (double)nf : 0.0;
+    const double dS0 = p.disc * p.S0, dK = p.disc * p.K;
+    p.pay_dS0 = (float)dS0;
+    p.pay_mdK = (float)(-dK);
+    p.pay_af = (float)(dS0 * p.inv_nf);
+    p.pay_bf = (float)(0.5 * dS0 * p.inv_nf - dK);
+    p.pay_ac = (float)(dS0 * p.inv_nc);
+    p.pay_bc = (float)(0.5 * dS0 * p.inv_nc - dK);
     p.first = first;
     p.N = N;
     p.key0 = (uint32_t)seed;

@@ -20,6 +20,9 @@ struct LevelParams {
     double sqrt_h;    // sqrt(h): Brownian increment scale of one fine step
     double sqrt_tg;   // sqrt(T / 16): scale of the control variate's grid increments
     double h;         // fine step T / M^l
+    // FP32 payoff constants of the call options on paths relative to S0 (rel_payoff): disc S0,
+    // -disc K, and for the fine (f) and coarse (c) path disc S0 / n, disc S0 / (2 n) - disc K
+    float pay_dS0, pay_mdK, pay_af, pay_bf, pay_ac, pay_bc;
     uint64_t first;   // first sample index
     uint64_t N;       // number of samples
     uint32_t key0, key1;  // Philox key (seed low, seed high)

@@ -134,6 +134,41 @@ __device__ __forceinline__ R payoff_value(R Sn, R post, R hi, R lpost, R inv_n, 
     return payoff_from<R, PAY>(Sn, post, hi, lpost, inv_n, R(p.K), R(p.disc), R(p.S0), R(p.Q));
 }
 
+// FP32 paths, European, arithmetic Asian and lookback calls: the payoff from the path relative to
+// S0 (start value 1; primes below) as one or two fused multiply-adds and a max, with constants
+// the host forms in FP64 (LevelParams::pay_*, kernel-parameter operands).  Since disc > 0,
+// disc max(x, 0) = max(disc x, 0):
+//   European  max(disc S0 S_n' - disc K, 0), lookback the same on the maximum;
+//   Asian     max(disc S0 / n (sum' - S_n' / 2) + (disc S0 / (2 n) - disc K), 0), sum' over the
+//             post-step values: (1/n) sum_{i<n} (S_i + S_{i+1}) / 2 written out as in payoff_from.
+// The values equal payoff_from's in exact arithmetic and differ by FP32 rounding only.  Every
+// one-thread-per-sample copy of the FP32 level kernels uses this form, so a sample's Y does not
+// depend on the copy that computes it.
+template <typename R, int PAY> constexpr bool kRelPayoff =
+    sizeof(R) == 4 && (PAY == kEuropean || PAY == kAsian || PAY == kLookback);
+template <int PAY>
+__device__ __forceinline__ float rel_payoff(const LevelParams &p, bool coarse, float S, float sum, float hi)
+{
+    if constexpr (PAY == kEuropean) return fmaxf(fmaf(p.pay_dS0, S, p.pay_mdK), 0.f);
+    else if constexpr (PAY == kLookback) return fmaxf(fmaf(p.pay_dS0, hi, p.pay_mdK), 0.f);
+    else return fmaxf(fmaf(coarse ? p.pay_ac : p.pay_af, fmaf(-0.5f, S, sum), coarse ? p.pay_bc : p.pay_bf), 0.f);
+}
+
+// Payoff of one whole path relative to S0 (values S, sum, hi, log-sum ls after its n steps, 1/n =
+// inv_n; `coarse` picks the coarse path): the relative form above where it exists, else
+// payoff_value on the values times S0.
+template <typename R, int PAY>
+__device__ __forceinline__ R path_payoff(const LevelParams &p, bool coarse, R S, R sum, R hi, R ls, R S0, R logS0,
+                                         R inv_n)
+{
+    if constexpr (kRelPayoff<R, PAY>) {
+        return rel_payoff<PAY>(p, coarse, S, sum, hi);
+    } else {
+        const R n = coarse ? R(p.nf / p.M) : R(p.nf);
+        return payoff_value<R, PAY>(S0 * S, S0 * sum, S0 * hi, lpost_of(n, logS0, ls), inv_n, p);
+    }
+}
+
 // Philox block of counter c under the parameters' key: from the precomputed round keys (RK, the
 // level kernels, whose parameters sit in the constant bank) or from the two key words (the
 // batched kernel, whose parameters sit in global memory).
@@ -547,11 +582,9 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
     if constexpr (!SPLIT) {
         simulate_steps<R, MT, PAY, false, MIL, RK, LONG>(p, slo, shi, 0, p.nf >> 2, fa, ca);
         const R logS0 = PAY == kGeoAsian ? PathAcc<R, PAY, false>::log_r(S0) : R(0);
-        const R Pf = payoff_value<R, PAY>(S0 * fa.S, S0 * fa.sum, S0 * fa.hi,
-                                          lpost_of(R(p.nf), logS0, fa.lsum), inv_nf, p);
+        const R Pf = path_payoff<R, PAY>(p, false, fa.S, fa.sum, fa.hi, fa.lsum, S0, logS0, inv_nf);
         if (p.fine_only) return Pf;
-        const R Pc = payoff_value<R, PAY>(S0 * ca.S, S0 * ca.sum, S0 * ca.hi,
-                                          lpost_of(R(p.nf / p.M), logS0, ca.lsum), inv_nc, p);
+        const R Pc = path_payoff<R, PAY>(p, true, ca.S, ca.sum, ca.hi, ca.lsum, S0, logS0, inv_nc);
         return Pf - Pc;
     } else {
         const int calls = (p.nf >> 2) / P;
@@ -572,8 +605,8 @@ __device__ __forceinline__ R sample_Y(const LevelParams &p, uint64_t s, int lig,
 template <typename R, int MT, int PAY, bool MIL, int NS, bool RK, int CALLS, bool ANTI, bool LONG>
 __device__ __forceinline__ void multi_samples(const LevelParams &p, uint32_t s_hi, uint32_t lo0, uint32_t i0,
                                               uint32_t T32, uint32_t n, uint64_t c0, R S0, R inv_nf, R inv_nc,
-                                              R logS0, double m[4], float &b1, float &b2, float &b3, float &b4,
-                                              int &nb, double *y_out)
+                                              R logS0, double m[4], float &b1, float &b2, float &b3,
+                                              float &b4, int &nb, double *y_out)
 {
     uint32_t s_lo[NS];
     bool valid[NS];
@@ -589,15 +622,12 @@ __device__ __forceinline__ void multi_samples(const LevelParams &p, uint32_t s_h
                                                                aS, asum, ahi, als);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        R Pf = payoff_value<R, PAY>(S0 * fS[i], S0 * fsum[i], S0 * fhi[i],
-                                    lpost_of(R(p.nf), logS0, fls[i]), inv_nf, p);
+        R Pf = path_payoff<R, PAY>(p, false, fS[i], fsum[i], fhi[i], fls[i], S0, logS0, inv_nf);
         if constexpr (ANTI)
-            Pf = mul_rn(R(0.5), add_rn(Pf, payoff_value<R, PAY>(S0 * aS[i], S0 * asum[i], S0 * ahi[i],
-                                                                lpost_of(R(p.nf), logS0, als[i]), inv_nf, p)));
+            Pf = mul_rn(R(0.5), add_rn(Pf, path_payoff<R, PAY>(p, false, aS[i], asum[i], ahi[i], als[i], S0,
+                                                                logS0, inv_nf)));
         R Y = Pf;
-        if (!p.fine_only)
-            Y -= payoff_value<R, PAY>(S0 * cS[i], S0 * csum[i], S0 * chi[i],
-                                      lpost_of(R(p.nf / p.M), logS0, cls[i]), inv_nc, p);
+        if (!p.fine_only) Y -= path_payoff<R, PAY>(p, true, cS[i], csum[i], chi[i], cls[i], S0, logS0, inv_nc);
         if (valid[i]) {
             if (y_out) y_out[c0 + i0 + (uint32_t)i * T32] = (double)Y;
             add_moments(Y, m, b1, b2, b3, b4, nb);
@@ -859,8 +889,7 @@ __device__ __forceinline__ void small_range(const LevelParams &p, uint64_t first
     // the blocks go in spans inside one 2^32-aligned run of block indices, so the counter's high
     // word and its Philox products stay fixed over a span.  Thread t takes blocks t, t + T, ... of
     // a span; on the FP32 one-step payoffs two at a time (two independent Philox chains for the
-    // scheduler: 8.9 -> 9.4e11 samples/s on the lookback, +8 % on the Asian, +5 % on the
-    // European at 4e8 samples), and an unpaired last block alone.
+    // scheduler: 1.3-1.9 % faster at 4e8 samples), and an unpaired last block alone.
     constexpr bool kPairBlocks = sizeof(R) == 4 && kLevel0Affine<PAY> && !MIL;
     auto whole_blocks = [&](auto with_output) {
         for (uint64_t qs = qa; qs < qb;) {
