@@ -128,11 +128,11 @@ def _oracle_job(args):
     return sum(n * M ** l for l, n in enumerate(e.N)), dt
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu (level_kernel, lookback,
-# level 6, N = 10^6, one thread per sample): the kernels read no input arrays; the algorithmic
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu (level_ns2_kernel, lookback,
+# level 6, N = 10^6, two samples per thread): the kernels read no input arrays; the algorithmic
 # bytes are the block partials and the four sums (608 x 32 + 32 = 19.5 KB).
-TRAFFIC_BYTES_PER_LAUNCH = 62976
-TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one level_kernel launch (lookback, "
+TRAFFIC_BYTES_PER_LAUNCH = 64512
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one level_ns2_kernel launch (lookback, "
                  "level 6, N=1e6, 608 blocks); algorithmic bytes 19.5 KB of block partials")
 # FP64 instructions (DFMA + DADD + DMUL, thread level) per coupled step of the FP64 Asian kernel, from
 # ncu's per-opcode counters on one launch (level 6, N = 1e5, one thread per sample).
@@ -449,7 +449,8 @@ def gpu_arm(args) -> None:
     achieved = instr / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginstr/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_basis": TRAFFIC_BASIS,
-                "kernel": "level_kernel (FP32 paths, all levels of the step; time = the driver's events around each "
+                "kernel": "level_ns2_kernel, level_kernel and level_small_kernel (FP32 paths, all levels of the "
+                          "step; time = the driver's events around each "
                           "round on the engine stream, which bracket its four streams' launches)",
                 "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz (max SM clock), "
                               "one warp instruction per scheduler per clock",
