@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmlmc_gb300.so")
-SOURCES = ["api.cu", "batch.cu", "cv.cu", "graph_driver.cu", "level_anti_fp32.cu", "level_anti_fp64.cu", "level_fp32.cu", "level_fp32_mil.cu", "level_fp32_ns2.cu",
+SOURCES = ["api.cu", "batch.cu", "cv.cu", "cv_level.cu", "graph_driver.cu", "level_anti_fp32.cu", "level_anti_fp64.cu", "level_fp32.cu", "level_fp32_mil.cu", "level_fp32_ns2.cu",
            "level_fp64.cu", "level_fp64_mil.cu", "ode.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -35,19 +35,6 @@ static_assert(kNumParams == MLMC_CV_PARAMS && kInputs == MLMC_CV_INPUTS, "networ
 constexpr int kCvThreads = 256;
 constexpr double kMinKappa = 1.0 / 64.0, kMaxKappa = 4096.0;  // mean points per path sample
 
-const void *cv_level_kernel_for(int payoff)
-{
-    switch (payoff) {
-    case kEuropean: return (const void *)cv_level_tc_kernel<kEuropean>;
-    case kAsian: return (const void *)cv_level_tc_kernel<kAsian>;
-    case kLookback: return (const void *)cv_level_tc_kernel<kLookback>;
-    case kDigital: return (const void *)cv_level_tc_kernel<kDigital>;
-    case kLinear: return (const void *)cv_level_tc_kernel<kLinear>;
-    case kGeoAsian: return (const void *)cv_level_tc_kernel<kGeoAsian>;
-    default: return nullptr;
-    }
-}
-
 const void *cv_data_kernel_for(int payoff)
 {
     switch (payoff) {
@@ -79,9 +66,9 @@ int grid_for(const void *kernel, uint64_t items, int *blocks)
 // out of step: 5% faster than one wave at 4e7 samples); one wave otherwise, since each block pays
 // for loading the network and for the FP64 warp reductions of its eight sums (with 8.6 tiles per
 // block these kept the FP64 pipe 20% busy).
-int cv_level_grid(int payoff, uint64_t items, int *blocks)
+int cv_level_grid(int payoff, int level, int M, uint64_t items, int *blocks)
 {
-    const void *k = cv_level_kernel_for(payoff);
+    const void *k = cv_level_kernel_fp32(payoff, level, M);
     if (!k) return fail(MLMC_EINVAL, "payoff %d has no control-variate kernel", payoff);
     int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserved = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -135,7 +122,7 @@ int launch_cv_level(const mlmc_cv *cv, int level, uint64_t N, uint64_t first, ui
     p.partials = (double *)((char *)ws + kTicketBytes);
     const float *params = cv->d_params[level];
     void *args[] = {&p, (void *)&params, &d_sums8, &d_r, &d_g};
-    CUDA_TRY(cudaLaunchKernel(cv_level_kernel_for(cv->payoff.kind), dim3(blocks), dim3(kCvTcThreads), args, 0, st));
+    CUDA_TRY(cudaLaunchKernel(cv_level_kernel_fp32(cv->payoff.kind, level, cv->M), dim3(blocks), dim3(kCvTcThreads), args, 0, st));
     return MLMC_OK;
 }
 
@@ -367,7 +354,7 @@ int mlmc_cv_level_sums(const mlmc_cv *cv, int level, uint64_t N, uint64_t first,
         return MLMC_OK;
     }
     int blocks = 0;
-    rc = cv_level_grid(cv->payoff.kind, N, &blocks);
+    rc = cv_level_grid(cv->payoff.kind, level, cv->M, N, &blocks);
     if (rc) return rc;
     return with_workspace(sums_workspace(blocks, 8), st, [&](void *ws) {
         return launch_cv_level(cv, level, N, first, seed, d_sums8, d_r, d_g, ws, blocks, st);
@@ -613,7 +600,7 @@ int mlmc_cv_train(int M, const mlmc_model *model, const mlmc_payoff *payoff, uin
                                      &warm_plan);
             if (rc) return cleanup(rc);
             int cvb = 0;
-            rc = cv_level_grid(payoff->kind, nc, &cvb);
+            rc = cv_level_grid(payoff->kind, l, M, nc, &cvb);
             if (rc) return cleanup(rc);
             // the lattice statistics use kStatReplicates replicates (2^23 points)
             constexpr uint64_t kStatReplicates = 128;
@@ -767,7 +754,7 @@ extern "C" int mlmc_estimate_cv(double eps, int M, int Lmin, int Lmax, uint64_t 
             if (uses(l)) {
                 drep[l] = mean_replicates(cv->info[l].kappa, dN[l], nrep[l]);
                 int cb = 0;
-                rc = cv_level_grid(payoff->kind, dN[l], &cb);
+                rc = cv_level_grid(payoff->kind, l, M, dN[l], &cb);
                 if (!rc)
                     rc = launch_cv_level(cv, l, dN[l], drv.samples_taken(l), seed, d_sums + stride * l, nullptr,
                                          nullptr, ws, std::min(cb, ws_blocks), sk);

@@ -79,6 +79,10 @@ constexpr int kNs2MaxThreads = 512;
 // on the Asian, 4.5 % over the whole set.  On the straight-line sample of M^l = 4 two samples per
 // thread were slower.
 constexpr long kNs2MinSteps = 16;
+// The control variate's level-estimator kernel (cv_level.cu) for a payoff on level `level` with
+// refinement M: compiled for M^l = 1, 4, 16 at M = 4, else for a run-time M^l; NULL for an unknown
+// payoff.
+const void *cv_level_kernel_fp32(int payoff, int level, int M);
 // Level kernel of the QUINTIC_ODE model (ode.cu): precision, scheme (EM or tamed EM).
 const void *ode_level_kernel(int precision, int scheme);
 const void *level_kernel_fp64(int payoff, int mt, bool split, int scheme, bool long_lanes, bool positive = false);
