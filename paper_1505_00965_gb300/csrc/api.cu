@@ -150,11 +150,13 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
     } else {
         // The power of two P (chunks of whole Philox blocks and coarse steps, at least 256 steps
         // each) with the least modelled launch time.  T resident threads run the N P lane-items
-        // in waves; a partial last wave filled to a fraction f costs min(1, 3 f) of a full one
-        // (its warps run faster on the emptier SMs).  A lane costs its M^l / P steps plus about
-        // 12 steps of chunk join, payoff and moments, and a split step about 5 % more than a
-        // whole-path one.  A larger P must win by more than 1 %.  (Fitted to launch timings
-        // of levels 3..8 at 0.25..4.5 waves.)  Fewer items than one wave still cost at least a
+        // in waves; after w >= 1 whole waves, a partial last wave filled to a fraction f costs
+        // min(1, 1.25 f + 0.1) of a full one (its warps run faster on the emptier SMs), and a
+        // launch of fewer items than a wave min(1, 3 f).  A lane costs its M^l / P steps plus
+        // about 12 steps of chunk join, payoff and moments, and a split step about 8 % more than
+        // a whole-path one (two samples per thread).  A larger P must win by more than 1 %.
+        // (Fitted to launch timings of the lookback, levels 5..8 at 0.2..3.7 waves: 1.3-1.6 %
+        // less time per level than the earlier fit.)  Fewer items than one wave still cost at least a
         // quarter of a wave: a warp alone on its scheduler takes about 64 cycles per step,
         // against about 266 for each warp of a full SM (measured on levels 6..12 at 1 to 2^15
         // samples), so short launches go to the most lanes.
@@ -178,8 +180,8 @@ int plan_level(int level, int M, uint64_t N, int precision, int payoff, int sche
                 const double w = (double)std::max<uint64_t>(N, 1) * P / T;
                 const double full = std::floor(w);
                 const double waves = w < 1.0 ? std::max(std::min(1.0, 3.0 * w), kLoneWaveCost)
-                                             : full + std::min(1.0, 3.0 * (w - full));
-                const double per_step = P > 1 ? 1.05 : 1.0;
+                                             : full + std::min(1.0, kLanesTailSlope * (w - full) + kLanesTailBase);
+                const double per_step = P > 1 ? kLanesSplitStep : 1.0;
                 const double cost = waves * ((double)nf / P + 12.0) * per_step;
                 if (P == 1 || cost < 0.99 * best) {
                     best = cost;

@@ -79,6 +79,10 @@ constexpr int kNs2MaxThreads = 512;
 // on the Asian, 4.5 % over the whole set.  On the straight-line sample of M^l = 4 two samples per
 // thread were slower.
 constexpr long kNs2MinSteps = 16;
+// The lanes-per-path model of both planners (plan_level and the device rounds): the cost of a
+// partial last wave after whole ones, min(1, kLanesTailSlope f + kLanesTailBase) of a wave at
+// fill f, and a split step's cost relative to a whole-path one.
+constexpr double kLanesTailSlope = 1.25, kLanesTailBase = 0.1, kLanesSplitStep = 1.08;
 // The control variate's level-estimator kernel (cv_level.cu) for a payoff on level `level` with
 // refinement M: compiled for M^l = 1, 4, 16 at M = 4, else for a run-time M^l; NULL for an unknown
 // payoff.

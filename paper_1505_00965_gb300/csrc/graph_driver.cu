@@ -164,8 +164,9 @@ __device__ void gd_plan(const GdState &s, int l, uint64_t dN, int &variant, int 
                 const double T = (double)(P == 1 ? s.res1[l] : s.resp[l]) * threads;
                 const double w = Nd * P / T;
                 const double full = floor(w);
-                const double waves = w < 1.0 ? fmax(fmin(1.0, 3.0 * w), kGdLoneWaveCost) : full + fmin(1.0, 3.0 * (w - full));
-                const double per_step = P > 1 ? 1.05 : 1.0;
+                const double waves = w < 1.0 ? fmax(fmin(1.0, 3.0 * w), kGdLoneWaveCost)
+                                             : full + fmin(1.0, kLanesTailSlope * (w - full) + kLanesTailBase);
+                const double per_step = P > 1 ? kLanesSplitStep : 1.0;
                 const double cost = waves * ((double)nf / P + 12.0) * per_step;
                 if (P == 1 || cost < 0.99 * best) {
                     best = cost;
