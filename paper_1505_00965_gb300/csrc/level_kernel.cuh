@@ -764,18 +764,22 @@ __device__ __forceinline__ void block_increments(const LevelParams &p, uint32_t 
 // n = 1) A = (S_0 + S_1) / 2 = S_0 (1 + d / 2); lookback max(S_0, S_1) = S_0 (1 + max(d, 0)).
 template <int PAY> constexpr bool kLevel0Affine = PAY == kEuropean || PAY == kAsian || PAY == kLookback;
 struct Level0Consts {
-    float dS0, half_dS0, dS0mK;
+    float dS0, half_dS0, dS0mK, dS0mK_pos;  // dS0mK_pos = max(dS0mK, 0)
 };
 __device__ __forceinline__ Level0Consts level0_consts(const LevelParams &p)
 {
-    return {(float)(p.disc * p.S0), (float)(0.5 * p.disc * p.S0), (float)(p.disc * (p.S0 - p.K))};
+    const float dS0mK = (float)(p.disc * (p.S0 - p.K));
+    return {(float)(p.disc * p.S0), (float)(0.5 * p.disc * p.S0), dS0mK, fmaxf(dS0mK, 0.f)};
 }
+// Lookback: max(fma(max(d, 0), dS0, dS0mK), 0) = max(fma(d, dS0, dS0mK), max(dS0mK, 0)) exactly,
+// since dS0 > 0: for d > 0 the fma rounds to at least dS0mK, and for d <= 0 it rounds to at most
+// dS0mK (equal at d = -0), so both forms give the same float.  One multiply-add and one max.
 template <int PAY>
 __device__ __forceinline__ float level0_payoff(float d, const Level0Consts &c)
 {
     if constexpr (PAY == kEuropean) return fmaxf(fmaf(d, c.dS0, c.dS0mK), 0.f);
     else if constexpr (PAY == kAsian) return fmaxf(fmaf(d, c.half_dS0, c.dS0mK), 0.f);
-    else return fmaxf(fmaf(fmaxf(d, 0.f), c.dS0, c.dS0mK), 0.f);
+    else return fmaxf(fmaf(d, c.dS0, c.dS0mK), c.dS0mK_pos);
 }
 
 // The samples of Philox block q (slots r = 0 .. G - 1, sample q G + r) that lie in
