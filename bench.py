@@ -131,7 +131,7 @@ def _oracle_job(args):
 # DRAM bytes (read + write) of one launch of the dominant kernel, from ncu (level_ns2_kernel, lookback,
 # level 6, N = 10^6, two samples per thread): the kernels read no input arrays; the algorithmic
 # bytes are the block partials and the four sums (608 x 32 + 32 = 19.5 KB).
-TRAFFIC_BYTES_PER_LAUNCH = 64512
+TRAFFIC_BYTES_PER_LAUNCH = 97280
 TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one level_ns2_kernel launch (lookback, "
                  "level 6, N=1e6, 608 blocks); algorithmic bytes 19.5 KB of block partials")
 # FP64 instructions (DFMA + DADD + DMUL, thread level) per coupled step of the FP64 Asian kernel, from
