@@ -21,6 +21,7 @@ import json
 import math
 import os
 import statistics
+import select
 import subprocess
 import sys
 import time
@@ -234,6 +235,13 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        # wait (at most 10 s) for the first sample, taken before the timed region and dropped, so
+        # that nvidia-smi's start-up (process and NVML initialisation) does not overlap the first
+        # timed step
+        if self.proc is not None and self.proc.stdout is not None:
+            ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+            if ready:
+                self.proc.stdout.readline()
 
     def stop(self) -> dict:
         if self.proc is None:

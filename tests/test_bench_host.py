@@ -38,6 +38,26 @@ def test_parse_clock_lines():
     assert bench.parse_clock_lines([])["sm_mhz"] is None
 
 
+def test_clock_sampler_drops_its_start_up_sample(tmp_path, monkeypatch):
+    """The sampler waits for nvidia-smi's first line before the timed region and drops it (here a
+    stand-in script on PATH prints a 1000 MHz line first, then 2000 MHz lines)."""
+    import time
+
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1000, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "while true; do\n"
+                    "  echo '0, 2000, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "  sleep 0.05\n"
+                    "done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    sampler = bench.ClockSampler(None)
+    time.sleep(0.3)
+    c = sampler.stop()
+    assert c["sm_mhz"] == 2000 and c["sm_max_mhz"] == 2070 and c["reasons"] == []
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
