@@ -127,6 +127,16 @@ def test_other_refinement_factors(mlmc, M, level, N, lanes, payoff, precision):
     _check_level(mlmc, level, M, N, 3, payoff, precision, launch={"lanes_per_path": lanes})
 
 
+@pytest.mark.parametrize("payoff", ["european", "asian", "lookback", "digital"])
+@pytest.mark.parametrize("first,N", [(0, 20011), (3, 20013), (2 ** 34 - 4098, 20000)])
+def test_level0_block_pairs_match_oracle(mlmc, payoff, first, N):
+    """Level 0 on a grid of 2 blocks (512 threads): each thread runs its whole Philox blocks two
+    at a time (the one-step call payoffs) and an unpaired last one alone, with partial blocks at
+    the range's ends and, in the last case, Philox block index 2^32 (a span boundary of the
+    loop's 32-bit offsets) inside the range."""
+    _check_level(mlmc, 0, 4, N, first, payoff, "fp32", launch={"threads_per_block": 256, "blocks": 2})
+
+
 @pytest.mark.parametrize("blocks", [0, 2])
 @pytest.mark.parametrize("payoff", PAYOFFS)
 @pytest.mark.parametrize("M,level,N,first", [(4, 1, 20011, 977), (4, 2, 8191, 5), (4, 3, 4001, 123456789),
